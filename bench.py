@@ -1,0 +1,326 @@
+"""Benchmark: Metropolis spin-flip attempts/s of the CUDA path on one GB300 (or N replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload fractal256|flat16|fractal2048]
+    python bench.py --impl reference ...      # the CPU oracle on a bounded sample, same metric
+
+One step = one pass of the whole hot path over one film: the full temperature scan (or
+hysteresis loop) of the workload, every sweep of every schedule step, with the spins resident
+in device memory.  Synthetic seeded inputs (fractal height maps) stand in for the paper's STM
+images.  Timing: CUDA events on the launching stream around each step; L2 is flushed between
+steps (outside the events); W untimed warm-up steps; max over ranks.  Under torchrun every rank
+runs its own replica of the film (the single-film path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spin-flip attempts/s and % roofline on 1 GB300, batched/served vs plain"
+UNIT = "attempts/s"
+# Integer work the method needs per attempt: a quarter Philox4x32-10 block
+# (10 rounds x (2 wide multiplies + 2 three-input XORs) / 4 sites = 10), the 12-neighbour sum
+# (3: four sites per 32-bit add) and the acceptance (2: table lookup, compare).
+OPS_PER_ATTEMPT = 15
+SMS, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+ALU_PEAK_TOPS = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12    # 40.3 T int32 lane-ops/s
+
+
+def workload(name: str):
+    from paper_1205_5588_gb300 import workloads as W
+    if name == "fractal256":
+        return W.fractal256_tscan()
+    if name == "flat16":
+        return W.flat16_hysteresis()
+    if name == "fractal2048":
+        return W.fractal2048_hysteresis()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fp:
+            for line in fp:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def flush_l2(buf):
+    buf.fill_(1)     # 256 MiB write: larger than the 129 MB L2
+
+
+def attempts_of(spec, n_occ):
+    s = spec["schedule"]
+    return int(n_occ) * int(s["eq"].sum() + s["meas"].sum())
+
+
+def run_impl(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_1205_5588_gb300 import build as B
+    B.build()
+    from paper_1205_5588_gb300 import isingfilm as I
+
+    spec = workload(args.workload)
+    sched = spec["schedule"]
+    seed = spec["seed"] + 1000003 * rank        # each rank: its own replica
+    stream = torch.cuda.current_stream()
+    lat = I.Lattice(spec["heights"], spec["layers"], periodic_x=spec["periodic_x"], periodic_y=spec["periodic_y"],
+                    packed=spec["packed"], seed=seed, init=spec["init"], stream=stream)
+    if args.ctas or args.threads:
+        lat.set_launch(args.ctas, args.threads)
+    n_occ = lat.info()["n_occ"]
+    per_step = attempts_of(spec, n_occ)
+    l2buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def one_step():
+        lat.set_schedule(sched["T"], sched["h"], sched["eq"], sched["meas"], J=spec["J"])
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lat.run(-1, stream=stream)
+        b.record(stream)
+        return a, b
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(dev) if rank == 0 else None
+    times = []
+    for _ in range(args.steps):
+        flush_l2(l2buf)
+        a, b = one_step()
+        b.synchronize()
+        times.append(a.elapsed_time(b) / 1e3)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    total = sum(times)
+    if ws > 1:
+        t = torch.tensor([total], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+        torch.distributed.barrier()
+    recs = lat.observables()
+    lat.close()
+    value = per_step * args.steps * ws / total
+
+    # end to end through the public API with host buffers: create from the host height map,
+    # upload the schedule, run, read the observables back, every step
+    e2e_times = []
+    h2d = int(spec["heights"].nbytes) + int(sched["T"].nbytes + sched["h"].nbytes + sched["eq"].nbytes
+                                             + sched["meas"].nbytes) + len(sched["T"]) * 52 * 4
+    d2h = len(sched["T"]) * 96 + 4          # exact per-step records + the kernel status word
+    heights_pinned = torch.from_numpy(spec["heights"]).pin_memory().numpy()
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L2 = I.Lattice(heights_pinned, spec["layers"], periodic_x=spec["periodic_x"],
+                       periodic_y=spec["periodic_y"], packed=spec["packed"], seed=seed, init=spec["init"],
+                       stream=stream)
+        L2.set_schedule(sched["T"], sched["h"], sched["eq"], sched["meas"], J=spec["J"])
+        L2.run(-1, stream=stream)
+        out = L2.observables()
+        t1 = time.perf_counter()
+        L2.close()
+        assert len(out) == len(sched["T"])
+        if i > 0:                      # first one warms the path
+            e2e_times.append(t1 - t0)
+    e2e_value = per_step * ws / statistics.mean(e2e_times)
+
+    ms = total / args.steps * 1e3
+    achieved_tops = OPS_PER_ATTEMPT * per_step / (total / args.steps) / 1e12
+    traffic = load_traffic(args.workload)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int8" if not spec["packed"] else "u32 (1 bit/spin)",
+        "data": "synthetic (seeded fractal height map stands in for the STM image)",
+        "config": {"workload": spec["name"], "rows": int(spec["heights"].shape[0]),
+                   "cols": int(spec["heights"].shape[1]), "layers": spec["layers"], "occupied_sites": n_occ,
+                   "schedule_steps": int(len(sched["T"])), "sweeps_per_step_of_bench": int(sched["eq"].sum() + sched["meas"].sum()),
+                   "attempts_per_step": per_step, "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+                   "final_abs_m_at_lowest_T": recs[0]["abs_m"] if recs else None},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "what": "isf_lattice_create from host heights + isf_set_schedule + isf_run_sweeps + isf_read_observables"},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                     "frac": achieved_tops / ALU_PEAK_TOPS, "traffic": traffic,
+                     "kernel": "k_sweep (persistent colour-pass kernel)",
+                     "peak_from": "152 SMs x 128 int32 lanes x 2070 MHz (issue-rate ceiling)",
+                     "ops_per_attempt": OPS_PER_ATTEMPT},
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(spec, budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def load_traffic(workload_name):
+    """Per-launch DRAM bytes of k_sweep from the committed ncu summary, when one exists for the
+    current kernel (profiles/k_sweep_<workload>.json)."""
+    p = os.path.join(ROOT, "profiles", f"k_sweep_{workload_name}.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        return d.get("traffic_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def cpu_baseline(spec, budget_s=15.0, max_sweeps=None):
+    """The oracle as it stands, single-threaded, on a bounded sample of the same film: sweeps of
+    the first schedule step until the time budget is used."""
+    from oracle import oracle
+    init = {"random": oracle.INIT_RANDOM, "up": oracle.INIT_UP, "down": oracle.INIT_DOWN}[spec["init"]]
+    flags = (1 if spec["periodic_x"] else 0) | (2 if spec["periodic_y"] else 0)
+    f = oracle.Film(spec["heights"], spec["layers"], flags=flags, seed=spec["seed"], init=init)
+    n_occ = f.info()["n_occ"]
+    s = spec["schedule"]
+    T0, h0 = float(s["T"][0]), float(s["h"][0])
+    done = 0
+    chunk = 1
+    t0 = time.perf_counter()
+    while True:
+        f.run([T0], [h0], [0], [chunk])
+        done += chunk
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_sweeps and done >= max_sweeps):
+            break
+        chunk = max(1, min(chunk * 2, int(done * (budget_s - el) / max(el, 1e-6)) or 1))
+    el = time.perf_counter() - t0
+    f.close()
+    return {"value": n_occ * done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} sweeps of the first schedule step (T={T0}, h={h0}) on the full {spec['name']} film, "
+                      f"{n_occ} occupied sites, {el:.1f} s single-threaded"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    spec = workload(args.workload)
+    from oracle import oracle
+    oracle.load()
+    init = {"random": oracle.INIT_RANDOM, "up": oracle.INIT_UP, "down": oracle.INIT_DOWN}[spec["init"]]
+    flags = (1 if spec["periodic_x"] else 0) | (2 if spec["periodic_y"] else 0)
+    f = oracle.Film(spec["heights"], spec["layers"], flags=flags, seed=spec["seed"], init=init)
+    n_occ = f.info()["n_occ"]
+    s = spec["schedule"]
+    sweeps = args.ref_sweeps or max(1, int(2.0e7 // max(n_occ, 1)))    # ~ a few seconds per step
+    for _ in range(args.warmup):
+        f.run([float(s["T"][0])], [float(s["h"][0])], [0], [1])
+    times = []
+    for k in range(args.steps):
+        kk = k % len(s["T"])
+        t0 = time.perf_counter()
+        f.run([float(s["T"][kk])], [float(s["h"][kk])], [0], [sweeps])
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n_occ * sweeps * args.steps / total
+    sample = (f"{sweeps} sweeps per step at the workload's schedule temperatures/fields, full {spec['name']} "
+              f"film ({n_occ} occupied sites), single-threaded CPU oracle")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": {"workload": spec["name"], "occupied_sites": n_occ, "sweeps_per_step": sweeps},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    f.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--workload", default="fractal256", choices=["fractal256", "flat16", "fractal2048"])
+    ap.add_argument("--ctas", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sweeps", type=int, default=0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "cuda":
+        print("note: warm-up raised to 3 steps", file=sys.stderr)
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_impl(args)
+
+
+if __name__ == "__main__":
+    main()

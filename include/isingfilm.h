@@ -1,0 +1,175 @@
+/*
+ * isingfilm.h — C ABI of the GB300 (sm_103a) Metropolis engine for Ising nanofilms.
+ *
+ * The method (Kapitan & Nefedev, "High Performance Calculation of Magnetic Properties and
+ * Simulation of Nonequilibrium Phenomena in nanofilms"):
+ *   - Sec. 2 and Sec. 3: a 3-D spin array of rows (image height) x columns (image width) x
+ *     layers (number of Co layers), sites occupied where the height image reaches the layer,
+ *     each spin with up to z = 12 nearest neighbours;
+ *   - Eq. 3: H = -J sum_bonds S S' - h sum S, S = +-1, k = 1;
+ *   - Eq. 8 and items 1-3 of Sec. 5: Metropolis single-spin flips, p = 1 if dE <= 0 else
+ *     exp(-dE/T), accepted when p exceeds a uniform random number in (0,1);
+ *   - Eq. 9 and items 4-5 of Sec. 5: optional switching-field gate with probability
+ *     exp(-|h_s|/T), drawn before the Metropolis step;
+ *   - Sec. 3, Fig. 1: "checkerboard" updates of one part of the spins while the rest is fixed;
+ *     here four conflict-free colours c = ((x+z)&1) | (((y+z)&1)<<1), order 0,1,2,3;
+ *   - Sec. 3 and Fig. 3/Fig. 5: temperature scans and field hysteresis loops, state carried
+ *     from one temperature or field step to the next.
+ *
+ * Lattice (the paper fixes only z = 12): FCC in primitive coordinates; a site (x, y, z) has
+ * the neighbours (+-1,0,0), (0,+-1,0), +-(1,-1,0) in its layer, (0,0,1), (0,-1,1), (-1,0,1)
+ * above and (0,0,-1), (0,1,-1), (1,0,-1) below.  Site (x, y, z) is occupied iff
+ * z < heights[y*cols + x].
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit seed, counter
+ * (q, sweep_lo, sweep_hi, stream), q = ((c*layers + z)*ceil(rows/2) + (y>>1))*ceil(ceil(cols/2)/4)
+ * + ((x>>1)>>2), word (x>>1)&3; stream 0 = Metropolis, 1 = switching gate, 2 = initial spins
+ * (sweep 0).  A site flips iff thr == 0xFFFFFFFF or u < thr, thr = ceil(p*2^32 - 0.5)
+ * clamped (the random number of Eq. 8 is r = (u + 0.5)*2^-32).  Trajectories are therefore a
+ * pure function of (heights, layers, flags, seed, init, schedule): the same on every launch
+ * configuration, spin layout and batch mix.
+ *
+ * Conventions.  Every function returns an isf_status (0 = ISF_OK) and, on failure, sets a
+ * thread-local message readable with isf_last_error().  Host arrays passed in are copied;
+ * the caller keeps them.  Device memory belongs to the library unless the *_in variant is
+ * given a caller-owned buffer, which must then outlive the lattice.  isf_run_sweeps is
+ * asynchronous on the given CUDA stream (a cudaStream_t, e.g. torch.cuda.Stream.cuda_stream;
+ * NULL = legacy default stream); the read functions synchronise.  Kernels report problems
+ * through a device status word; nothing traps.
+ */
+#ifndef ISINGFILM_H
+#define ISINGFILM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct isf_lattice isf_lattice;
+
+typedef enum {
+    ISF_OK = 0,
+    ISF_ERR_ARG = -1,        /* bad argument (size, pointer, value range) */
+    ISF_ERR_OOM = -2,        /* device or host allocation failed, or caller buffer too small */
+    ISF_ERR_CUDA = -3,       /* a CUDA runtime call failed (message has the CUDA error) */
+    ISF_ERR_COLOURING = -4,  /* periodic extent odd or < 4: the 4-colouring would not be conflict-free */
+    ISF_ERR_SCHEDULE = -5,   /* bad schedule, or running past its end */
+    ISF_ERR_TIMEOUT = -6,    /* a bounded device wait expired; the kernel returned early */
+    ISF_ERR_STATE = -7       /* call not valid in the current state (e.g. no schedule set) */
+} isf_status;
+
+enum {
+    ISF_PERIODIC_X = 1,      /* wrap x (columns); needs cols even and >= 4 */
+    ISF_PERIODIC_Y = 2,      /* wrap y (rows);    needs rows even and >= 4 */
+    ISF_PERIODIC_Z = 4,      /* wrap z (layers);  needs layers even and >= 4 (bulk tests) */
+    ISF_PACKED = 8           /* one bit per spin (32 spins per uint32) + occupancy bit-plane;
+                                open boundaries only */
+};
+
+enum { ISF_INIT_RANDOM = 0, ISF_INIT_UP = 1, ISF_INIT_DOWN = 2 };
+
+/* Per-step record.  The integer fields are exact sums over the step's measured sweeps (the
+ * last sweeps_meas sweeps of the step), taken after each sweep; the doubles are derived from
+ * them on the host (N = number of occupied sites, E = -J*B - h*M per Eq. 3):
+ *   m = <M>/N, abs_m = <|M|>/N, e = <E>/N, chi = (<M^2> - <M>^2)/(N T),
+ *   chi_abs = (<M^2> - <|M|>^2)/(N T), C = (<E^2> - <E>^2)/(N T^2).
+ * B is the bond sum sum_bonds S S' (each bond once).  128-bit sums are two little-endian
+ * uint64 words; sumMB is two's complement.  Derived values are NaN when n_meas = 0. */
+typedef struct {
+    double T, h;
+    int64_t M_last, B_last, n_meas;
+    int64_t sumM, sumAbsM;
+    uint64_t sumM2[2], sumB2[2], sumMB[2];
+    int64_t sumB;
+    double m, abs_m, e, chi, chi_abs, C;
+} isf_step_obs;
+
+/* Device bytes a lattice of this shape needs (spins, heights, state).  0 if invalid. */
+size_t isf_lattice_bytes(int32_t rows, int32_t cols, int32_t layers, uint32_t flags);
+
+/* Build a film on the current CUDA device from a host height map.
+ *   heights: host, rows*cols bytes, row-major [y][x], each value in 0..layers (Sec. 3).
+ *   flags:   ISF_PERIODIC_* | ISF_PACKED.   seed: Philox key.   init: ISF_INIT_*.
+ *   cuda_stream: stream for the set-up kernels (the call returns once they are done).
+ * Errors: ISF_ERR_ARG (sizes, heights > layers, packed with periodic axes, null pointers),
+ * ISF_ERR_COLOURING, ISF_ERR_OOM, ISF_ERR_CUDA. */
+int isf_lattice_create(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers,
+                       uint32_t flags, uint64_t seed, int32_t init, void* cuda_stream,
+                       isf_lattice** out);
+
+/* As isf_lattice_create, but the film lives in a caller-owned device buffer of dev_bytes
+ * (>= isf_lattice_bytes, 256-byte aligned), e.g. a torch tensor.  ISF_ERR_OOM if too small. */
+int isf_lattice_create_in(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers,
+                          uint32_t flags, uint64_t seed, int32_t init, void* cuda_stream,
+                          void* dev_buf, size_t dev_bytes, isf_lattice** out);
+
+/* Set the temperature / field schedule (Sec. 3: one "step of temperature or field" after
+ * another).  Step k: temperature T[k] >= 0 (T = +inf allowed), field h[k] (finite),
+ * sweeps_eq[k] discarded then sweeps_meas[k] measured sweeps, eq + meas >= 1.  J: exchange
+ * (Eq. 3).  h_s: switching field of Eq. 9 (0 disables the gate).  Host arrays of nsteps
+ * entries, copied.  Resets the schedule cursor and records; the spins and the sweep counter
+ * carry on.  The threshold tables are built here on the host in fp64 (std::exp).
+ * Errors: ISF_ERR_ARG, ISF_ERR_SCHEDULE, ISF_ERR_OOM, ISF_ERR_CUDA. */
+int isf_set_schedule(isf_lattice* lat, int32_t nsteps, const double* T, const double* h,
+                     const int32_t* sweeps_eq, const int32_t* sweeps_meas, double J, double h_s);
+
+/* Enqueue nsweeps Metropolis sweeps (each: colours 0..3, every occupied site once) on
+ * cuda_stream; nsweeps = -1 runs to the end of the schedule.  Asynchronous.
+ * Errors: ISF_ERR_STATE (no schedule), ISF_ERR_SCHEDULE (past the end), ISF_ERR_CUDA,
+ * ISF_ERR_TIMEOUT (reported by a previous launch's status word). */
+int isf_run_sweeps(isf_lattice* lat, int64_t nsweeps, void* cuda_stream);
+
+/* Copy the records of the completed schedule steps (at most max) to out; *n_out = count.
+ * Synchronises with the lattice's last stream.  Errors: ISF_ERR_ARG, ISF_ERR_CUDA,
+ * ISF_ERR_TIMEOUT. */
+int isf_read_observables(isf_lattice* lat, isf_step_obs* out, int32_t max, int32_t* n_out);
+
+/* Spins to host_out (layers*rows*cols int8, [z][y][x], +1 / -1, 0 on vacancies).  Syncs. */
+int isf_read_spins(isf_lattice* lat, int8_t* host_out);
+
+/* Replace the spins (same layout; must be +-1 exactly on occupied sites, 0 elsewhere) and
+ * set the film-local sweep counter (the next sweep draws sweep + 1), e.g. to resume from a
+ * state.  Recomputes M and B.  Synchronous.  Errors: ISF_ERR_ARG, ISF_ERR_CUDA. */
+int isf_write_spins(isf_lattice* lat, const int8_t* host_in, int64_t sweep);
+
+/* Occupied sites, occupied bonds, mean coordination zbar = 2*bonds/sites (Sec. 4, Table 1),
+ * sweeps done.  Any pointer may be NULL.  No device work. */
+int isf_lattice_info(isf_lattice* lat, int64_t* n_occ, int64_t* n_bonds, double* zbar,
+                     int64_t* sweep);
+
+/* Current magnetisation sum M and bond sum B from the incremental bookkeeping (synchronises),
+ * and, if recompute != 0, recomputed from the spins on the device for comparison. */
+int isf_read_state(isf_lattice* lat, int64_t* M, int64_t* B, int32_t recompute,
+                   int64_t* M_full, int64_t* B_full);
+
+/* Keep M and B after every sweep for the next max_sweeps sweeps (0 = off); read them with
+ * isf_read_trace as (M, B) int64 pairs in sweep order. */
+int isf_enable_trace(isf_lattice* lat, int64_t max_sweeps);
+int isf_read_trace(isf_lattice* lat, int64_t* host_out, int64_t max_pairs, int64_t* n_out);
+
+/* Launch shape override for the sweep kernel: ctas (0 = automatic) and threads per CTA
+ * (0 = automatic; else a multiple of 32 in 64..1024).  Trajectories do not depend on it. */
+int isf_set_launch(isf_lattice* lat, int32_t ctas, int32_t threads);
+
+/* Save the film (shape, flags, seed, spins, sweep counter) to a file; load it back onto the
+ * current device (schedule not saved).  Errors: ISF_ERR_ARG, ISF_ERR_CUDA, ISF_ERR_OOM. */
+int isf_save(isf_lattice* lat, const char* path);
+int isf_load(const char* path, void* cuda_stream, isf_lattice** out);
+
+void isf_lattice_destroy(isf_lattice* lat);
+
+/* Message of the last failure on this thread ("" if none); valid until the next call. */
+const char* isf_last_error(void);
+
+/* Device Philox4x32-10 blocks for checking the generator: for b in [0, nblocks), the block
+ * with key (seed_lo, seed_hi) and counter (q0 + b, sweep_lo, sweep_hi, stream) goes to
+ * host_out[4b .. 4b+3].  Synchronous. */
+int isf_philox_blocks(uint64_t seed, uint32_t stream, uint64_t sweep, uint32_t q0,
+                      int64_t nblocks, uint32_t* host_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

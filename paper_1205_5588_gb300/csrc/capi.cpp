@@ -1,0 +1,506 @@
+// capi.cpp — the C ABI (include/isingfilm.h): film lifetime, schedule, sweeps, read-out.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "isf_internal.h"
+#include "../../include/isingfilm.h"
+
+using namespace isf;
+
+struct isf_lattice {
+    Layout lay{};
+    uint64_t seed = 0;
+    int32_t init = 0;
+    int device = 0;
+    uint8_t* dev = nullptr;         // film buffer: spins | heights | state
+    bool owns_dev = false;
+    DevFilm f{};
+    FilmState* st = nullptr;
+    std::vector<uint8_t> heights;   // host copy (validation of written spins, save)
+    int64_t n_occ = 0, n_bonds = 0;
+    int64_t sweep = 0;              // Metropolis sweeps done
+    // schedule
+    int32_t nsteps = 0;
+    std::vector<double> T, h;
+    std::vector<int32_t> eq, tot;
+    double J = 1.0, h_s = 0.0;
+    bool use_gate = false;
+    uint8_t* sched = nullptr;       // tables | eq | tot | records
+    uint32_t* d_tables = nullptr;
+    int32_t* d_eq = nullptr;
+    int32_t* d_tot = nullptr;
+    StepRec* d_recs = nullptr;
+    int32_t k = 0, pos = 0;         // cursor: step, sweeps done in it
+    // trace
+    long long* d_trace = nullptr;
+    int64_t trace_cap = 0, trace_n = 0;
+    // launch shape
+    int32_t ctas = 0, threads = 0;
+    cudaStream_t last = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(ISF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+#define CUDA_TRY(expr, what)                         \
+    do {                                             \
+        cudaError_t e_ = (cudaError_t)(expr);        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+void free_schedule(isf_lattice* L) {
+    if (L->sched) cudaFree(L->sched);
+    L->sched = nullptr;
+    L->d_tables = nullptr; L->d_eq = nullptr; L->d_tot = nullptr; L->d_recs = nullptr;
+    L->nsteps = 0;
+    L->T.clear(); L->h.clear(); L->eq.clear(); L->tot.clear();
+    L->k = 0; L->pos = 0;
+}
+
+// Sync with the last stream this film ran on and surface any status word a kernel set.
+int sync_film(isf_lattice* L) {
+    CUDA_TRY(cudaSetDevice(L->device), "cudaSetDevice");
+    CUDA_TRY(L->last ? cudaStreamSynchronize(L->last) : cudaDeviceSynchronize(), "synchronise");
+    int err = 0, where = 0;
+    CUDA_TRY(cudaMemcpy(&err, &L->st->error, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+    if (err) {
+        CUDA_TRY(cudaMemcpy(&where, &L->st->error_where, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+        return fail(err, "a sweep kernel stopped: bounded wait expired (barrier " + std::to_string(where) + ")");
+    }
+    return ISF_OK;
+}
+
+int recompute(isf_lattice* L, cudaStream_t s, long long red[4]) {
+    int e = launch_recompute(L->f, L->st, s);
+    if (e) return cuda_fail((cudaError_t)e, "recompute kernel");
+    CUDA_TRY(cudaMemcpyAsync(red, L->st->red, 4 * sizeof(long long), cudaMemcpyDeviceToHost, s), "read recompute");
+    CUDA_TRY(cudaStreamSynchronize(s), "recompute sync");
+    return ISF_OK;
+}
+
+int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, uint32_t flags,
+                  uint64_t seed, int32_t init, void* cuda_stream, void* dev_buf, size_t dev_bytes,
+                  isf_lattice** out) {
+    if (!out) return fail(ISF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!heights) return fail(ISF_ERR_ARG, "heights is NULL");
+    if (init < ISF_INIT_RANDOM || init > ISF_INIT_DOWN) return fail(ISF_ERR_ARG, "init must be ISF_INIT_*");
+    Layout lay;
+    const char* why = "";
+    int rc = make_layout(rows, cols, layers, flags, &lay, &why);
+    if (rc) return fail(rc, why);
+    rc = check_colouring(lay, &why);
+    if (rc) return fail(rc, why);
+    const size_t n_px = (size_t)rows * (size_t)cols;
+    for (size_t p = 0; p < n_px; ++p)
+        if (heights[p] > layers) return fail(ISF_ERR_ARG, "a height exceeds the number of layers");
+
+    isf_lattice* L = new (std::nothrow) isf_lattice();
+    if (!L) return fail(ISF_ERR_OOM, "host allocation failed");
+    L->lay = lay;
+    L->seed = seed;
+    L->init = init;
+    L->heights.assign(heights, heights + n_px);
+    cudaError_t e = cudaGetDevice(&L->device);
+    if (e != cudaSuccess) { delete L; return cuda_fail(e, "cudaGetDevice"); }
+    if (dev_buf) {
+        if (dev_bytes < lay.total_bytes) { delete L; return fail(ISF_ERR_OOM, "caller buffer smaller than isf_lattice_bytes"); }
+        if (reinterpret_cast<uintptr_t>(dev_buf) % 256) { delete L; return fail(ISF_ERR_ARG, "caller buffer must be 256-byte aligned"); }
+        L->dev = static_cast<uint8_t*>(dev_buf);
+    } else {
+        e = cudaMalloc(&L->dev, lay.total_bytes);
+        if (e != cudaSuccess) { delete L; cudaGetLastError(); return fail(ISF_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+        L->owns_dev = true;
+    }
+    DevFilm& f = L->f;
+    f.R = rows; f.C = cols; f.L = layers;
+    f.Rh = lay.Rh; f.Ch = lay.Ch; f.Qw = lay.Qw;
+    f.flags = flags; f.packed = lay.packed ? 1 : 0;
+    f.key0 = (uint32_t)seed; f.key1 = (uint32_t)(seed >> 32);
+    f.P = lay.P; f.ls8 = lay.ls8; f.cs8 = lay.cs8; f.nck = (int32_t)lay.nck;
+    f.Wp = lay.Wp; f.lsw = lay.lsw; f.csw = lay.csw; f.nw = (int32_t)lay.nw;
+    if (lay.packed) {
+        f.sp = reinterpret_cast<uint32_t*>(L->dev);
+        f.op = f.sp + 4 * lay.csw;
+    } else {
+        f.s8 = L->dev;
+    }
+    f.heights = L->dev + lay.heights_off;
+    fill_neighbour_classes(lay, &f);
+    L->st = reinterpret_cast<FilmState*>(L->dev + lay.state_off);
+
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    auto bail = [&](int code) { isf_lattice_destroy(L); return code; };
+    e = cudaMemsetAsync(L->st, 0, sizeof(FilmState), s);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "memset state"));
+    e = cudaMemcpyAsync(L->dev + lay.heights_off, heights, n_px, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "copy heights"));
+    int ke = launch_init(f, init, s);
+    if (ke) return bail(cuda_fail((cudaError_t)ke, "init kernel"));
+    long long red[4];
+    rc = recompute(L, s, red);
+    if (rc) return bail(rc);
+    L->n_occ = red[2];
+    L->n_bonds = red[3] / 2;
+    long long mb[2] = {red[0], red[1] / 2};
+    e = cudaMemcpyAsync(&L->st->M, mb, sizeof(mb), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "write state"));
+    L->last = s;
+    *out = L;
+    g_err.clear();
+    return ISF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* isf_last_error(void) { return g_err.c_str(); }
+
+size_t isf_lattice_bytes(int32_t rows, int32_t cols, int32_t layers, uint32_t flags) {
+    Layout lay;
+    const char* why = "";
+    if (make_layout(rows, cols, layers, flags, &lay, &why)) return 0;
+    return lay.total_bytes;
+}
+
+int isf_lattice_create(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, uint32_t flags,
+                       uint64_t seed, int32_t init, void* cuda_stream, isf_lattice** out) {
+    return create_common(heights, rows, cols, layers, flags, seed, init, cuda_stream, nullptr, 0, out);
+}
+
+int isf_lattice_create_in(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, uint32_t flags,
+                          uint64_t seed, int32_t init, void* cuda_stream, void* dev_buf, size_t dev_bytes,
+                          isf_lattice** out) {
+    if (!dev_buf) return fail(ISF_ERR_ARG, "dev_buf is NULL");
+    return create_common(heights, rows, cols, layers, flags, seed, init, cuda_stream, dev_buf, dev_bytes, out);
+}
+
+void isf_lattice_destroy(isf_lattice* L) {
+    if (!L) return;
+    cudaSetDevice(L->device);
+    if (L->last) cudaStreamSynchronize(L->last);
+    else cudaDeviceSynchronize();
+    free_schedule(L);
+    if (L->d_trace) cudaFree(L->d_trace);
+    if (L->owns_dev && L->dev) cudaFree(L->dev);
+    delete L;
+}
+
+int isf_set_schedule(isf_lattice* L, int32_t nsteps, const double* T, const double* h,
+                     const int32_t* sweeps_eq, const int32_t* sweeps_meas, double J, double h_s) {
+    if (!L) return fail(ISF_ERR_ARG, "lattice is NULL");
+    if (nsteps < 1) return fail(ISF_ERR_ARG, "nsteps must be >= 1");
+    if (!T || !h || !sweeps_eq || !sweeps_meas) return fail(ISF_ERR_ARG, "schedule array is NULL");
+    if (!std::isfinite(J) || !std::isfinite(h_s)) return fail(ISF_ERR_SCHEDULE, "J and h_s must be finite");
+    for (int32_t k = 0; k < nsteps; ++k) {
+        if (std::isnan(T[k]) || T[k] < 0.0) return fail(ISF_ERR_SCHEDULE, "T must be >= 0 (inf allowed)");
+        if (!std::isfinite(h[k])) return fail(ISF_ERR_SCHEDULE, "h must be finite");
+        if (sweeps_eq[k] < 0 || sweeps_meas[k] < 0) return fail(ISF_ERR_SCHEDULE, "sweep counts must be >= 0");
+        if ((int64_t)sweeps_eq[k] + sweeps_meas[k] < 1) return fail(ISF_ERR_SCHEDULE, "every step needs at least one sweep");
+        if ((int64_t)sweeps_eq[k] + sweeps_meas[k] > 0x7FFFFFFF) return fail(ISF_ERR_SCHEDULE, "too many sweeps in a step");
+    }
+    int rc = sync_film(L);
+    if (rc) return rc;
+    free_schedule(L);
+    const size_t tb = align256((size_t)nsteps * kTableStride * 4);
+    const size_t ib = align256((size_t)nsteps * 4);
+    const size_t rb = align256((size_t)nsteps * sizeof(StepRec));
+    cudaError_t e = cudaMalloc(&L->sched, tb + 2 * ib + rb);
+    if (e != cudaSuccess) { cudaGetLastError(); L->sched = nullptr; return fail(ISF_ERR_OOM, "cudaMalloc schedule"); }
+    L->d_tables = reinterpret_cast<uint32_t*>(L->sched);
+    L->d_eq = reinterpret_cast<int32_t*>(L->sched + tb);
+    L->d_tot = reinterpret_cast<int32_t*>(L->sched + tb + ib);
+    L->d_recs = reinterpret_cast<StepRec*>(L->sched + tb + 2 * ib);
+    std::vector<uint32_t> tables((size_t)nsteps * kTableStride);
+    L->use_gate = false;
+    for (int32_t k = 0; k < nsteps; ++k) {
+        build_step_table(T[k], h[k], J, h_s, &tables[(size_t)k * kTableStride]);
+        if (tables[(size_t)k * kTableStride + kGateSlot] != kAlways) L->use_gate = true;
+    }
+    L->T.assign(T, T + nsteps);
+    L->h.assign(h, h + nsteps);
+    L->eq.assign(sweeps_eq, sweeps_eq + nsteps);
+    L->tot.resize(nsteps);
+    for (int32_t k = 0; k < nsteps; ++k) L->tot[k] = sweeps_eq[k] + sweeps_meas[k];
+    L->J = J;
+    L->h_s = h_s;
+    CUDA_TRY(cudaMemcpy(L->d_tables, tables.data(), tables.size() * 4, cudaMemcpyHostToDevice), "upload tables");
+    CUDA_TRY(cudaMemcpy(L->d_eq, L->eq.data(), (size_t)nsteps * 4, cudaMemcpyHostToDevice), "upload schedule");
+    CUDA_TRY(cudaMemcpy(L->d_tot, L->tot.data(), (size_t)nsteps * 4, cudaMemcpyHostToDevice), "upload schedule");
+    CUDA_TRY(cudaMemset(L->d_recs, 0, (size_t)nsteps * sizeof(StepRec)), "clear records");
+    // fresh step sums (M, B and the sweep counter carry on)
+    CUDA_TRY(cudaMemset(&L->st->n_meas, 0, offsetof(FilmState, red) - offsetof(FilmState, n_meas)), "clear sums");
+    L->nsteps = nsteps;
+    L->k = 0;
+    L->pos = 0;
+    g_err.clear();
+    return ISF_OK;
+}
+
+int isf_run_sweeps(isf_lattice* L, int64_t nsweeps, void* cuda_stream) {
+    if (!L) return fail(ISF_ERR_ARG, "lattice is NULL");
+    if (!L->nsteps) return fail(ISF_ERR_STATE, "no schedule set");
+    int64_t remaining = 0;
+    for (int32_t k = L->k; k < L->nsteps; ++k) remaining += L->tot[k];
+    remaining -= L->pos;
+    if (nsweeps == -1) nsweeps = remaining;
+    if (nsweeps < 0) return fail(ISF_ERR_ARG, "nsweeps must be >= 0 or -1");
+    if (nsweeps > remaining) return fail(ISF_ERR_SCHEDULE, "past the end of the schedule");
+    if (nsweeps == 0) return ISF_OK;
+    CUDA_TRY(cudaSetDevice(L->device), "cudaSetDevice");
+    SweepArgs a{};
+    a.f = L->f;
+    a.st = L->st;
+    a.tables = L->d_tables;
+    a.step_eq = L->d_eq;
+    a.step_total = L->d_tot;
+    a.recs = L->d_recs;
+    a.trace = L->d_trace;
+    a.trace_begin = L->trace_n;
+    a.trace_cap = L->trace_cap;
+    a.sweep0 = L->sweep;
+    a.nsweeps = nsweeps;
+    a.k0 = L->k;
+    a.pos0 = L->pos;
+    a.nsteps = L->nsteps;
+    a.use_gate = L->use_gate ? 1 : 0;
+    int threads = L->threads ? L->threads : 256;
+    int maxc = 0;
+    int e = sweep_max_ctas_for(L->f, threads, &maxc);
+    if (e) return cuda_fail((cudaError_t)e, "occupancy query");
+    if (maxc < 1) return fail(ISF_ERR_CUDA, "sweep kernel cannot be resident with this block size");
+    int ctas = L->ctas;
+    if (ctas <= 0) {
+        const int64_t items = sweep_items_per_pass(L->f);
+        int64_t want = (items + threads - 1) / threads;   // about one work item per thread
+        ctas = (int)(want < 1 ? 1 : want);
+    }
+    if (ctas > maxc) ctas = maxc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    e = launch_sweeps(a, ctas, threads, s);
+    if (e) return cuda_fail((cudaError_t)e, "sweep kernel launch");
+    L->last = s;
+    L->sweep += nsweeps;
+    if (L->d_trace) L->trace_n = std::min<int64_t>(L->trace_cap, L->trace_n + nsweeps);
+    int64_t left = nsweeps;
+    while (left > 0) {
+        const int64_t room = L->tot[L->k] - L->pos;
+        if (left >= room) { left -= room; L->k += 1; L->pos = 0; }
+        else { L->pos += (int32_t)left; left = 0; }
+    }
+    return ISF_OK;
+}
+
+int isf_read_observables(isf_lattice* L, isf_step_obs* out, int32_t max, int32_t* n_out) {
+    if (!L || !n_out || (max > 0 && !out)) return fail(ISF_ERR_ARG, "bad arguments");
+    int rc = sync_film(L);
+    if (rc) return rc;
+    const int32_t n = std::min<int32_t>(L->k, std::max<int32_t>(max, 0));
+    std::vector<StepRec> recs(n);
+    if (n) CUDA_TRY(cudaMemcpy(recs.data(), L->d_recs, (size_t)n * sizeof(StepRec), cudaMemcpyDeviceToHost), "read records");
+    for (int32_t k = 0; k < n; ++k) {
+        const StepRec& r = recs[k];
+        isf_step_obs& o = out[k];
+        o.T = L->T[k]; o.h = L->h[k];
+        o.M_last = r.M_last; o.B_last = r.B_last; o.n_meas = r.n_meas;
+        o.sumM = r.sumM; o.sumAbsM = r.sumAbsM; o.sumB = r.sumB;
+        for (int w = 0; w < 2; ++w) { o.sumM2[w] = r.sumM2[w]; o.sumB2[w] = r.sumB2[w]; o.sumMB[w] = r.sumMB[w]; }
+        double d[6];
+        derive_record(r, L->T[k], L->h[k], L->J, L->n_occ, d);
+        o.m = d[0]; o.abs_m = d[1]; o.e = d[2]; o.chi = d[3]; o.chi_abs = d[4]; o.C = d[5];
+    }
+    *n_out = n;
+    g_err.clear();
+    return ISF_OK;
+}
+
+int isf_read_spins(isf_lattice* L, int8_t* host_out) {
+    if (!L || !host_out) return fail(ISF_ERR_ARG, "bad arguments");
+    int rc = sync_film(L);
+    if (rc) return rc;
+    const size_t n = (size_t)L->lay.R * L->lay.C * L->lay.L;
+    int8_t* d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, n), "cudaMalloc read buffer");
+    int e = launch_unpack(L->f, d, L->last);
+    cudaError_t ce = (cudaError_t)e;
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(host_out, d, n, cudaMemcpyDeviceToHost, L->last);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(L->last);
+    cudaFree(d);
+    if (ce != cudaSuccess) return cuda_fail(ce, "read spins");
+    return ISF_OK;
+}
+
+int isf_write_spins(isf_lattice* L, const int8_t* host_in, int64_t sweep) {
+    if (!L || !host_in || sweep < 0) return fail(ISF_ERR_ARG, "bad arguments");
+    const int R = L->lay.R, C = L->lay.C, Lz = L->lay.L;
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < R; ++y)
+            for (int x = 0; x < C; ++x) {
+                const int8_t v = host_in[((size_t)z * R + y) * C + x];
+                const bool occ = z < L->heights[(size_t)y * C + x];
+                if (occ ? (v != 1 && v != -1) : (v != 0)) return fail(ISF_ERR_ARG, "spins must be +-1 on occupied sites and 0 elsewhere");
+            }
+    int rc = sync_film(L);
+    if (rc) return rc;
+    const size_t n = (size_t)R * C * Lz;
+    int8_t* d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, n), "cudaMalloc write buffer");
+    cudaError_t ce = cudaMemcpyAsync(d, host_in, n, cudaMemcpyHostToDevice, L->last);
+    if (ce == cudaSuccess) ce = (cudaError_t)launch_pack(L->f, d, L->last);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(L->last);
+    cudaFree(d);
+    if (ce != cudaSuccess) return cuda_fail(ce, "write spins");
+    long long red[4];
+    rc = recompute(L, L->last, red);
+    if (rc) return rc;
+    long long mb[2] = {red[0], red[1] / 2};
+    CUDA_TRY(cudaMemcpy(&L->st->M, mb, sizeof(mb), cudaMemcpyHostToDevice), "write state");
+    L->sweep = sweep;
+    return ISF_OK;
+}
+
+int isf_lattice_info(isf_lattice* L, int64_t* n_occ, int64_t* n_bonds, double* zbar, int64_t* sweep) {
+    if (!L) return fail(ISF_ERR_ARG, "lattice is NULL");
+    if (n_occ) *n_occ = L->n_occ;
+    if (n_bonds) *n_bonds = L->n_bonds;
+    if (zbar) *zbar = L->n_occ ? 2.0 * (double)L->n_bonds / (double)L->n_occ : 0.0;
+    if (sweep) *sweep = L->sweep;
+    return ISF_OK;
+}
+
+int isf_read_state(isf_lattice* L, int64_t* M, int64_t* B, int32_t recompute_too, int64_t* M_full, int64_t* B_full) {
+    if (!L) return fail(ISF_ERR_ARG, "lattice is NULL");
+    int rc = sync_film(L);
+    if (rc) return rc;
+    long long mb[2];
+    CUDA_TRY(cudaMemcpy(mb, &L->st->M, sizeof(mb), cudaMemcpyDeviceToHost), "read state");
+    if (M) *M = mb[0];
+    if (B) *B = mb[1];
+    if (recompute_too) {
+        long long red[4];
+        rc = recompute(L, L->last, red);
+        if (rc) return rc;
+        if (M_full) *M_full = red[0];
+        if (B_full) *B_full = red[1] / 2;
+    }
+    return ISF_OK;
+}
+
+int isf_enable_trace(isf_lattice* L, int64_t max_sweeps) {
+    if (!L || max_sweeps < 0) return fail(ISF_ERR_ARG, "bad arguments");
+    int rc = sync_film(L);
+    if (rc) return rc;
+    if (L->d_trace) cudaFree(L->d_trace);
+    L->d_trace = nullptr;
+    L->trace_cap = 0;
+    L->trace_n = 0;
+    if (max_sweeps == 0) return ISF_OK;
+    cudaError_t e = cudaMalloc(&L->d_trace, (size_t)max_sweeps * 2 * sizeof(long long));
+    if (e != cudaSuccess) { cudaGetLastError(); L->d_trace = nullptr; return fail(ISF_ERR_OOM, "cudaMalloc trace"); }
+    L->trace_cap = max_sweeps;
+    return ISF_OK;
+}
+
+int isf_read_trace(isf_lattice* L, int64_t* host_out, int64_t max_pairs, int64_t* n_out) {
+    if (!L || !n_out || (max_pairs > 0 && !host_out)) return fail(ISF_ERR_ARG, "bad arguments");
+    int rc = sync_film(L);
+    if (rc) return rc;
+    const int64_t n = std::min<int64_t>(L->trace_n, std::max<int64_t>(max_pairs, 0));
+    if (n) CUDA_TRY(cudaMemcpy(host_out, L->d_trace, (size_t)n * 2 * sizeof(long long), cudaMemcpyDeviceToHost), "read trace");
+    *n_out = n;
+    return ISF_OK;
+}
+
+int isf_set_launch(isf_lattice* L, int32_t ctas, int32_t threads) {
+    if (!L || ctas < 0) return fail(ISF_ERR_ARG, "bad arguments");
+    if (threads != 0 && (threads % 32 || threads < 32 || threads > 256))
+        return fail(ISF_ERR_ARG, "threads must be 0 or a multiple of 32 in 32..256");
+    L->ctas = ctas;
+    L->threads = threads;
+    return ISF_OK;
+}
+
+int isf_save(isf_lattice* L, const char* path) {
+    if (!L || !path) return fail(ISF_ERR_ARG, "bad arguments");
+    const size_t n = (size_t)L->lay.R * L->lay.C * L->lay.L;
+    std::vector<int8_t> spins(n);
+    int rc = isf_read_spins(L, spins.data());
+    if (rc) return rc;
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(ISF_ERR_ARG, std::string("cannot open ") + path);
+    const char magic[8] = {'I', 'S', 'F', 'I', 'L', 'M', '0', '1'};
+    int32_t hdr[5] = {L->lay.R, L->lay.C, L->lay.L, (int32_t)L->lay.flags, L->init};
+    int64_t tail[2] = {(int64_t)L->seed, L->sweep};
+    bool ok = std::fwrite(magic, 1, 8, fp) == 8 && std::fwrite(hdr, 4, 5, fp) == 5 &&
+              std::fwrite(tail, 8, 2, fp) == 2 &&
+              std::fwrite(L->heights.data(), 1, L->heights.size(), fp) == L->heights.size() &&
+              std::fwrite(spins.data(), 1, n, fp) == n;
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) return fail(ISF_ERR_ARG, "write failed");
+    return ISF_OK;
+}
+
+int isf_load(const char* path, void* cuda_stream, isf_lattice** out) {
+    if (!path || !out) return fail(ISF_ERR_ARG, "bad arguments");
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(ISF_ERR_ARG, std::string("cannot open ") + path);
+    char magic[8];
+    int32_t hdr[5];
+    int64_t tail[2];
+    bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, "ISFILM01", 8) == 0 &&
+              std::fread(hdr, 4, 5, fp) == 5 && std::fread(tail, 8, 2, fp) == 2;
+    if (!ok || hdr[0] < 1 || hdr[1] < 1 || hdr[2] < 1 || hdr[0] > 65536 || hdr[1] > 65536 || hdr[2] > 255) {
+        std::fclose(fp);
+        return fail(ISF_ERR_ARG, "not a film file");
+    }
+    const size_t npx = (size_t)hdr[0] * hdr[1], n = npx * hdr[2];
+    std::vector<uint8_t> H(npx);
+    std::vector<int8_t> S(n);
+    ok = std::fread(H.data(), 1, npx, fp) == npx && std::fread(S.data(), 1, n, fp) == n;
+    std::fclose(fp);
+    if (!ok) return fail(ISF_ERR_ARG, "truncated film file");
+    isf_lattice* L = nullptr;
+    int rc = isf_lattice_create(H.data(), hdr[0], hdr[1], hdr[2], (uint32_t)hdr[3], (uint64_t)tail[0], hdr[4],
+                                cuda_stream, &L);
+    if (rc) return rc;
+    rc = isf_write_spins(L, S.data(), tail[1]);
+    if (rc) { isf_lattice_destroy(L); return rc; }
+    *out = L;
+    return ISF_OK;
+}
+
+int isf_philox_blocks(uint64_t seed, uint32_t stream, uint64_t sweep, uint32_t q0, int64_t nblocks,
+                      uint32_t* host_out) {
+    if (nblocks < 0 || (nblocks > 0 && !host_out)) return fail(ISF_ERR_ARG, "bad arguments");
+    if (nblocks == 0) return ISF_OK;
+    uint32_t* d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, (size_t)nblocks * 16), "cudaMalloc");
+    cudaError_t e = (cudaError_t)launch_philox_blocks(seed, stream, sweep, q0, nblocks, d, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(host_out, d, (size_t)nblocks * 16, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "philox blocks");
+    return ISF_OK;
+}
+
+}  // extern "C"

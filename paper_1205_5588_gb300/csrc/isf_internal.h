@@ -1,0 +1,134 @@
+// isf_internal.h — data layout and launch interfaces shared by the library's host and device
+// translation units.  Not part of the public ABI.
+//
+// Spin storage (one array set per colour c = ((x+z)&1) | (((y+z)&1)<<1), Sec. 3 "checkerboard"):
+// a site (x, y, z) of colour c lives at column i = x>>1, row j = y>>1, layer z of colour c's
+// array.  Its x parity is (c&1)^(z&1) and its y parity ((c>>1)&1)^(z&1), so inside one
+// (colour, layer parity) class every one of the 12 neighbours sits at a FIXED address offset
+// (one of three of them shifted by one column), which is what makes the colour pass a
+// stencil with constant offsets.
+//
+//  int8 layout  : per colour [L+2][Rh+2][P] bytes, halo layer/row on each side, 16 halo bytes
+//                 left of column 0; P = 16*(nck+2), nck = ceil(Ch/16).  Byte values:
+//                 0 = spin down, 1 = vacancy (also every halo/padding byte), 2 = spin up,
+//                 i.e. S + 1, so a plain 32-bit add of 12 neighbour words gives n + 12 per
+//                 byte (n = neighbour spin sum, no carries: at most 24).
+//  packed layout: per colour two bit-planes [L+2][Rh+2][Wp] uint32 (spin bit = 1 for up,
+//                 occupancy bit = 1 for occupied, both 0 on vacancies and halos); word w of a
+//                 row holds columns 32w..32w+31 and sits at index w+1; Wp = nw + 2.
+#pragma once
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __CUDACC__
+#define ISF_HD __host__ __device__
+#else
+#define ISF_HD
+#endif
+
+namespace isf {
+
+constexpr uint32_t kAlways = 0xFFFFFFFFu;
+constexpr int kTableStride = 52;    // per step: thr[n+12][s'] (50 words), gate threshold, pad
+constexpr int kGateSlot = 50;
+constexpr int kMaxThreads = 1024;
+
+// Neighbour offsets of one (colour, layer parity) class: 9 unshifted, then 3 shifted by `sgn`
+// columns (-1 or +1).  Units: bytes (int8) or words (packed).
+struct NbrClass {
+    int64_t off[12];
+    int32_t sgn;
+    int32_t pad_;
+};
+
+struct DevFilm {
+    // geometry
+    int32_t R, C, L;
+    int32_t Rh, Ch, Qw;
+    uint32_t flags;
+    int32_t packed;
+    uint32_t key0, key1;
+    // int8 layout
+    uint8_t* s8;
+    int64_t P, ls8, cs8;          // row pitch, layer stride, colour stride (bytes)
+    int32_t nck;                  // 16-site chunks per row
+    // packed layout
+    uint32_t* sp;                 // spin bit-planes
+    uint32_t* op;                 // occupancy bit-planes
+    int64_t Wp, lsw, csw;         // row pitch, layer stride, colour stride (words)
+    int32_t nw;                   // words per row
+    int32_t pad_;
+    const uint8_t* heights;       // [y][x]
+    NbrClass nb[4][2];            // [colour][layer parity]
+};
+
+// Running state of one film on the device (library scratch, 256-byte aligned).
+struct FilmState {
+    long long M, B;               // magnetisation sum, bond sum (after the last folded sweep)
+    long long acc[2][2];          // per-sweep deltas (dM, dB), double-buffered by sweep parity
+    unsigned int bar_count, bar_gen;
+    int error;                    // isf_status set by a kernel (0 = fine)
+    int error_where;
+    long long n_meas, sumM, sumAbsM, sumB;      // running sums of the current step
+    unsigned long long sumM2[2], sumB2[2], sumMB[2];
+    long long red[4];             // reduction scratch of the recompute kernel
+    long long pad_[6];
+};
+
+// Exact per-step record written by the device at the end of each step.
+struct StepRec {
+    long long M_last, B_last, n_meas, sumM, sumAbsM, sumB;
+    unsigned long long sumM2[2], sumB2[2], sumMB[2];
+};
+
+// Arguments of one sweep launch.
+struct SweepArgs {
+    DevFilm f;
+    FilmState* st;
+    const uint32_t* tables;       // [nsteps][kTableStride]
+    const int32_t* step_eq;       // [nsteps]
+    const int32_t* step_total;    // [nsteps] eq + meas
+    StepRec* recs;                // [nsteps]
+    long long* trace;             // optional (M, B) per sweep
+    long long trace_begin, trace_cap;  // trace index of the first sweep of this launch, capacity
+    long long sweep0;             // sweeps done before this launch; first RNG sweep = sweep0 + 1
+    long long nsweeps;
+    int32_t k0, pos0;             // schedule cursor at launch: step, sweeps done in that step
+    int32_t nsteps;
+    int32_t use_gate;             // any step with a gate threshold != always
+};
+
+// Host-side layout computation (lattice.cpp).
+struct Layout {
+    int32_t R, C, L, Rh, Ch, Qw;
+    uint32_t flags;
+    bool packed;
+    int64_t P, ls8, cs8, nck;
+    int64_t nw, Wp, lsw, csw;
+    size_t spin_bytes;            // int8 array, or both bit-plane sets
+    size_t heights_off, state_off, total_bytes;
+};
+
+int make_layout(int32_t rows, int32_t cols, int32_t layers, uint32_t flags, Layout* out,
+                const char** why);
+int check_colouring(const Layout& lay, const char** why);
+void fill_neighbour_classes(const Layout& lay, DevFilm* f);
+
+// Host threshold table (schedule.cpp): thr[n+12][s'] for one step, plus the gate slot.
+void build_step_table(double T, double h, double J, double h_s, uint32_t* out52);
+// FP64 derivation from exact sums (schedule.cpp).
+void derive_record(const StepRec& r, double T, double h, double J, long long n_occ,
+                   double out[6]);
+
+// Device launchers (kernels.cu); all return a cudaError_t as int.
+int launch_init(const DevFilm& f, int init, void* stream);
+int launch_recompute(const DevFilm& f, FilmState* st, void* stream);  // M, B, n_occ, bonds -> st->red
+int launch_sweeps(const SweepArgs& a, int ctas, int threads, void* stream);
+int launch_unpack(const DevFilm& f, int8_t* dev_out, void* stream);
+int launch_pack(const DevFilm& f, const int8_t* dev_in, void* stream);
+int launch_philox_blocks(uint64_t seed, uint32_t stream_id, uint64_t sweep, uint32_t q0,
+                         int64_t nblocks, uint32_t* dev_out, void* stream);
+int sweep_max_ctas_for(const DevFilm& f, int threads, int* max_ctas);  // co-resident CTAs
+int sweep_items_per_pass(const DevFilm& f);                            // work items per colour pass
+
+}  // namespace isf

@@ -1,0 +1,213 @@
+// kernels_aux.cu — set-up and read-out kernels: initial spins (Philox stream 2, or all up /
+// all down) with the occupancy of the height map (Sec. 3), full recomputation of M and B
+// (Eq. 3) and of the occupied site and bond counts, unpack to / pack from [z][y][x] int8, and
+// raw Philox blocks for checking the generator.
+#include <cuda_runtime.h>
+
+#include "../../include/isingfilm.h"
+#include "device_common.cuh"
+
+namespace isf {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t n) {
+    int64_t g = (n + kThreads - 1) / kThreads;
+    if (g > 152 * 64) g = 152 * 64;
+    return g < 1 ? 1 : (int)g;
+}
+
+// One thread per 4-byte word of the int8 arrays, halo included: 4 sites = one Philox block.
+__global__ void k_init_int8(DevFilm f, int init, const int8_t* src) {
+    const int64_t wpr = f.P / 4;
+    const int64_t total = (int64_t)4 * (f.L + 2) * (f.Rh + 2) * wpr;
+    uint32_t* out = reinterpret_cast<uint32_t*>(f.s8);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = t / wpr;
+        const int wd = (int)(t - row * wpr);
+        const int jj = (int)(row % (f.Rh + 2));
+        const int64_t r2 = row / (f.Rh + 2);
+        const int zz = (int)(r2 % (f.L + 2));
+        const int c = (int)(r2 / (f.L + 2));
+        const int z = zz - 1, j = jj - 1, i0 = wd * 4 - 16;
+        uint32_t word = 0x01010101u;   // vacancy in every byte
+        if (z >= 0 && z < f.L && j >= 0 && j < f.Rh && i0 >= 0 && i0 < f.Ch) {
+            const int zp = z & 1, px = (c & 1) ^ zp, py = ((c >> 1) & 1) ^ zp;
+            const int y = 2 * j + py;
+            uint4 rnd = make_uint4(0, 0, 0, 0);
+            bool have = false;
+            for (int b = 0; b < 4; ++b) {
+                const int i = i0 + b, x = 2 * i + px;
+                if (i >= f.Ch || x >= f.C || y >= f.R || !site_occupied(f, x, y, z)) continue;
+                int s;
+                if (src) {
+                    s = src[((int64_t)z * f.R + y) * f.C + x];
+                } else if (init == ISF_INIT_RANDOM) {
+                    if (!have) {
+                        rnd = philox10(make_uint4(block_counter(f, c, z, j, i0), 0u, 0u, 2u), f.key0, f.key1);
+                        have = true;
+                    }
+                    s = (word_of(rnd, b) >> 31) ? -1 : 1;
+                } else {
+                    s = init == ISF_INIT_UP ? 1 : -1;
+                }
+                word = (word & ~(0xFFu << (8 * b))) | ((uint32_t)(s + 1) << (8 * b));
+            }
+        }
+        out[t] = word;
+    }
+}
+
+// One thread per word of the packed bit-planes, halo included: 32 sites = 8 Philox blocks.
+__global__ void k_init_packed(DevFilm f, int init, const int8_t* src) {
+    const int64_t total = (int64_t)4 * (f.L + 2) * (f.Rh + 2) * f.Wp;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = t / f.Wp;
+        const int wd = (int)(t - row * f.Wp);
+        const int jj = (int)(row % (f.Rh + 2));
+        const int64_t r2 = row / (f.Rh + 2);
+        const int zz = (int)(r2 % (f.L + 2));
+        const int c = (int)(r2 / (f.L + 2));
+        const int z = zz - 1, j = jj - 1, w = wd - 1;
+        uint32_t sbits = 0, obits = 0;
+        if (z >= 0 && z < f.L && j >= 0 && j < f.Rh && w >= 0 && w < f.nw) {
+            const int zp = z & 1, px = (c & 1) ^ zp, py = ((c >> 1) & 1) ^ zp;
+            const int y = 2 * j + py;
+            for (int v = 0; v < 8; ++v) {
+                uint4 rnd = make_uint4(0, 0, 0, 0);
+                bool have = false;
+                for (int b = 0; b < 4; ++b) {
+                    const int lane = 4 * v + b, i = 32 * w + lane, x = 2 * i + px;
+                    if (i >= f.Ch || x >= f.C || y >= f.R || !site_occupied(f, x, y, z)) continue;
+                    int s;
+                    if (src) {
+                        s = src[((int64_t)z * f.R + y) * f.C + x];
+                    } else if (init == ISF_INIT_RANDOM) {
+                        if (!have) {
+                            rnd = philox10(make_uint4(block_counter(f, c, z, j, 32 * w + 4 * v), 0u, 0u, 2u),
+                                           f.key0, f.key1);
+                            have = true;
+                        }
+                        s = (word_of(rnd, b) >> 31) ? -1 : 1;
+                    } else {
+                        s = init == ISF_INIT_UP ? 1 : -1;
+                    }
+                    obits |= 1u << lane;
+                    if (s > 0) sbits |= 1u << lane;
+                }
+            }
+        }
+        f.sp[t] = sbits;
+        f.op[t] = obits;
+    }
+}
+
+// M = sum S, 2B = sum S * (neighbour sum), occupied sites, 2 * occupied bonds -> st->red[0..3].
+__global__ void k_recompute(DevFilm f, FilmState* st) {
+    const int64_t total = (int64_t)f.L * f.R * f.C;
+    long long m = 0, b2 = 0, occ = 0, nb2 = 0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(t % f.C);
+        const int64_t r = t / f.C;
+        const int y = (int)(r % f.R), z = (int)(r / f.R);
+        if (!site_occupied(f, x, y, z)) continue;
+        const int s = site_spin(f, x, y, z);
+        int n = 0, no = 0;
+        for (int k = 0; k < 12; ++k) {
+            int a, b, c;
+            if (!neighbour_of(f, x, y, z, k, a, b, c)) continue;
+            if (!site_occupied(f, a, b, c)) continue;
+            n += site_spin(f, a, b, c);
+            ++no;
+        }
+        m += s;
+        b2 += (long long)s * n;
+        occ += 1;
+        nb2 += no;
+    }
+    m = warp_sum(m);
+    b2 = warp_sum(b2);
+    occ = warp_sum(occ);
+    nb2 = warp_sum(nb2);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&st->red[0]), (unsigned long long)m);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&st->red[1]), (unsigned long long)b2);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&st->red[2]), (unsigned long long)occ);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&st->red[3]), (unsigned long long)nb2);
+    }
+}
+
+__global__ void k_unpack(DevFilm f, int8_t* out) {
+    const int64_t total = (int64_t)f.L * f.R * f.C;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(t % f.C);
+        const int64_t r = t / f.C;
+        const int y = (int)(r % f.R), z = (int)(r / f.R);
+        out[t] = (int8_t)site_spin(f, x, y, z);
+    }
+}
+
+__global__ void k_philox_blocks(uint64_t seed, uint32_t stream_id, uint64_t sweep, uint32_t q0,
+                                int64_t n, uint4* out) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        out[b] = philox10(make_uint4(q0 + (uint32_t)b, (uint32_t)sweep, (uint32_t)(sweep >> 32), stream_id),
+                          (uint32_t)seed, (uint32_t)(seed >> 32));
+    }
+}
+
+}  // namespace
+
+int launch_init(const DevFilm& f, int init, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (f.packed) {
+        const int64_t total = (int64_t)4 * (f.L + 2) * (f.Rh + 2) * f.Wp;
+        k_init_packed<<<grid_for(total), kThreads, 0, s>>>(f, init, nullptr);
+    } else {
+        const int64_t total = (int64_t)4 * (f.L + 2) * (f.Rh + 2) * (f.P / 4);
+        k_init_int8<<<grid_for(total), kThreads, 0, s>>>(f, init, nullptr);
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_pack(const DevFilm& f, const int8_t* dev_in, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (f.packed) {
+        const int64_t total = (int64_t)4 * (f.L + 2) * (f.Rh + 2) * f.Wp;
+        k_init_packed<<<grid_for(total), kThreads, 0, s>>>(f, 0, dev_in);
+    } else {
+        const int64_t total = (int64_t)4 * (f.L + 2) * (f.Rh + 2) * (f.P / 4);
+        k_init_int8<<<grid_for(total), kThreads, 0, s>>>(f, 0, dev_in);
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_recompute(const DevFilm& f, FilmState* st, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(st->red, 0, sizeof(st->red), s);
+    if (e != cudaSuccess) return (int)e;
+    const int64_t total = (int64_t)f.L * f.R * f.C;
+    k_recompute<<<grid_for(total), kThreads, 0, s>>>(f, st);
+    return (int)cudaGetLastError();
+}
+
+int launch_unpack(const DevFilm& f, int8_t* dev_out, void* stream) {
+    const int64_t total = (int64_t)f.L * f.R * f.C;
+    k_unpack<<<grid_for(total), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(f, dev_out);
+    return (int)cudaGetLastError();
+}
+
+int launch_philox_blocks(uint64_t seed, uint32_t stream_id, uint64_t sweep, uint32_t q0,
+                         int64_t nblocks, uint32_t* dev_out, void* stream) {
+    k_philox_blocks<<<grid_for(nblocks), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+        seed, stream_id, sweep, q0, nblocks, reinterpret_cast<uint4*>(dev_out));
+    return (int)cudaGetLastError();
+}
+
+}  // namespace isf

@@ -1,0 +1,264 @@
+"""Thin Python binding of libisingfilm.so (include/isingfilm.h): argument marshalling only.
+
+Every step of the sweep runs in the library's CUDA kernels.  PyTorch supplies device memory
+(the film lives in a torch uint8 tensor handed to isf_lattice_create_in) and CUDA streams.
+Importing this module fails loudly if the library has not been built; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PERIODIC_X, PERIODIC_Y, PERIODIC_Z, PACKED = 1, 2, 4, 8
+INIT = {"random": 0, "up": 1, "down": 2}
+STATUS = {0: "ISF_OK", -1: "ISF_ERR_ARG", -2: "ISF_ERR_OOM", -3: "ISF_ERR_CUDA", -4: "ISF_ERR_COLOURING",
+          -5: "ISF_ERR_SCHEDULE", -6: "ISF_ERR_TIMEOUT", -7: "ISF_ERR_STATE"}
+
+
+class StepObs(C.Structure):
+    _fields_ = [
+        ("T", C.c_double), ("h", C.c_double),
+        ("M_last", C.c_int64), ("B_last", C.c_int64), ("n_meas", C.c_int64),
+        ("sumM", C.c_int64), ("sumAbsM", C.c_int64),
+        ("sumM2", C.c_uint64 * 2), ("sumB2", C.c_uint64 * 2), ("sumMB", C.c_uint64 * 2),
+        ("sumB", C.c_int64),
+        ("m", C.c_double), ("abs_m", C.c_double), ("e", C.c_double),
+        ("chi", C.c_double), ("chi_abs", C.c_double), ("C", C.c_double),
+    ]
+
+
+class IsfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _declare(lib):
+    vp, u8p, i8p, i64p, dp = C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_int8), C.POINTER(C.c_int64), C.POINTER(C.c_double)
+    i32p, u32p = C.POINTER(C.c_int32), C.POINTER(C.c_uint32)
+    sig = {
+        "isf_lattice_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_uint32]),
+        "isf_lattice_create": (C.c_int, [u8p, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, C.c_uint64, C.c_int32, vp,
+                                         C.POINTER(vp)]),
+        "isf_lattice_create_in": (C.c_int, [u8p, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, C.c_uint64, C.c_int32,
+                                            vp, vp, C.c_size_t, C.POINTER(vp)]),
+        "isf_set_schedule": (C.c_int, [vp, C.c_int32, dp, dp, i32p, i32p, C.c_double, C.c_double]),
+        "isf_run_sweeps": (C.c_int, [vp, C.c_int64, vp]),
+        "isf_read_observables": (C.c_int, [vp, C.POINTER(StepObs), C.c_int32, i32p]),
+        "isf_read_spins": (C.c_int, [vp, i8p]),
+        "isf_write_spins": (C.c_int, [vp, i8p, C.c_int64]),
+        "isf_lattice_info": (C.c_int, [vp, i64p, i64p, dp, i64p]),
+        "isf_read_state": (C.c_int, [vp, i64p, i64p, C.c_int32, i64p, i64p]),
+        "isf_enable_trace": (C.c_int, [vp, C.c_int64]),
+        "isf_read_trace": (C.c_int, [vp, i64p, C.c_int64, i64p]),
+        "isf_set_launch": (C.c_int, [vp, C.c_int32, C.c_int32]),
+        "isf_save": (C.c_int, [vp, C.c_char_p]),
+        "isf_load": (C.c_int, [C.c_char_p, vp, C.POINTER(vp)]),
+        "isf_lattice_destroy": (None, [vp]),
+        "isf_last_error": (C.c_char_p, []),
+        "isf_philox_blocks": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, C.c_int64, u32p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+def _load():
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is not built; run `python -m paper_1205_5588_gb300.build` "
+                          "(the library has no CPU fallback)")
+    return _declare(C.CDLL(path))
+
+
+lib = _load()
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise IsfError(rc, f"{what}: {lib.isf_last_error().decode(errors='replace')}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def obs_to_dicts(recs) -> list[dict]:
+    out = []
+    for r in recs:
+        d = {f: getattr(r, f) for f, _ in StepObs._fields_}
+        for f in ("sumM2", "sumB2", "sumMB"):
+            w = list(d[f])
+            v = w[0] | (w[1] << 64)
+            if f == "sumMB" and v >= 1 << 127:
+                v -= 1 << 128
+            d[f] = v
+        out.append(d)
+    return out
+
+
+def flags_of(periodic_x=False, periodic_y=False, periodic_z=False, packed=False) -> int:
+    return (PERIODIC_X if periodic_x else 0) | (PERIODIC_Y if periodic_y else 0) | \
+           (PERIODIC_Z if periodic_z else 0) | (PACKED if packed else 0)
+
+
+def lattice_bytes(rows, cols, layers, flags) -> int:
+    return int(lib.isf_lattice_bytes(rows, cols, layers, flags))
+
+
+class Lattice:
+    """One film on the current CUDA device (isf_lattice_create / isf_lattice_create_in)."""
+
+    def __init__(self, heights, layers, *, periodic_x=False, periodic_y=False, periodic_z=False,
+                 packed=False, seed=1, init="random", stream=None, torch_buffer=True):
+        H = np.ascontiguousarray(heights, dtype=np.uint8)
+        if H.ndim != 2:
+            raise ValueError("heights must be 2-D (rows, cols)")
+        self.rows, self.cols = H.shape
+        self.layers = int(layers)
+        self.flags = flags_of(periodic_x, periodic_y, periodic_z, packed)
+        self.heights = H
+        self._buf = None
+        h = C.c_void_p()
+        s = _stream_handle(stream)
+        initv = INIT[init] if isinstance(init, str) else int(init)
+        if torch_buffer:
+            import torch
+            nbytes = lattice_bytes(self.rows, self.cols, self.layers, self.flags)
+            if nbytes == 0:
+                # let the library report the reason
+                _check(lib.isf_lattice_create(_ptr(H, C.c_uint8), self.rows, self.cols, self.layers, self.flags,
+                                              int(seed), initv, s, C.byref(h)), "lattice_create")
+            self._buf = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            base = self._buf.data_ptr()
+            aligned = (base + 255) & ~255
+            rc = lib.isf_lattice_create_in(_ptr(H, C.c_uint8), self.rows, self.cols, self.layers, self.flags,
+                                           int(seed), initv, s, C.c_void_p(aligned), nbytes, C.byref(h))
+        else:
+            rc = lib.isf_lattice_create(_ptr(H, C.c_uint8), self.rows, self.cols, self.layers, self.flags,
+                                        int(seed), initv, s, C.byref(h))
+        _check(rc, "lattice_create")
+        self._h = h
+
+    @classmethod
+    def _wrap(cls, handle, rows, cols, layers, flags, heights):
+        self = cls.__new__(cls)
+        self._h, self.rows, self.cols, self.layers, self.flags = handle, rows, cols, layers, flags
+        self.heights, self._buf = heights, None
+        return self
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.isf_lattice_destroy(self._h)
+            self._h = None
+        self._buf = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_schedule(self, T, h, sweeps_eq, sweeps_meas, J=1.0, h_s=0.0):
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        eq = np.ascontiguousarray(sweeps_eq, dtype=np.int32)
+        me = np.ascontiguousarray(sweeps_meas, dtype=np.int32)
+        n = len(T)
+        if not (len(h) == len(eq) == len(me) == n):
+            raise ValueError("schedule arrays differ in length")
+        self._nsteps = n
+        _check(lib.isf_set_schedule(self._h, n, _ptr(T, C.c_double), _ptr(h, C.c_double), _ptr(eq, C.c_int32),
+                                    _ptr(me, C.c_int32), float(J), float(h_s)), "set_schedule")
+
+    def run(self, nsweeps=-1, stream=None):
+        _check(lib.isf_run_sweeps(self._h, int(nsweeps), _stream_handle(stream)), "run_sweeps")
+
+    def observables(self, max_steps=None) -> list[dict]:
+        n = max_steps if max_steps is not None else getattr(self, "_nsteps", 0)
+        recs = (StepObs * max(n, 1))()
+        got = C.c_int32()
+        _check(lib.isf_read_observables(self._h, recs, n, C.byref(got)), "read_observables")
+        return obs_to_dicts(recs[:got.value])
+
+    def spins(self) -> np.ndarray:
+        out = np.zeros((self.layers, self.rows, self.cols), dtype=np.int8)
+        _check(lib.isf_read_spins(self._h, _ptr(out, C.c_int8)), "read_spins")
+        return out
+
+    def write_spins(self, s, sweep):
+        s = np.ascontiguousarray(s, dtype=np.int8)
+        _check(lib.isf_write_spins(self._h, _ptr(s, C.c_int8), int(sweep)), "write_spins")
+
+    def info(self) -> dict:
+        n, b, sw = C.c_int64(), C.c_int64(), C.c_int64()
+        z = C.c_double()
+        _check(lib.isf_lattice_info(self._h, C.byref(n), C.byref(b), C.byref(z), C.byref(sw)), "lattice_info")
+        return {"n_occ": n.value, "n_bonds": b.value, "zbar": z.value, "sweep": sw.value}
+
+    def state(self, recompute=False) -> dict:
+        M, B, Mf, Bf = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib.isf_read_state(self._h, C.byref(M), C.byref(B), 1 if recompute else 0, C.byref(Mf), C.byref(Bf)),
+               "read_state")
+        d = {"M": M.value, "B": B.value}
+        if recompute:
+            d.update(M_full=Mf.value, B_full=Bf.value)
+        return d
+
+    def enable_trace(self, max_sweeps):
+        _check(lib.isf_enable_trace(self._h, int(max_sweeps)), "enable_trace")
+        self._trace_cap = int(max_sweeps)
+
+    def trace(self) -> np.ndarray:
+        """(M, B) after each sweep since enable_trace, as an (n, 2) int64 array."""
+        buf = np.zeros((max(getattr(self, "_trace_cap", 0), 1), 2), dtype=np.int64)
+        n = C.c_int64()
+        _check(lib.isf_read_trace(self._h, _ptr(buf, C.c_int64), getattr(self, "_trace_cap", 0), C.byref(n)),
+               "read_trace")
+        return buf[: n.value]
+
+    def set_launch(self, ctas=0, threads=0):
+        _check(lib.isf_set_launch(self._h, int(ctas), int(threads)), "set_launch")
+
+    def save(self, path):
+        _check(lib.isf_save(self._h, str(path).encode()), "save")
+
+    @classmethod
+    def load(cls, path, stream=None):
+        h = C.c_void_p()
+        _check(lib.isf_load(str(path).encode(), _stream_handle(stream), C.byref(h)), "load")
+        with open(path, "rb") as fp:
+            fp.read(8)
+            hdr = np.frombuffer(fp.read(20), dtype=np.int32)
+            fp.read(16)
+            rows, cols, layers, flags = (int(v) for v in hdr[:4])
+            heights = np.frombuffer(fp.read(rows * cols), dtype=np.uint8).reshape(rows, cols).copy()
+        return cls._wrap(h, rows, cols, layers, flags, heights)
+
+
+def philox_blocks(seed, stream, sweep, q0, n) -> np.ndarray:
+    out = np.zeros((n, 4), dtype=np.uint32)
+    _check(lib.isf_philox_blocks(int(seed), int(stream), int(sweep), int(q0), int(n), _ptr(out, C.c_uint32)),
+           "philox_blocks")
+    return out

@@ -1,0 +1,249 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, bit for bit.
+
+Integer state (spins, M and B after every sweep, the exact per-step sums) must be identical;
+fp64 estimators derived from those sums agree to 1e-12 relative.  Sizes span several CTAs,
+several 16-site chunks / 32-site words per row and ragged tails; the full-size workloads are
+checked on sampled sweeps that the oracle recomputes one at a time from the GPU's own state.
+"""
+import numpy as np
+import pytest
+
+from paper_1205_5588_gb300 import workloads as W
+from tests.gpu_common import (assert_records_equal, assert_same_run, gpu_lib, run_gpu, run_oracle)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def I():
+    return gpu_lib()
+
+
+def film(heights, layers, seed=1, init="random", **kw):
+    d = {"heights": np.ascontiguousarray(heights, dtype=np.uint8), "layers": layers, "seed": seed, "init": init}
+    d.update(kw)
+    return d
+
+
+def test_philox_device_matches_oracle(I):
+    from oracle import oracle
+    lib = oracle.load()
+    rng = np.random.Generator(np.random.PCG64(99))
+    for _ in range(40):
+        seed = int(rng.integers(0, 2**64, dtype=np.uint64))
+        stream = int(rng.integers(0, 3))
+        sweep = int(rng.integers(0, 2**40))
+        q0 = int(rng.integers(0, 2**32 - 600))
+        got = I.philox_blocks(seed, stream, sweep, q0, 500)
+        for b in range(0, 500, 7):
+            want = oracle.philox([q0 + b, sweep & 0xFFFFFFFF, sweep >> 32, stream],
+                                 [seed & 0xFFFFFFFF, seed >> 32], lib=lib)
+            assert np.array_equal(got[b], want)
+
+
+def test_flat16_hysteresis_full_run(I):
+    """16x16x3 periodic film, T = 3, h = +4 -> -4 -> +4 by 0.1, 100 sweeps per step: every one
+    of the 16,100 sweeps and all 161 step records bit-exact."""
+    spec = W.flat16_hysteresis()
+    sched = spec["schedule"]
+    g = run_gpu(I, spec, sched)
+    o = run_oracle(spec, sched)
+    assert_same_run(g, o)
+    assert g["info"]["n_occ"] == 768 and g["info"]["n_bonds"] == 3840
+
+
+def test_fractal256_tscan_prefix(I):
+    """256x256 fractal map, 1..6 layers, the T-scan's first steps at reduced sweep counts."""
+    spec = W.fractal256_tscan()
+    s = spec["schedule"]
+    sched = W.schedule(s["T"][:3], s["h"][:3], 6, 8)
+    assert_same_run(run_gpu(I, spec, sched), run_oracle(spec, sched))
+
+
+def _spot_check(I, spec, sched, stops, packed=None):
+    """Run the full schedule on the GPU, stopping at the given sweeps; at each stop the oracle
+    takes the GPU's spins and sweep counter and computes the next sweep itself."""
+    from oracle import oracle
+    packed = spec.get("packed", False) if packed is None else packed
+    lat = I.Lattice(spec["heights"], spec["layers"], packed=packed, seed=spec["seed"], init=spec["init"])
+    total = int(sched["eq"].sum() + sched["meas"].sum())
+    lat.enable_trace(total)
+    lat.set_schedule(sched["T"], sched["h"], sched["eq"], sched["meas"])
+    ends = np.cumsum(sched["eq"] + sched["meas"])
+    init = {"random": oracle.INIT_RANDOM, "up": oracle.INIT_UP, "down": oracle.INIT_DOWN}[spec["init"]]
+    of = oracle.Film(spec["heights"], spec["layers"], seed=spec["seed"], init=init)
+    done = 0
+    for t in stops:
+        lat.run(t - done)
+        before = lat.spins()
+        lat.run(1)
+        after = lat.spins()
+        done = t + 1
+        k = int(np.searchsorted(ends, t + 1))     # step holding sweep t+1
+        of.set_spins(before)
+        of.set_sweep(t)
+        recs, ser = of.run([sched["T"][k]], [sched["h"][k]], [0], [1], series=True)
+        assert np.array_equal(after, of.spins()), f"spins differ after sweep {t + 1}"
+        tr = lat.trace()
+        assert tuple(tr[t]) == tuple(ser[0]), (t, tr[t], ser[0])
+    lat.run(-1)
+    st = lat.state(recompute=True)
+    assert st["M"] == st["M_full"] and st["B"] == st["B_full"]
+    recs = lat.observables()
+    tr = lat.trace()
+    assert len(recs) == len(sched["T"])
+    for k, r in enumerate(recs):
+        assert r["M_last"] == tr[ends[k] - 1, 0] and r["B_last"] == tr[ends[k] - 1, 1]
+        seg = tr[ends[k] - sched["meas"][k]: ends[k]]
+        assert r["sumM"] == int(seg[:, 0].sum()) and r["sumB"] == int(seg[:, 1].sum())
+        assert r["sumM2"] == sum(int(v) ** 2 for v in seg[:, 0])
+    lat.close()
+
+
+def test_fractal256_tscan_full_size_sampled(I):
+    spec = W.fractal256_tscan()
+    s = spec["schedule"]
+    _spot_check(I, spec, s, stops=[0, 3999, 4000, 95999, 190000, 191998])
+
+
+def test_fractal2048_hysteresis_full_size_sampled(I):
+    spec = W.fractal2048_hysteresis()
+    s = spec["schedule"]
+    sched = W.schedule(s["T"][:4], s["h"][:4], s["eq"][:4], s["meas"][:4])
+    _spot_check(I, spec, sched, stops=[0, 399, 799])
+
+
+def test_packed_int8_oracle_agree_on_ragged_films(I):
+    for (R, C, L, hurst, lo) in [(37, 77, 4, 0.6, 0), (64, 96, 5, 0.8, 1), (9, 130, 3, 0.7, 1), (50, 33, 8, 0.5, 0)]:
+        spec = film(W.fractal_heights(R, C, hurst, lo, L, seed=R * C), L, seed=R + C)
+        sched = W.schedule([1.5, 4.0, 9.0], [0.6, -0.3, 0.0], [3, 2, 0], [4, 5, 6])
+        o = run_oracle(spec, sched)
+        assert_same_run(run_gpu(I, spec, sched, packed=False), o)
+        assert_same_run(run_gpu(I, spec, sched, packed=True), o)
+
+
+def test_fractal2048_int8_and_packed_identical(I):
+    spec = W.fractal2048_hysteresis()
+    s = spec["schedule"]
+    sched = W.schedule(s["T"][:2], s["h"][:2], 0, 25)
+    a = run_gpu(I, spec, sched, packed=True, trace=True)
+    b = run_gpu(I, spec, sched, packed=False, trace=True)
+    assert np.array_equal(a["trace"], b["trace"])
+    assert np.array_equal(a["spins"], b["spins"])
+    assert_records_equal(a["recs"], b["recs"])
+
+
+@pytest.mark.parametrize("packed", [False, True])
+def test_launch_shape_does_not_change_the_trajectory(I, packed):
+    spec = film(W.fractal_heights(80, 120, 0.7, 1, 6, seed=5), 6, seed=11)
+    sched = W.schedule([2.0, 6.0], [0.5, -0.5], [2, 2], [5, 5])
+    ref = run_gpu(I, spec, sched, packed=packed)
+    for launch in [(1, 256), (2, 64), (7, 128), (3, 32)]:
+        g = run_gpu(I, spec, sched, packed=packed, launch=launch)
+        assert np.array_equal(g["trace"], ref["trace"]) and np.array_equal(g["spins"], ref["spins"]), launch
+
+
+def test_chunked_runs_equal_one_run(I):
+    spec = film(W.fractal_heights(40, 52, 0.7, 1, 4, seed=6), 4, seed=3)
+    sched = W.schedule([3.0, 2.0, 5.0], [0.0, 0.7, -0.7], [5, 0, 3], [6, 9, 4])
+    o = run_oracle(spec, sched)
+    for chunks in ([1, 1, 1], [7, 3, 11], [20]):      # 27 sweeps in all
+        assert_same_run(run_gpu(I, spec, sched, chunks=chunks), o)
+
+
+@pytest.mark.parametrize("case", ["single_site", "all_vacant", "one_row", "thin_column", "tall_sparse",
+                                  "infinite_T", "zero_T", "down_start"])
+def test_edge_films(I, case):
+    sched = W.schedule([2.5, 3.5], [0.3, -0.3], [1, 0], [3, 4])
+    if case == "single_site":
+        spec = film(np.ones((1, 1)), 1)
+    elif case == "all_vacant":
+        spec = film(np.zeros((5, 7)), 3)
+    elif case == "one_row":
+        spec = film(np.full((1, 45), 2), 2)
+    elif case == "thin_column":
+        spec = film(np.full((31, 1), 3), 3)
+    elif case == "tall_sparse":
+        rng = np.random.Generator(np.random.PCG64(4))
+        spec = film(rng.integers(0, 9, size=(23, 19)), 8)
+    elif case == "infinite_T":
+        spec = film(W.fractal_heights(20, 24, 0.7, 1, 3, seed=1), 3)
+        sched = W.schedule([float("inf")] * 2, [0.0, 2.0], 0, 5)
+    elif case == "zero_T":
+        spec = film(W.fractal_heights(20, 24, 0.7, 1, 3, seed=1), 3)
+        sched = W.schedule([0.0, 0.0], [0.0, 1.0], 0, 5)
+    else:
+        spec = film(W.fractal_heights(17, 29, 0.7, 0, 4, seed=2), 4, init="down")
+    o = run_oracle(spec, sched)
+    for packed in (False, True):
+        assert_same_run(run_gpu(I, spec, sched, packed=packed), o)
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 2, (True, True, False)), (6, 8, 3, (True, False, False)),
+                                   (8, 6, 3, (False, True, False)), (4, 4, 4, (True, True, True)),
+                                   (10, 12, 2, (True, True, False))])
+def test_periodic_films(I, shape):
+    R, C, L, (px, py, pz) = shape
+    spec = film(np.full((R, C), L), L, seed=R * 7 + C, periodic_x=px, periodic_y=py, periodic_z=pz)
+    sched = W.schedule([2.0, 8.0, 5.0], [1.0, 0.0, -1.0], [1, 1, 1], [4, 4, 4])
+    assert_same_run(run_gpu(I, spec, sched), run_oracle(spec, sched))
+
+
+@pytest.mark.parametrize("packed,periodic", [(False, False), (True, False), (False, True)])
+def test_switching_gate_parity(I, packed, periodic):
+    if periodic:
+        spec = film(np.full((8, 8), 3), 3, periodic_x=True, periodic_y=True)
+    else:
+        spec = film(W.fractal_heights(30, 70, 0.7, 1, 4, seed=9), 4, seed=5)
+    sched = W.schedule([2.0, 4.0, 6.0], [2.0, -2.0, 0.5], [2, 2, 2], [4, 4, 4])
+    o = run_oracle(spec, sched, h_s=4.0)
+    assert_same_run(run_gpu(I, spec, sched, packed=packed, h_s=4.0), o)
+
+
+def test_write_spins_resume_and_save_load(I, tmp_path):
+    spec = film(W.fractal_heights(24, 40, 0.7, 1, 4, seed=8), 4, seed=21)
+    sched = W.schedule([2.0, 3.0], [0.4, -0.4], [0, 0], [6, 7])
+    full = run_gpu(I, spec, sched, trace=False)
+    lat = I.Lattice(spec["heights"], 4, seed=21)
+    lat.set_schedule(sched["T"][:1], sched["h"][:1], [0], [6])
+    lat.run(-1)
+    path = tmp_path / "film.isf"
+    lat.save(path)
+    lat.close()
+    lat2 = I.Lattice.load(path)
+    assert lat2.info()["sweep"] == 6
+    lat2.set_schedule(sched["T"][1:], sched["h"][1:], [0], [7])
+    lat2.run(-1)
+    assert np.array_equal(lat2.spins(), full["spins"])
+    assert lat2.observables()[0]["sumM"] == full["recs"][1]["sumM"]
+    lat2.close()
+
+
+def test_errors_are_reported(I):
+    lat = I.Lattice(np.full((6, 6), 2), 2)
+    with pytest.raises(I.IsfError) as e:
+        lat.run(1)
+    assert e.value.code == -7
+    lat.set_schedule([2.0], [0.0], [0], [3])
+    with pytest.raises(I.IsfError) as e:
+        lat.run(4)
+    assert e.value.code == -5
+    with pytest.raises(I.IsfError) as e:
+        lat.write_spins(np.full((2, 6, 6), 3, dtype=np.int8), 0)
+    assert e.value.code == -1
+    with pytest.raises(I.IsfError) as e:
+        lat.set_schedule([2.0], [0.0], [0], [0])
+    assert e.value.code == -5
+    lat.close()
+
+
+def test_runs_on_a_side_stream(I):
+    import torch
+    spec = film(W.fractal_heights(32, 48, 0.7, 1, 3, seed=3), 3, seed=2)
+    sched = W.schedule([2.0], [0.1], [2], [5])
+    s = torch.cuda.Stream()
+    lat = I.Lattice(spec["heights"], 3, seed=2, stream=s)
+    lat.set_schedule(sched["T"], sched["h"], sched["eq"], sched["meas"])
+    lat.run(-1, stream=s)
+    assert_records_equal(lat.observables(), run_oracle(spec, sched)["recs"])
+    lat.close()
