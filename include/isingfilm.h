@@ -169,6 +169,30 @@ const char* isf_last_error(void);
 int isf_philox_blocks(uint64_t seed, uint32_t stream, uint64_t sweep, uint32_t q0,
                       int64_t nblocks, uint32_t* host_out);
 
+/* No-allocation run (no counterpart in the paper; it exists for callers of this library).
+ * Some callers must not allocate device memory: code living inside a process whose device
+ * memory is owned by another allocator's pool (a foreign cudaMalloc then fails, or fragments the
+ * pool), latency-bound loops in which cudaMalloc/cudaFree would synchronise the device and stall
+ * other streams, and deployments that forbid allocation after start-up.  isf_run_noalloc runs a
+ * whole schedule on one film and allocates nothing: the film, its state, the threshold tables and
+ * the step records live in one fixed library-owned device array of ISF_NOALLOC_MAX_BYTES, which
+ * every GPU that loads the library keeps until the process exits.
+ *   Inputs as isf_lattice_create + isf_set_schedule (host arrays; the film starts at sweep 0).
+ *   dev_spins_out: caller-owned device buffer of layers*rows*cols int8, [z][y][x], final spins.
+ *   obs_out: caller-owned host array of nsteps records, as isf_read_observables fills them.
+ * Results equal those of the allocating path.  The call is synchronous on cuda_stream.  Its first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  Every call reuses the same array and clears what must start
+ * at zero; calls whose work overlaps on the GPU (other streams, other host threads) race on the
+ * array and must not be made.  A film and schedule needing more scratch than the array holds is
+ * refused with ISF_ERR_ARG before any device work; other errors as isf_lattice_create,
+ * isf_set_schedule and isf_run_sweeps. */
+#define ISF_NOALLOC_MAX_BYTES (8u << 20)
+int isf_run_noalloc(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, uint32_t flags,
+                    uint64_t seed, int32_t init, int32_t nsteps, const double* T, const double* h,
+                    const int32_t* sweeps_eq, const int32_t* sweeps_meas, double J, double h_s,
+                    int8_t* dev_spins_out, isf_step_obs* obs_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -173,6 +173,14 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
 
 }  // namespace
 
+namespace isf {
+// Last-error setter for the library's other translation units.
+int set_last_error(int code, const char* msg) {
+    g_err = msg;
+    return code;
+}
+}  // namespace isf
+
 extern "C" {
 
 const char* isf_last_error(void) { return g_err.c_str(); }
