@@ -299,6 +299,26 @@ def run_reference(args):
     f.close()
 
 
+def profile_case(args):
+    """Small case for ncu captures of the sweep kernel: the workload's film, one launch of
+    --profile-sweeps sweeps at the first schedule step."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1205_5588_gb300 import build as B
+    B.build()
+    from paper_1205_5588_gb300 import isingfilm as I
+    spec = workload(args.workload)
+    s = spec["schedule"]
+    lat = I.Lattice(spec["heights"], spec["layers"], periodic_x=spec["periodic_x"], periodic_y=spec["periodic_y"],
+                    packed=spec["packed"], seed=spec["seed"], init=spec["init"])
+    if args.ctas or args.threads:
+        lat.set_launch(args.ctas, args.threads)
+    lat.set_schedule(s["T"][:1], s["h"][:1], [0], [args.profile_sweeps], J=spec["J"])
+    lat.run(-1)
+    print("profile case done, M_last =", lat.observables()[0]["M_last"])
+    lat.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -312,7 +332,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sweeps", type=int, default=0)
+    ap.add_argument("--profile-sweeps", type=int, default=0,
+                    help="profiling case: one launch of this many sweeps at the first schedule step, no JSON")
     args = ap.parse_args()
+    if args.profile_sweeps:
+        profile_case(args)
+        return
     if args.warmup < 3 and args.impl == "cuda":
         print("note: warm-up raised to 3 steps", file=sys.stderr)
         args.warmup = 3
