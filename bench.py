@@ -165,6 +165,7 @@ def run_impl(args):
         total = float(t.item())
         torch.distributed.barrier()
     recs = lat.observables()
+    shape = lat.launch_info()
     lat.close()
     value = per_step * args.steps * ws / total
 
@@ -210,7 +211,10 @@ def run_impl(args):
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
                      "frac": achieved_tops / ALU_PEAK_TOPS, "traffic": traffic,
-                     "kernel": "k_sweep (persistent colour-pass kernel)",
+                     "kernel": ("k_resident (film in one cluster's shared memory)" if shape["path"] == "resident"
+                                else "k_sweep (global-memory persistent kernel)"),
+                     "launch": shape,
+                     "sms_usable": shape["ctas"] if shape["path"] == "resident" else 152,
                      "peak_from": "152 SMs x 128 int32 lanes x 2070 MHz (issue-rate ceiling)",
                      "ops_per_attempt": OPS_PER_ATTEMPT},
         "clocks": clk,

@@ -149,9 +149,25 @@ int isf_read_state(isf_lattice* lat, int64_t* M, int64_t* B, int32_t recompute,
 int isf_enable_trace(isf_lattice* lat, int64_t max_sweeps);
 int isf_read_trace(isf_lattice* lat, int64_t* host_out, int64_t max_pairs, int64_t* n_out);
 
-/* Launch shape override for the sweep kernel: ctas (0 = automatic) and threads per CTA
- * (0 = automatic; else a multiple of 32 in 64..1024).  Trajectories do not depend on it. */
+/* Which sweep kernel runs the film (trajectories are identical on all of them):
+ *   ISF_PATH_RESIDENT: the whole film in the shared memory of one thread-block cluster of up to
+ *     16 CTAs (row slabs, neighbour rows through distributed shared memory, hardware cluster
+ *     barrier between colour passes) — the paper's row decomposition with CTAs as processes
+ *     (Sec. 3, list items 1-2); int8 films that fit only;
+ *   ISF_PATH_GLOBAL: spins in device memory, all SMs, a grid barrier between colour passes;
+ *   ISF_PATH_AUTO (default): resident when the film fits, else global.
+ * Errors: ISF_ERR_ARG (unknown path; resident for a packed film). */
+enum { ISF_PATH_AUTO = 0, ISF_PATH_GLOBAL = 1, ISF_PATH_RESIDENT = 2 };
+int isf_set_path(isf_lattice* lat, int32_t path);
+
+/* Launch shape override: ctas = CTAs of the global kernel or cluster size (1..16) of the
+ * resident kernel (0 = automatic); threads per CTA (0 = automatic; else a multiple of 32 up to
+ * 1024; the global kernel uses at most 256).  Trajectories do not depend on it. */
 int isf_set_launch(isf_lattice* lat, int32_t ctas, int32_t threads);
+
+/* Shape of the last isf_run_sweeps launch: path (ISF_PATH_GLOBAL / ISF_PATH_RESIDENT, 0 before
+ * any launch), CTAs (global) or cluster size (resident), threads per CTA.  No device work. */
+int isf_launch_info(isf_lattice* lat, int32_t* path, int32_t* ctas, int32_t* threads);
 
 /* Save the film (shape, flags, seed, spins, sweep counter) to a file; load it back onto the
  * current device (schedule not saved).  Errors: ISF_ERR_ARG, ISF_ERR_CUDA, ISF_ERR_OOM. */

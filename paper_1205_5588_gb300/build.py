@@ -21,9 +21,9 @@ LIB_NAME = "libisingfilm.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels_sweep.cu", "kernels_aux.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels_sweep.cu", "kernels_resident.cu", "kernels_aux.cu", "noalloc.cu"]
 CPP_SOURCES = ["capi.cpp", "lattice.cpp", "schedule.cpp"]
-HEADERS = ["isf_internal.h", "device_common.cuh"]
+HEADERS = ["isf_internal.h", "device_common.cuh", "sweep_core.cuh"]
 
 
 def cuda_home() -> str:

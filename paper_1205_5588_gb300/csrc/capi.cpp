@@ -41,8 +41,10 @@ struct isf_lattice {
     // trace
     long long* d_trace = nullptr;
     int64_t trace_cap = 0, trace_n = 0;
-    // launch shape
+    // launch shape and path
     int32_t ctas = 0, threads = 0;
+    int32_t path = ISF_PATH_AUTO;
+    int32_t last_path = 0, last_ctas = 0, last_threads = 0;   // shape of the last sweep launch
     cudaStream_t last = nullptr;
 };
 
@@ -293,21 +295,38 @@ int isf_run_sweeps(isf_lattice* L, int64_t nsweeps, void* cuda_stream) {
     a.pos0 = L->pos;
     a.nsteps = L->nsteps;
     a.use_gate = L->use_gate ? 1 : 0;
-    int threads = L->threads ? L->threads : 256;
-    int maxc = 0;
-    int e = sweep_max_ctas_for(L->f, threads, &maxc);
-    if (e) return cuda_fail((cudaError_t)e, "occupancy query");
-    if (maxc < 1) return fail(ISF_ERR_CUDA, "sweep kernel cannot be resident with this block size");
-    int ctas = L->ctas;
-    if (ctas <= 0) {
-        const int64_t items = sweep_items_per_pass(L->f);
-        int64_t want = (items + threads - 1) / threads;   // about one work item per thread
-        ctas = (int)(want < 1 ? 1 : want);
-    }
-    if (ctas > maxc) ctas = maxc;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    e = launch_sweeps(a, ctas, threads, s);
-    if (e) return cuda_fail((cudaError_t)e, "sweep kernel launch");
+    bool launched = false;
+    if (L->path != ISF_PATH_GLOBAL && !L->lay.packed) {
+        ResPlan plan;
+        const bool forced = L->path == ISF_PATH_RESIDENT;
+        if (resident_plan(L->f, L->ctas, L->threads, &plan) == 0) {
+            int e = launch_resident(a, plan, s);
+            if (e) return cuda_fail((cudaError_t)e, "resident sweep kernel launch");
+            launched = true;
+            L->last_path = ISF_PATH_RESIDENT; L->last_ctas = plan.K; L->last_threads = plan.threads;
+        } else {
+            cudaGetLastError();
+            if (forced) return fail(ISF_ERR_ARG, "film does not fit one cluster's shared memory with this launch shape");
+        }
+    }
+    if (!launched) {
+        int threads = L->threads ? std::min(L->threads, 256) : 256;
+        int maxc = 0;
+        int e = sweep_max_ctas_for(L->f, threads, &maxc);
+        if (e) return cuda_fail((cudaError_t)e, "occupancy query");
+        if (maxc < 1) return fail(ISF_ERR_CUDA, "sweep kernel cannot be resident with this block size");
+        int ctas = L->ctas;
+        if (ctas <= 0) {
+            const int64_t items = sweep_items_per_pass(L->f);
+            int64_t want = (items + threads - 1) / threads;   // about one work item per thread
+            ctas = (int)(want < 1 ? 1 : want);
+        }
+        if (ctas > maxc) ctas = maxc;
+        e = launch_sweeps(a, ctas, threads, s);
+        if (e) return cuda_fail((cudaError_t)e, "sweep kernel launch");
+        L->last_path = ISF_PATH_GLOBAL; L->last_ctas = ctas; L->last_threads = threads;
+    }
     L->last = s;
     L->sweep += nsweeps;
     if (L->d_trace) L->trace_n = std::min<int64_t>(L->trace_cap, L->trace_n + nsweeps);
@@ -442,10 +461,25 @@ int isf_read_trace(isf_lattice* L, int64_t* host_out, int64_t max_pairs, int64_t
 
 int isf_set_launch(isf_lattice* L, int32_t ctas, int32_t threads) {
     if (!L || ctas < 0) return fail(ISF_ERR_ARG, "bad arguments");
-    if (threads != 0 && (threads % 32 || threads < 32 || threads > 256))
-        return fail(ISF_ERR_ARG, "threads must be 0 or a multiple of 32 in 32..256");
+    if (threads != 0 && (threads % 32 || threads < 32 || threads > 1024))
+        return fail(ISF_ERR_ARG, "threads must be 0 or a multiple of 32 in 32..1024");
     L->ctas = ctas;
     L->threads = threads;
+    return ISF_OK;
+}
+
+int isf_launch_info(isf_lattice* L, int32_t* path, int32_t* ctas, int32_t* threads) {
+    if (!L) return fail(ISF_ERR_ARG, "lattice is NULL");
+    if (path) *path = L->last_path;
+    if (ctas) *ctas = L->last_ctas;
+    if (threads) *threads = L->last_threads;
+    return ISF_OK;
+}
+
+int isf_set_path(isf_lattice* L, int32_t path) {
+    if (!L || path < ISF_PATH_AUTO || path > ISF_PATH_RESIDENT) return fail(ISF_ERR_ARG, "bad arguments");
+    if (path == ISF_PATH_RESIDENT && L->lay.packed) return fail(ISF_ERR_ARG, "the resident path holds int8 films only");
+    L->path = path;
     return ISF_OK;
 }
 

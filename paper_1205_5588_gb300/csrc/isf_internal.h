@@ -39,6 +39,8 @@ struct NbrClass {
     int64_t off[12];
     int32_t sgn;
     int32_t pad_;
+    int8_t c2[12], dz[12], dj[12];   // same order: neighbour colour, layer step, row step
+    int8_t pad2_[4];
 };
 
 struct DevFilm {
@@ -129,6 +131,17 @@ int launch_pack(const DevFilm& f, const int8_t* dev_in, void* stream);
 int launch_philox_blocks(uint64_t seed, uint32_t stream_id, uint64_t sweep, uint32_t q0,
                          int64_t nblocks, uint32_t* dev_out, void* stream);
 int sweep_max_ctas_for(const DevFilm& f, int threads, int* max_ctas);  // co-resident CTAs
+
+// Cluster-resident sweeps (kernels_resident.cu): the film sits in the shared memory of one
+// thread-block cluster of K CTAs (row slabs), int8 layout, any boundary flags.
+struct ResPlan {
+    int32_t K, Jb, threads;
+    uint32_t film_off, vac_off, ptr_off, misc_off, smem;
+};
+// Plan for a film: K = want_K (0: automatic), threads = want_threads (0: automatic).
+// Returns 0 and fills out when the film fits, else a nonzero code (no device work).
+int resident_plan(const DevFilm& f, int want_K, int want_threads, ResPlan* out);
+int launch_resident(const SweepArgs& a, const ResPlan& plan, void* stream);
 int sweep_items_per_pass(const DevFilm& f);                            // work items per colour pass
 
 }  // namespace isf

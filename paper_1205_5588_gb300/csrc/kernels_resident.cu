@@ -1,0 +1,334 @@
+// kernels_resident.cu — Metropolis sweeps (Eq. 8; Eq. 9 gate) with the whole film held in the
+// shared memory of one thread-block cluster.
+//
+// The film's int8 layout is cut into row slabs: CTA r of a K-CTA cluster keeps rows
+// [r*Jb, (r+1)*Jb) of every (colour, layer) in its shared memory for the whole launch.  A
+// neighbour row that belongs to another CTA is read through distributed shared memory; rows
+// outside an open boundary point at a shared row of vacancies; periodic rows and layers wrap in
+// the row-pointer table, and periodic columns through two wrap bytes per row (column -1 and
+// column Ch mirror Ch-1 and 0).  Colour passes are separated by the hardware cluster barrier
+// (release / acquire), so one sweep costs four on-chip barriers and no L2 round trip.  This is
+// the paper's row decomposition (Sec. 3, list items 1-2: rows per process plus the neighbouring
+// processes' boundary rows) with CTAs of one cluster as the processes and DSMEM as the halo.
+//
+// The state is copied in from the global layout at the start of a launch and written back at
+// the end, so launches of this kernel and of the global-memory kernel interleave freely; the
+// random words are the same Philox words, so the trajectory is the same.
+#include <cuda_runtime.h>
+
+#include "sweep_core.cuh"
+
+namespace isf {
+
+namespace {
+
+constexpr int kMaxK = 16;
+constexpr uint32_t kMiscBytes = 128 * 4 + 16 + 64 * 8 + 2 * kMaxK * 8 + kMaxK * 8;
+
+struct ResArgs {
+    SweepArgs s;
+    int32_t K, Jb;
+    uint32_t film_off, vac_off, ptr_off, misc_off;
+};
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// generic address of the same shared-memory location in CTA `rank` of this cluster
+__device__ __forceinline__ uint8_t* map_rank(uint8_t* p, unsigned rank) {
+    uint64_t out;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(reinterpret_cast<uint64_t>(p)), "r"(rank));
+    return reinterpret_cast<uint8_t*>(out);
+}
+
+template <bool CLUSTER>
+__device__ __forceinline__ void sync_all() {
+    if (CLUSTER) cluster_sync_all();
+    else __syncthreads();
+}
+
+template <bool CLUSTER, bool PX>
+__global__ void __launch_bounds__(1024, 1) k_resident(const __grid_constant__ ResArgs a) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const SweepArgs& s = a.s;
+    const DevFilm& f = s.f;
+    const unsigned K = CLUSTER ? (unsigned)a.K : 1u;
+    const unsigned rank = CLUSTER ? cluster_rank() : 0u;
+    const int Jb = a.Jb, L = f.L, Rh = f.Rh, nck = f.nck, Ch = f.Ch;
+    const int P = (int)f.P;
+    const int j0 = (int)rank * Jb;
+    const int nown = min(Jb, Rh - j0);
+    uint8_t* film = sm + a.film_off;
+    uint8_t* vac = sm + a.vac_off;
+    uint8_t** ptrs = reinterpret_cast<uint8_t**>(sm + a.ptr_off);
+    uint32_t* tab = reinterpret_cast<uint32_t*>(sm + a.misc_off);
+    uint32_t* gate = tab + 128;
+    long long* red = reinterpret_cast<long long*>(sm + a.misc_off + 128 * 4 + 16);
+    long long* slots = red + 64;
+    uint8_t** base = reinterpret_cast<uint8_t**>(slots + 2 * kMaxK);
+
+    // slab in, vacancy row, every rank's slab address
+    const int words = P / 16;
+    for (int t = threadIdx.x; t < 4 * L * nown * words; t += blockDim.x) {
+        const int w = t % words;
+        const int rr = t / words;
+        const int jl = rr % nown, cz = rr / nown;
+        const uint4* src = reinterpret_cast<const uint4*>(f.s8 + addr8(f, cz / L, cz % L, j0 + jl, -16));
+        reinterpret_cast<uint4*>(film + ((size_t)cz * Jb + jl) * P)[w] = src[w];
+    }
+    for (int t = threadIdx.x; t < P / 4; t += blockDim.x) reinterpret_cast<uint32_t*>(vac)[t] = 0x01010101u;
+    if (threadIdx.x < K) base[threadIdx.x] = CLUSTER ? map_rank(film, threadIdx.x) : film;
+    __syncthreads();
+    if (PX) {
+        for (int rr = threadIdx.x; rr < 4 * L * nown; rr += blockDim.x) {
+            uint8_t* row = film + ((size_t)(rr / nown) * Jb + rr % nown) * P;
+            row[15] = row[16 + Ch - 1];
+            row[16 + Ch] = row[16];
+        }
+    }
+    // neighbour-row table of every own row, in the class order (9 unshifted, 3 shifted)
+    for (int t = threadIdx.x; t < 4 * L * nown * 12; t += blockDim.x) {
+        const int k = t % 12;
+        const int rr = t / 12;
+        const int jl = rr % nown, cz = rr / nown;
+        const int c = cz / L, z = cz % L;
+        const NbrClass& nc = f.nb[c][z & 1];
+        int zz = z + nc.dz[k], jj = j0 + jl + nc.dj[k];
+        bool inside = true;
+        if (zz < 0 || zz >= L) {
+            if (f.flags & 4u) zz = (zz + L) % L;
+            else inside = false;
+        }
+        if (jj < 0 || jj >= Rh) {
+            if (f.flags & 2u) jj = (jj + Rh) % Rh;
+            else inside = false;
+        }
+        uint8_t* p = vac;
+        if (inside) {
+            const int rk = jj / Jb;
+            p = base[rk] + ((size_t)(nc.c2[k] * L + zz) * Jb + (jj - rk * Jb)) * P;
+        }
+        ptrs[((size_t)cz * Jb + jl) * 12 + k] = p;
+    }
+    sync_all<CLUSTER>();    // every slab loaded before anyone reads a neighbour's
+
+    const int items = L * nown * nck;
+    ItemWalk walk0;
+    walk0.init(threadIdx.x, blockDim.x, nck, nown);
+    int k = s.k0, pos = s.pos0;
+    const bool folder = rank == 0 && threadIdx.x == 0;
+    __shared__ RunState rs;     // touched by the folding thread only
+    int k_eq = 0, k_tot = 0;
+    if (folder) {
+        load_run_state(s.st, rs);
+        k_eq = s.step_eq[k];
+        k_tot = s.step_total[k];
+    }
+    stage_table<false>(s.tables, k, tab, gate);
+    for (long long t = 0; t < s.nsweeps; ++t) {
+        if (pos == s.step_total[k]) {
+            ++k;
+            pos = 0;
+            stage_table<false>(s.tables, k, tab, gate);
+            if (folder) { k_eq = s.step_eq[k]; k_tot = s.step_total[k]; }
+        }
+        const unsigned long long sweep = (unsigned long long)(s.sweep0 + t + 1);
+        const uint32_t gthr = *gate;
+        int dM = 0, dB = 0;
+        for (int c = 0; c < 4; ++c) {
+            ItemWalk w = walk0;
+            for (int it = threadIdx.x; it < items; it += blockDim.x, w.next()) {
+                const int ck = w.ck, jl = w.jr, z = w.z;
+                const size_t r = (size_t)(c * L + z) * Jb + jl;
+                uint8_t* row = film + r * P;
+                uint8_t* own = row + 16 + 16 * ck;
+                uint8_t* const* pr = ptrs + r * 12;
+                const uint8_t* nbp[12];
+#pragma unroll
+                for (int kk = 0; kk < 12; ++kk) nbp[kk] = pr[kk] + 16 + 16 * ck;
+                const uint32_t q0 = block_counter(f, c, z, j0 + jl, 16 * ck);
+                const int sgn = f.nb[c][z & 1].sgn;
+                if (s.use_gate)
+                    update_chunk16<true, PX>(own, nbp, sgn, q0, sweep, tab, gthr, f.key0, f.key1, 16 * ck, Ch, row, dM, dB);
+                else
+                    update_chunk16<false, PX>(own, nbp, sgn, q0, sweep, tab, gthr, f.key0, f.key1, 16 * ck, Ch, row, dM, dB);
+            }
+            if (c == 3) {
+                long long sM = dM, sB = dB;
+                block_sum2(sM, sB, red);
+                if (threadIdx.x == 0) {
+                    long long* slot = CLUSTER ? reinterpret_cast<long long*>(map_rank(reinterpret_cast<uint8_t*>(slots + 2 * rank), 0))
+                                              : slots;
+                    slot[0] = sM;
+                    slot[1] = sB;
+                }
+            }
+            sync_all<CLUSTER>();
+        }
+        if (folder) {
+            long long sM = 0, sB = 0;
+            for (unsigned r = 0; r < K; ++r) { sM += slots[2 * r]; sB += slots[2 * r + 1]; }
+            fold_sweep(s, rs, k, pos, k_eq, k_tot, sM, sB, t);
+        }
+        ++pos;
+    }
+    if (folder) store_run_state(s.st, rs);
+
+    // slab out: the site columns only (the wrap bytes and halo stay out of the global layout)
+    const int cw = nck;   // 16-byte words holding columns 0 .. 16*nck-1
+    for (int t = threadIdx.x; t < 4 * L * nown * cw; t += blockDim.x) {
+        const int w = t % cw;
+        const int rr = t / cw;
+        const int jl = rr % nown, cz = rr / nown;
+        uint4 v = reinterpret_cast<const uint4*>(film + ((size_t)cz * Jb + jl) * P + 16)[w];
+        if (PX && Ch < 16 * nck && (Ch >> 4) == w) {
+            // column Ch (a wrap byte) falls in this word: put the vacancy padding back
+            uint32_t* vw = reinterpret_cast<uint32_t*>(&v);
+            const int b = Ch & 15;
+            vw[b >> 2] = (vw[b >> 2] & ~(0xFFu << (8 * (b & 3)))) | (0x01u << (8 * (b & 3)));
+        }
+        uint8_t* dst = f.s8 + addr8(f, cz / L, cz % L, j0 + jl, 0);
+        reinterpret_cast<uint4*>(dst)[w] = v;
+    }
+    sync_all<CLUSTER>();    // no CTA leaves while another may still address its shared memory
+}
+
+template <bool CLUSTER, bool PX>
+int launch_variant(const ResArgs& ra, const ResPlan& p, cudaStream_t s) {
+    auto kern = k_resident<CLUSTER, PX>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return (int)e;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(p.K);
+    cfg.blockDim = dim3(p.threads);
+    cfg.dynamicSmemBytes = p.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    if (CLUSTER) {
+        if (p.K > 8) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return (int)e;
+        }
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = p.K;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return (int)cudaLaunchKernelEx(&cfg, kern, ra);
+}
+
+template <bool CLUSTER, bool PX>
+int clusters_possible(const ResPlan& p, int* n) {
+    auto kern = k_resident<CLUSTER, PX>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    if (e != cudaSuccess) return (int)e;
+    if (!CLUSTER) { *n = 1; return 0; }
+    if (p.K > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return (int)e;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(p.K);
+    cfg.blockDim = dim3(p.threads);
+    cfg.dynamicSmemBytes = p.smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = p.K;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return (int)cudaOccupancyMaxActiveClusters(n, kern, &cfg);
+}
+
+inline uint32_t round16(uint32_t v) { return (v + 15u) & ~15u; }
+
+bool layout_for(const DevFilm& f, int K, int threads, int max_smem, ResPlan* out) {
+    if (K < 1 || K > kMaxK || K > f.Rh) return false;
+    const int Jb = (f.Rh + K - 1) / K;
+    if ((K - 1) * Jb >= f.Rh) return false;      // every CTA owns at least one row
+    const uint64_t rows = (uint64_t)4 * f.L * Jb;
+    ResPlan p{};
+    p.K = K;
+    p.Jb = Jb;
+    p.threads = threads;
+    p.film_off = 0;
+    p.vac_off = round16((uint32_t)(rows * f.P));
+    p.ptr_off = round16(p.vac_off + (uint32_t)f.P);
+    p.misc_off = round16(p.ptr_off + (uint32_t)(rows * 12 * 8));
+    p.smem = round16(p.misc_off + kMiscBytes);
+    if (rows * f.P > (uint64_t)max_smem || p.smem > (uint32_t)max_smem) return false;
+    *out = p;
+    return true;
+}
+
+}  // namespace
+
+int resident_plan(const DevFilm& f, int want_K, int want_threads, ResPlan* out) {
+    if (f.packed) return 1;                               // int8 layout only
+    int dev = 0, max_smem = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 2;
+    if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 2;
+    const int threads = want_threads > 0 ? want_threads : 0;
+    // Work of one colour pass per CTA: about 4096 lattice sites (one 16-site chunk per thread
+    // of a 256-thread CTA); the smallest power of two that also fits the shared memory.
+    const int64_t per_pass = (int64_t)f.L * f.Rh * f.Ch;
+    int K0 = 1;
+    while (K0 < kMaxK && per_pass / K0 > 4096) K0 *= 2;
+    // candidates: K0, 2*K0, ..., 16, then K0/2, ..., 1 (or only the requested size)
+    int cand[8], nc = 0;
+    if (want_K > 0) {
+        cand[nc++] = want_K;
+    } else {
+        for (int K = K0; K <= kMaxK; K *= 2) cand[nc++] = K;
+        for (int K = K0 / 2; K >= 1; K /= 2) cand[nc++] = K;
+    }
+    for (int ci = 0; ci < nc; ++ci) {
+        const int K = cand[ci];
+        ResPlan p;
+        // threads: one per 16-site chunk of a pass, rounded to whole warps, 64..1024
+        int th = threads;
+        if (!th) {
+            const int Jb = (f.Rh + K - 1) / K;
+            const int64_t items = (int64_t)f.L * Jb * f.nck;
+            th = (int)((items + 31) / 32 * 32);
+            if (th < 64) th = 64;
+            if (th > 1024) th = 1024;
+        }
+        if (!layout_for(f, K, th, max_smem, &p)) continue;
+        int n = 0;
+        const bool px = (f.flags & 1u) != 0;
+        const int e = K > 1 ? (px ? clusters_possible<true, true>(p, &n) : clusters_possible<true, false>(p, &n))
+                            : (px ? clusters_possible<false, true>(p, &n) : clusters_possible<false, false>(p, &n));
+        if (e == 0 && n >= 1) {
+            *out = p;
+            return 0;
+        }
+        cudaGetLastError();
+    }
+    return 3;
+}
+
+int launch_resident(const SweepArgs& a, const ResPlan& p, void* stream) {
+    ResArgs ra{};
+    ra.s = a;
+    ra.K = p.K;
+    ra.Jb = p.Jb;
+    ra.film_off = p.film_off;
+    ra.vac_off = p.vac_off;
+    ra.ptr_off = p.ptr_off;
+    ra.misc_off = p.misc_off;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool px = (a.f.flags & 1u) != 0;
+    if (p.K > 1) return px ? launch_variant<true, true>(ra, p, s) : launch_variant<true, false>(ra, p, s);
+    return px ? launch_variant<false, true>(ra, p, s) : launch_variant<false, false>(ra, p, s);
+}
+
+}  // namespace isf

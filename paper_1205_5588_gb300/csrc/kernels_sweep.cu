@@ -13,8 +13,7 @@
 // last barrier CTA 0 folds the deltas into M and B and into the step's exact sums.
 #include <cuda_runtime.h>
 
-#include "../../include/isingfilm.h"
-#include "device_common.cuh"
+#include "sweep_core.cuh"
 
 namespace isf {
 
@@ -29,174 +28,61 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
 
-// Barrier over the G co-resident CTAs.  Thread 0 of each CTA arrives on a counter; the last one
-// resets it and publishes a new generation; the others wait for it with a bounded spin.
-__device__ bool grid_barrier(FilmState* st, unsigned G, unsigned& gen, int* ok_s) {
+// Barrier over the G co-resident CTAs of a cooperative launch.  The arrival counter only grows
+// during a launch (the host zeroes it before each launch): barrier b is passed once it reaches
+// b * G.  Thread 0 of each CTA adds 1 with release semantics and polls with acquire loads; the
+// wait is bounded, and on expiry the kernel records ISF_ERR_TIMEOUT and every CTA returns.
+__device__ __forceinline__ bool grid_barrier(FilmState* st, unsigned G, unsigned& target, int* ok_s) {
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        if (G > 1) {
-            __threadfence();
-            const unsigned arrived = atomicAdd(&st->bar_count, 1u) + 1u;
-            if (arrived == G) {
-                atomicExch(&st->bar_count, 0u);
-                __threadfence();
-                st_release_u32(&st->bar_gen, gen + 1u);
-            } else {
-                unsigned spins = 0;
-                while (ld_acquire_u32(&st->bar_gen) == gen) {
-                    if (ld_volatile_i32(&st->error)) { ok = 0; break; }
-                    if (++spins > kSpinLimit) {
-                        atomicCAS(&st->error, 0, (int)ISF_ERR_TIMEOUT);
-                        st->error_where = 1;
-                        ok = 0;
-                        break;
-                    }
-                    if (spins > 32) __nanosleep(40);
+    if (G > 1) {
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            target += G;
+            red_release_add_u32(&st->bar_count, 1u);
+            unsigned spins = 0;
+            while ((int)(ld_acquire_u32(&st->bar_count) - target) < 0) {
+                ++spins;
+                if ((spins & 15u) == 0 && ld_volatile_i32(&st->error)) { ok = 0; break; }
+                if (spins > kSpinLimit) {
+                    atomicCAS(&st->error, 0, (int)ISF_ERR_TIMEOUT);
+                    st->error_where = 1;
+                    ok = 0;
+                    break;
                 }
+                if (spins > 64) __nanosleep(32);
             }
-            gen += 1u;
-            __threadfence();
+            *ok_s = ok;
         }
-        if (ld_volatile_i32(&st->error)) ok = 0;
-        *ok_s = ok;
+        __syncthreads();
+        return *ok_s != 0;
     }
-    __syncthreads();
-    return *ok_s != 0;
-}
-
-// Table of the current step in shared memory, indexed by the per-site byte the pass forms:
-//   int8 / generic: (stored byte << 5) | (n + 12), stored byte 0 = down, 1 = vacancy, 2 = up
-//   packed        : (occupied << 6) | (up << 5) | (n + 12)
-// Vacancies map to 0 ("never"), so they never flip and never draw a random word.
-template <int MODE>
-__device__ void load_table(const SweepArgs& a, int k, uint32_t* tab, uint32_t* gate) {
-    const uint32_t* src = a.tables + (size_t)k * kTableStride;
-    for (int t = threadIdx.x; t < 128; t += blockDim.x) {
-        uint32_t v = 0;
-        const int X = t & 31;
-        if (X <= 24) {
-            if (MODE == MODE_PACKED) {
-                if (t >> 6) v = src[X * 2 + ((t >> 5) & 1)];
-            } else {
-                const int sb = t >> 5;
-                if (sb == 0) v = src[X * 2 + 0];
-                else if (sb == 2) v = src[X * 2 + 1];
-            }
-        }
-        tab[t] = v;
-    }
-    if (threadIdx.x == 0) *gate = src[kGateSlot];
-    __syncthreads();
-}
-
-// accept iff u < thr, or thr == always (min keeps u = 2^32-1 below always)
-__device__ __forceinline__ bool metropolis_accept(uint32_t u, uint32_t thr) {
-    return min(u, 0xFFFFFFFEu) < thr;
-}
-// a random word decides the site only when thr is neither 0 ("never") nor always
-__device__ __forceinline__ bool needs_word(uint32_t thr) { return (thr - 1u) < 0xFFFFFFFEu; }
-
-__device__ __forceinline__ uint4 ld16(const uint8_t* p) { return *reinterpret_cast<const uint4*>(p); }
-__device__ __forceinline__ uint32_t ld4(const uint8_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
-__device__ __forceinline__ void add4(uint4& a, const uint4& b) {
-    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
-}
-
-// Eq. 9 gate for the accepted lanes of one 4-site block (stream 1): clears the lanes that fail.
-__device__ __forceinline__ uint32_t gate_block(uint32_t acc_lanes, uint32_t gthr, uint32_t q,
-                                               unsigned long long sweep, const DevFilm& f) {
-    if (!acc_lanes || gthr == kAlways) return acc_lanes;
-    if (gthr == 0u) return 0u;
-    const uint4 g = philox10(make_uint4(q, (uint32_t)sweep, (uint32_t)(sweep >> 32), 1u), f.key0, f.key1);
-    uint32_t keep = 0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-        if (metropolis_accept(word_of(g, b), gthr)) keep |= 1u << b;
-    return acc_lanes & keep;
+    return true;
 }
 
 // ---- int8 layout, open boundaries: one thread per 16-site chunk of a colour row ------------
 template <bool GATE>
 __device__ __forceinline__ void chunk_int8(const DevFilm& f, int c, int z, int j, int ck,
                                            unsigned long long sweep, const uint32_t* tab,
-                                           uint32_t gthr, long long& dM, long long& dB) {
+                                           uint32_t gthr, int& dM, int& dB) {
     const NbrClass& nc = f.nb[c][z & 1];
     uint8_t* own = f.s8 + addr8(f, c, z, j, 16 * ck);
-    const uint4 S = ld16(own);
-    // n + 12 per byte: sum of the 12 neighbour bytes (S + 1, vacancy 1), no carries (<= 24)
-    uint4 acc = ld16(own + nc.off[0]);
+    const uint8_t* nbp[12];
 #pragma unroll
-    for (int k = 1; k < 9; ++k) add4(acc, ld16(own + nc.off[k]));
-    if (nc.sgn < 0) {
-#pragma unroll
-        for (int k = 9; k < 12; ++k) {
-            const uint8_t* p = own + nc.off[k];
-            const uint4 v = ld16(p);
-            const uint32_t e = ld4(p - 4);
-            add4(acc, make_uint4(__funnelshift_l(e, v.x, 8), __funnelshift_l(v.x, v.y, 8),
-                                 __funnelshift_l(v.y, v.z, 8), __funnelshift_l(v.z, v.w, 8)));
-        }
-    } else {
-#pragma unroll
-        for (int k = 9; k < 12; ++k) {
-            const uint8_t* p = own + nc.off[k];
-            const uint4 v = ld16(p);
-            const uint32_t e = ld4(p + 16);
-            add4(acc, make_uint4(__funnelshift_r(v.x, v.y, 8), __funnelshift_r(v.y, v.z, 8),
-                                 __funnelshift_r(v.z, v.w, 8), __funnelshift_r(v.w, e, 8)));
-        }
-    }
-    const uint32_t q0 = block_counter(f, c, z, j, 16 * ck);
-    const uint32_t Sw[4] = {S.x, S.y, S.z, S.w};
-    const uint32_t Aw[4] = {acc.x, acc.y, acc.z, acc.w};
-    uint32_t out[4];
-    uint32_t any = 0;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const uint32_t iw = (Sw[v] << 5) + Aw[v];
-        uint32_t thr[4];
-        bool need = false;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            thr[b] = tab[(iw >> (8 * b)) & 0xFFu];
-            need |= needs_word(thr[b]);
-        }
-        uint4 u = make_uint4(0, 0, 0, 0);
-        if (need) u = philox10(make_uint4(q0 + v, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u), f.key0, f.key1);
-        uint32_t lanes = 0;
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-            if (metropolis_accept(word_of(u, b), thr[b])) lanes |= 1u << b;
-        if (GATE) lanes = gate_block(lanes, gthr, q0 + v, sweep, f);
-        uint32_t flip = 0;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            if (lanes & (1u << b)) {
-                const uint32_t byte = (iw >> (8 * b)) & 0xFFu;
-                const int s = (byte & 64u) ? 1 : -1;
-                const int n = (int)(byte & 31u) - 12;
-                dM -= 2 * s;
-                dB -= 2 * s * n;
-                flip |= 2u << (8 * b);   // 0 <-> 2
-            }
-        }
-        out[v] = Sw[v] ^ flip;
-        any |= flip;
-    }
-    if (any) *reinterpret_cast<uint4*>(own) = make_uint4(out[0], out[1], out[2], out[3]);
+    for (int k = 0; k < 12; ++k) nbp[k] = own + nc.off[k];
+    update_chunk16<GATE, false>(own, nbp, nc.sgn, block_counter(f, c, z, j, 16 * ck), sweep, tab, gthr,
+                                f.key0, f.key1, 16 * ck, f.Ch, nullptr, dM, dB);
 }
 
 // ---- int8 layout, any boundary (periodic wraps): one thread per 4-site Philox block --------
 template <bool GATE>
 __device__ __forceinline__ void block_generic(const DevFilm& f, int c, int z, int j, int blk,
                                               unsigned long long sweep, const uint32_t* tab,
-                                              uint32_t gthr, long long& dM, long long& dB) {
+                                              uint32_t gthr, int& dM, int& dB) {
     const int zp = z & 1, px = (c & 1) ^ zp, py = ((c >> 1) & 1) ^ zp;
     const int y = 2 * j + py;
     if (y >= f.R) return;
@@ -229,7 +115,7 @@ __device__ __forceinline__ void block_generic(const DevFilm& f, int c, int z, in
 #pragma unroll
     for (int b = 0; b < 4; ++b)
         if (metropolis_accept(word_of(u, b), thr[b])) lanes |= 1u << b;
-    if (GATE) lanes = gate_block(lanes, gthr, q, sweep, f);
+    if (GATE) lanes = gate_block(lanes, gthr, q, sweep, f.key0, f.key1);
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         if (!(lanes & (1u << b))) continue;
@@ -268,7 +154,7 @@ __device__ __forceinline__ void popcount12(const uint32_t* x, uint32_t& b0, uint
 template <bool GATE>
 __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int j, int w,
                                             unsigned long long sweep, const uint32_t* tab,
-                                            uint32_t gthr, long long& dM, long long& dB) {
+                                            uint32_t gthr, int& dM, int& dB) {
     const NbrClass& nc = f.nb[c][z & 1];
     const int64_t base = addrw(f, c, z, j, w);
     const uint32_t* sp = f.sp;
@@ -343,7 +229,7 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
 #pragma unroll
         for (int b = 0; b < 4; ++b)
             if (metropolis_accept(word_of(u, b), thr[b])) lanes |= 1u << b;
-        if (GATE) lanes = gate_block(lanes, gthr, q0 + v, sweep, f);
+        if (GATE) lanes = gate_block(lanes, gthr, q0 + v, sweep, f.key0, f.key1);
         F |= lanes << (4 * v);
     }
     if (F) {
@@ -356,62 +242,20 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
             xu += __popc(X[p] & Fu) << p;
             xd += __popc(X[p] & Fd) << p;
         }
-        dM += -2LL * (nu - nd);
-        dB += -2LL * ((xu - 12 * nu) - (xd - 12 * nd));
-    }
-}
-
-__device__ void fold_sweep(const SweepArgs& a, int k, int pos, unsigned long long sweep, long long t) {
-    FilmState* st = a.st;
-    unsigned long long* acc = reinterpret_cast<unsigned long long*>(&st->acc[sweep & 1][0]);
-    const long long dM = (long long)atomicExch(acc, 0ull);
-    const long long dB = (long long)atomicExch(acc + 1, 0ull);
-    const long long M = st->M + dM, B = st->B + dB;
-    st->M = M;
-    st->B = B;
-    if (pos >= a.step_eq[k]) {
-        st->n_meas += 1;
-        st->sumM += M;
-        st->sumAbsM += M < 0 ? -M : M;
-        st->sumB += B;
-        typedef unsigned __int128 u128;
-        u128 m2 = ((u128)st->sumM2[1] << 64 | st->sumM2[0]) + (u128)((__int128)M * M);
-        u128 b2 = ((u128)st->sumB2[1] << 64 | st->sumB2[0]) + (u128)((__int128)B * B);
-        u128 mb = ((u128)st->sumMB[1] << 64 | st->sumMB[0]) + (u128)((__int128)M * B);
-        st->sumM2[0] = (unsigned long long)m2; st->sumM2[1] = (unsigned long long)(m2 >> 64);
-        st->sumB2[0] = (unsigned long long)b2; st->sumB2[1] = (unsigned long long)(b2 >> 64);
-        st->sumMB[0] = (unsigned long long)mb; st->sumMB[1] = (unsigned long long)(mb >> 64);
-    }
-    if (pos + 1 == a.step_total[k]) {
-        StepRec r;
-        r.M_last = M; r.B_last = B; r.n_meas = st->n_meas;
-        r.sumM = st->sumM; r.sumAbsM = st->sumAbsM; r.sumB = st->sumB;
-        r.sumM2[0] = st->sumM2[0]; r.sumM2[1] = st->sumM2[1];
-        r.sumB2[0] = st->sumB2[0]; r.sumB2[1] = st->sumB2[1];
-        r.sumMB[0] = st->sumMB[0]; r.sumMB[1] = st->sumMB[1];
-        a.recs[k] = r;
-        st->n_meas = 0; st->sumM = 0; st->sumAbsM = 0; st->sumB = 0;
-        st->sumM2[0] = st->sumM2[1] = 0; st->sumB2[0] = st->sumB2[1] = 0; st->sumMB[0] = st->sumMB[1] = 0;
-    }
-    if (a.trace && a.trace_begin + t < a.trace_cap) {
-        a.trace[2 * (a.trace_begin + t)] = M;
-        a.trace[2 * (a.trace_begin + t) + 1] = B;
+        dM += -2 * (nu - nd);
+        dB += -2 * ((xu - 12 * nu) - (xd - 12 * nd));
     }
 }
 
 template <int MODE, bool GATE>
 __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned long long sweep,
-                                            const uint32_t* tab, uint32_t gthr, int per_row,
-                                            int items, long long& dM, long long& dB) {
+                                            const uint32_t* tab, uint32_t gthr, int items,
+                                            ItemWalk w, int& dM, int& dB) {
     const int stride = gridDim.x * blockDim.x;
-    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += stride) {
-        const int row = it / per_row;
-        const int w = it - row * per_row;
-        const int z = row / f.Rh;
-        const int j = row - z * f.Rh;
-        if (MODE == MODE_INT8) chunk_int8<GATE>(f, c, z, j, w, sweep, tab, gthr, dM, dB);
-        else if (MODE == MODE_GENERIC) block_generic<GATE>(f, c, z, j, w, sweep, tab, gthr, dM, dB);
-        else word_packed<GATE>(f, c, z, j, w, sweep, tab, gthr, dM, dB);
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += stride, w.next()) {
+        if (MODE == MODE_INT8) chunk_int8<GATE>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
+        else if (MODE == MODE_GENERIC) block_generic<GATE>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
+        else word_packed<GATE>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
     }
 }
 
@@ -419,53 +263,59 @@ template <int MODE>
 __global__ void __launch_bounds__(kBlock) k_sweep(const __grid_constant__ SweepArgs a) {
     __shared__ uint32_t tab[128];
     __shared__ uint32_t gate_s;
-    __shared__ long long red[2][32];
+    __shared__ long long red[64];
     __shared__ int ok_s;
     const DevFilm& f = a.f;
     FilmState* st = a.st;
     const unsigned G = gridDim.x;
-    unsigned gen = 0;
-    if (threadIdx.x == 0 && G > 1) gen = *reinterpret_cast<const volatile unsigned*>(&st->bar_gen);
+    unsigned target = 0;
     const int per_row = MODE == MODE_INT8 ? f.nck : (MODE == MODE_GENERIC ? f.Qw : f.nw);
     const int items = f.L * f.Rh * per_row;
+    ItemWalk walk0;
+    walk0.init(blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, per_row, f.Rh);
     int k = a.k0, pos = a.pos0;
-    load_table<MODE>(a, k, tab, &gate_s);
+    const bool folder = blockIdx.x == 0 && threadIdx.x == 0;
+    __shared__ RunState rs;     // touched by the folding thread only
+    int k_eq = 0, k_tot = 0;
+    if (folder) {
+        load_run_state(st, rs);
+        k_eq = a.step_eq[k];
+        k_tot = a.step_total[k];
+    }
+    stage_table<MODE == MODE_PACKED>(a.tables, k, tab, &gate_s);
     for (long long t = 0; t < a.nsweeps; ++t) {
         if (pos == a.step_total[k]) {
             ++k;
             pos = 0;
-            load_table<MODE>(a, k, tab, &gate_s);
+            stage_table<MODE == MODE_PACKED>(a.tables, k, tab, &gate_s);
+            if (folder) { k_eq = a.step_eq[k]; k_tot = a.step_total[k]; }
         }
         const unsigned long long sweep = (unsigned long long)(a.sweep0 + t + 1);
         const uint32_t gthr = gate_s;
-        long long dM = 0, dB = 0;
+        int dM = 0, dB = 0;
         for (int c = 0; c < 4; ++c) {
-            if (a.use_gate) colour_pass<MODE, true>(f, c, sweep, tab, gthr, per_row, items, dM, dB);
-            else colour_pass<MODE, false>(f, c, sweep, tab, gthr, per_row, items, dM, dB);
+            if (a.use_gate) colour_pass<MODE, true>(f, c, sweep, tab, gthr, items, walk0, dM, dB);
+            else colour_pass<MODE, false>(f, c, sweep, tab, gthr, items, walk0, dM, dB);
             if (c == 3) {
-                dM = warp_sum(dM);
-                dB = warp_sum(dB);
-                const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-                if (lane == 0) { red[0][wid] = dM; red[1][wid] = dB; }
-                __syncthreads();
-                if (wid == 0) {
-                    const int nw = blockDim.x >> 5;
-                    dM = lane < nw ? red[0][lane] : 0;
-                    dB = lane < nw ? red[1][lane] : 0;
-                    dM = warp_sum(dM);
-                    dB = warp_sum(dB);
-                    if (lane == 0 && (dM | dB)) {
-                        unsigned long long* acc = reinterpret_cast<unsigned long long*>(&st->acc[sweep & 1][0]);
-                        atomicAdd(acc, (unsigned long long)dM);
-                        atomicAdd(acc + 1, (unsigned long long)dB);
-                    }
+                long long sM = dM, sB = dB;
+                block_sum2(sM, sB, red);
+                if (threadIdx.x == 0 && (sM | sB)) {
+                    unsigned long long* acc = reinterpret_cast<unsigned long long*>(&st->acc[sweep & 1][0]);
+                    atomicAdd(acc, (unsigned long long)sM);
+                    atomicAdd(acc + 1, (unsigned long long)sB);
                 }
             }
-            if (!grid_barrier(st, G, gen, &ok_s)) return;
+            if (!grid_barrier(st, G, target, &ok_s)) return;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) fold_sweep(a, k, pos, sweep, t);
+        if (folder) {
+            unsigned long long* acc = reinterpret_cast<unsigned long long*>(&st->acc[sweep & 1][0]);
+            const long long sM = (long long)atomicExch(acc, 0ull);
+            const long long sB = (long long)atomicExch(acc + 1, 0ull);
+            fold_sweep(a, rs, k, pos, k_eq, k_tot, sM, sB, t);
+        }
         ++pos;
     }
+    if (folder) store_run_state(st, rs);
 }
 
 template <int MODE>
@@ -474,6 +324,8 @@ int launch_mode(const SweepArgs& a, int ctas, int threads, cudaStream_t s) {
         k_sweep<MODE><<<1, threads, 0, s>>>(a);
         return (int)cudaGetLastError();
     }
+    cudaError_t e = cudaMemsetAsync(&a.st->bar_count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return (int)e;
     void* args[] = {const_cast<SweepArgs*>(&a)};
     return (int)cudaLaunchCooperativeKernel((const void*)k_sweep<MODE>, dim3(ctas), dim3(threads), args, 0, s);
 }

@@ -134,6 +134,7 @@ void fill_neighbour_classes(const Layout& lay, DevFilm* f) {
             const int px = (c & 1) ^ zp, py = ((c >> 1) & 1) ^ zp;
             NbrClass nc{};
             int64_t plain8[12], plainw[12];
+            int8_t pc[12], pz[12], pj[12], sc[3], sz[3], sj[3];
             int np = 0, ns = 0, sgn = 0;
             int64_t sh8[3] = {0, 0, 0}, shw[3] = {0, 0, 0};
             for (int k = 0; k < 12; ++k) {
@@ -143,15 +144,25 @@ void fill_neighbour_classes(const Layout& lay, DevFilm* f) {
                 const int64_t row8 = (int64_t)(c2 - c) * lay.cs8 + dz * lay.ls8 + dj * lay.P;
                 const int64_t roww = (int64_t)(c2 - c) * lay.csw + dz * lay.lsw + dj * lay.Wp;
                 if (di == 0) {
-                    plain8[np] = row8; plainw[np] = roww; ++np;
+                    plain8[np] = row8; plainw[np] = roww;
+                    pc[np] = (int8_t)c2; pz[np] = (int8_t)dz; pj[np] = (int8_t)dj;
+                    ++np;
                 } else {
                     sgn = di;   // the same sign for all three: -1 when px = 0, +1 when px = 1
-                    sh8[ns] = row8; shw[ns] = roww; ++ns;
+                    sh8[ns] = row8; shw[ns] = roww;
+                    sc[ns] = (int8_t)c2; sz[ns] = (int8_t)dz; sj[ns] = (int8_t)dj;
+                    ++ns;
                 }
             }
             // np == 9, ns == 3 by construction of the stencil (checked by the caller's tests)
-            for (int k = 0; k < 9; ++k) nc.off[k] = lay.packed ? plainw[k] : plain8[k];
-            for (int k = 0; k < 3; ++k) nc.off[9 + k] = lay.packed ? shw[k] : sh8[k];
+            for (int k = 0; k < 9; ++k) {
+                nc.off[k] = lay.packed ? plainw[k] : plain8[k];
+                nc.c2[k] = pc[k]; nc.dz[k] = pz[k]; nc.dj[k] = pj[k];
+            }
+            for (int k = 0; k < 3; ++k) {
+                nc.off[9 + k] = lay.packed ? shw[k] : sh8[k];
+                nc.c2[9 + k] = sc[k]; nc.dz[9 + k] = sz[k]; nc.dj[9 + k] = sj[k];
+            }
             nc.sgn = sgn;
             f->nb[c][zp] = nc;
             (void)np; (void)ns;

@@ -1,0 +1,245 @@
+// sweep_core.cuh — the per-site Metropolis update (Eq. 8; the Eq. 9 gate of items 4-5 of
+// Sec. 5), shared by the global-memory and the cluster-resident sweep kernels, plus the
+// step-table staging and the per-sweep fold of M, B into the step's exact sums.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "../../include/isingfilm.h"
+#include "device_common.cuh"
+
+namespace isf {
+
+// Table of the current step in shared memory, indexed by the per-site byte a pass forms:
+//   int8   : (stored byte << 5) | (n + 12), stored byte 0 = down, 1 = vacancy, 2 = up
+//   packed : (occupied << 6) | (up << 5) | (n + 12)
+// Vacancies map to 0 ("never"), so they never flip and never draw a random word.
+template <bool PACKED>
+__device__ __forceinline__ void stage_table(const uint32_t* tables, int k, uint32_t* tab, uint32_t* gate) {
+    const uint32_t* src = tables + (size_t)k * kTableStride;
+    for (int t = threadIdx.x; t < 128; t += blockDim.x) {
+        uint32_t v = 0;
+        const int X = t & 31;
+        if (X <= 24) {
+            if (PACKED) {
+                if (t >> 6) v = src[X * 2 + ((t >> 5) & 1)];
+            } else {
+                const int sb = t >> 5;
+                if (sb == 0) v = src[X * 2 + 0];
+                else if (sb == 2) v = src[X * 2 + 1];
+            }
+        }
+        tab[t] = v;
+    }
+    if (threadIdx.x == 0) *gate = src[kGateSlot];
+    __syncthreads();
+}
+
+// accept iff u < thr, or thr == always (min keeps u = 2^32-1 below always)
+__device__ __forceinline__ bool metropolis_accept(uint32_t u, uint32_t thr) { return min(u, 0xFFFFFFFEu) < thr; }
+// a random word decides the site only when thr is neither 0 ("never") nor always
+__device__ __forceinline__ bool needs_word(uint32_t thr) { return (thr - 1u) < 0xFFFFFFFEu; }
+
+__device__ __forceinline__ uint4 ld16(const uint8_t* p) { return *reinterpret_cast<const uint4*>(p); }
+__device__ __forceinline__ uint32_t ld4(const uint8_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ void add4(uint4& a, const uint4& b) {
+    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+}
+
+// Eq. 9 gate for the accepted lanes of one 4-site block (stream 1): clears the lanes that fail.
+__device__ __forceinline__ uint32_t gate_block(uint32_t lanes, uint32_t gthr, uint32_t q,
+                                               unsigned long long sweep, uint32_t key0, uint32_t key1) {
+    if (!lanes || gthr == kAlways) return lanes;
+    if (gthr == 0u) return 0u;
+    const uint4 g = philox10(make_uint4(q, (uint32_t)sweep, (uint32_t)(sweep >> 32), 1u), key0, key1);
+    uint32_t keep = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        if (metropolis_accept(word_of(g, b), gthr)) keep |= 1u << b;
+    return lanes & keep;
+}
+
+// One 16-site chunk of an int8 colour row.  own: the chunk's 16 bytes.  nb[k]: the same
+// columns' 16 bytes in neighbour row k (k < 9 unshifted; k = 9..11 shifted by sgn columns,
+// completed from the word before / after).  Bytes hold S + 1 (vacancy 1), so 12 word adds give
+// n + 12 per byte.  Per 4-site word: four table lookups, one Philox block when any of the four
+// thresholds is neither 0 nor "always", the flips as a byte mask (0 <-> 2 is XOR 2), and dM, dB
+// from popcounts of that mask and a multiply-add of the masked neighbour sums.  PX (periodic
+// x): lanes past the row end are masked, stores go byte by byte, and column 0 / column Ch-1
+// also refresh their wrap copies at row[16 + Ch] / row[15].
+template <bool GATE, bool PX>
+__device__ __forceinline__ void update_chunk16(uint8_t* own, const uint8_t* const* nb, int sgn, uint32_t q0,
+                                               unsigned long long sweep, const uint32_t* tab, uint32_t gthr,
+                                               uint32_t key0, uint32_t key1, int i0, int Ch, uint8_t* row,
+                                               int& dM, int& dB) {
+    const uint4 S = ld16(own);
+    uint4 acc = ld16(nb[0]);
+#pragma unroll
+    for (int k = 1; k < 9; ++k) add4(acc, ld16(nb[k]));
+    if (sgn < 0) {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) {
+            const uint4 v = ld16(nb[k]);
+            const uint32_t e = ld4(nb[k] - 4);
+            add4(acc, make_uint4(__funnelshift_l(e, v.x, 8), __funnelshift_l(v.x, v.y, 8),
+                                 __funnelshift_l(v.y, v.z, 8), __funnelshift_l(v.z, v.w, 8)));
+        }
+    } else {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) {
+            const uint4 v = ld16(nb[k]);
+            const uint32_t e = ld4(nb[k] + 16);
+            add4(acc, make_uint4(__funnelshift_r(v.x, v.y, 8), __funnelshift_r(v.y, v.z, 8),
+                                 __funnelshift_r(v.z, v.w, 8), __funnelshift_r(v.w, e, 8)));
+        }
+    }
+    const uint32_t Sw[4] = {S.x, S.y, S.z, S.w};
+    const uint32_t Aw[4] = {acc.x, acc.y, acc.z, acc.w};
+    uint32_t out[4];
+    uint32_t any = 0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const uint32_t iw = (Sw[v] << 5) + Aw[v];
+        uint32_t thr[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            thr[b] = tab[(iw >> (8 * b)) & 0xFFu];
+            if (PX && i0 + 4 * v + b >= Ch) thr[b] = 0u;
+        }
+        const bool need = needs_word(thr[0]) | needs_word(thr[1]) | needs_word(thr[2]) | needs_word(thr[3]);
+        uint4 u = make_uint4(0, 0, 0, 0);
+        if (need) u = philox10(make_uint4(q0 + v, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u), key0, key1);
+        uint32_t fm = (metropolis_accept(u.x, thr[0]) ? 0x00000002u : 0u) |
+                      (metropolis_accept(u.y, thr[1]) ? 0x00000200u : 0u) |
+                      (metropolis_accept(u.z, thr[2]) ? 0x00020000u : 0u) |
+                      (metropolis_accept(u.w, thr[3]) ? 0x02000000u : 0u);
+        if (GATE && fm) {
+            uint32_t lanes = ((fm >> 1) & 1u) | ((fm >> 8) & 2u) | ((fm >> 15) & 4u) | ((fm >> 22) & 8u);
+            lanes = gate_block(lanes, gthr, q0 + v, sweep, key0, key1);
+            fm = ((lanes & 1u) << 1) | ((lanes & 2u) << 8) | ((lanes & 4u) << 15) | ((lanes & 8u) << 22);
+        }
+        // flipped from up (byte 2) and from down (byte 0); dM = -2 (n_up - n_down),
+        // dB = -2 [sum over up-flips of n - sum over down-flips of n], n = byte of Aw - 12
+        const uint32_t up = fm & Sw[v], dn = fm ^ up;
+        const int nu = __popc(up), nd = __popc(dn);
+        const uint32_t xu = ((Aw[v] & ((up >> 1) * 0xFFu)) * 0x01010101u) >> 24;
+        const uint32_t xd = ((Aw[v] & ((dn >> 1) * 0xFFu)) * 0x01010101u) >> 24;
+        dM += 2 * (nd - nu);
+        dB += 2 * (((int)xd - 12 * nd) - ((int)xu - 12 * nu));
+        out[v] = Sw[v] ^ fm;
+        any |= fm;
+    }
+    if (!any) return;
+    if (!PX) {
+        *reinterpret_cast<uint4*>(own) = make_uint4(out[0], out[1], out[2], out[3]);
+        return;
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        if (out[v] == Sw[v]) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint8_t nbyte = (uint8_t)(out[v] >> (8 * b));
+            if (nbyte == (uint8_t)(Sw[v] >> (8 * b))) continue;
+            const int i = i0 + 4 * v + b;
+            own[4 * v + b] = nbyte;
+            if (i == 0) row[16 + Ch] = nbyte;
+            if (i == Ch - 1) row[15] = nbyte;
+        }
+    }
+}
+
+// Walks a thread's work items it, it + T, it + 2T, ... of a pass laid out as (z, row, chunk)
+// with nc chunks per row and nr rows per layer, by carries instead of divisions.
+struct ItemWalk {
+    int ck, jr, z;              // current item
+    int dck, djr, dz;           // the stride T split the same way
+    int nc, nr;
+    __device__ __forceinline__ void init(int it, int T, int nc_, int nr_) {
+        nc = nc_; nr = nr_;
+        ck = it % nc; const int rz = it / nc; jr = rz % nr; z = rz / nr;
+        dck = T % nc; const int drz = T / nc; djr = drz % nr; dz = drz / nr;
+    }
+    __device__ __forceinline__ void next() {
+        ck += dck;
+        int carry = 0;
+        if (ck >= nc) { ck -= nc; carry = 1; }
+        jr += djr + carry;
+        z += dz;
+        if (jr >= nr) { jr -= nr; z += 1; }
+    }
+};
+
+// Running film state kept in shared memory by the one folding thread for a whole launch;
+// loaded from and stored to the FilmState at the launch's start and end, so a sweep's fold
+// costs no device-memory round trip.
+struct RunState {
+    long long M, B, n_meas, sumM, sumAbsM, sumB;
+    unsigned __int128 sumM2, sumB2, sumMB;
+};
+
+__device__ __forceinline__ void load_run_state(const FilmState* st, RunState& r) {
+    r.M = st->M; r.B = st->B; r.n_meas = st->n_meas;
+    r.sumM = st->sumM; r.sumAbsM = st->sumAbsM; r.sumB = st->sumB;
+    r.sumM2 = (unsigned __int128)st->sumM2[1] << 64 | st->sumM2[0];
+    r.sumB2 = (unsigned __int128)st->sumB2[1] << 64 | st->sumB2[0];
+    r.sumMB = (unsigned __int128)st->sumMB[1] << 64 | st->sumMB[0];
+}
+
+__device__ __forceinline__ void store_run_state(FilmState* st, const RunState& r) {
+    st->M = r.M; st->B = r.B; st->n_meas = r.n_meas;
+    st->sumM = r.sumM; st->sumAbsM = r.sumAbsM; st->sumB = r.sumB;
+    st->sumM2[0] = (unsigned long long)r.sumM2; st->sumM2[1] = (unsigned long long)(r.sumM2 >> 64);
+    st->sumB2[0] = (unsigned long long)r.sumB2; st->sumB2[1] = (unsigned long long)(r.sumB2 >> 64);
+    st->sumMB[0] = (unsigned long long)r.sumMB; st->sumMB[1] = (unsigned long long)(r.sumMB >> 64);
+}
+
+// Fold one sweep's (dM, dB) into M, B and the current step's exact sums; write the step's
+// record after its last sweep; keep the trace.  Single thread, stores only.
+__device__ __forceinline__ void fold_sweep(const SweepArgs& a, RunState& r, int k, int pos, int step_eq,
+                                           int step_total, long long dM, long long dB, long long t) {
+    r.M += dM;
+    r.B += dB;
+    const long long M = r.M, B = r.B;
+    if (pos >= step_eq) {
+        r.n_meas += 1;
+        r.sumM += M;
+        r.sumAbsM += M < 0 ? -M : M;
+        r.sumB += B;
+        r.sumM2 += (unsigned __int128)((__int128)M * M);
+        r.sumB2 += (unsigned __int128)((__int128)B * B);
+        r.sumMB += (unsigned __int128)((__int128)M * B);
+    }
+    if (pos + 1 == step_total) {
+        StepRec rec;
+        rec.M_last = M; rec.B_last = B; rec.n_meas = r.n_meas;
+        rec.sumM = r.sumM; rec.sumAbsM = r.sumAbsM; rec.sumB = r.sumB;
+        rec.sumM2[0] = (unsigned long long)r.sumM2; rec.sumM2[1] = (unsigned long long)(r.sumM2 >> 64);
+        rec.sumB2[0] = (unsigned long long)r.sumB2; rec.sumB2[1] = (unsigned long long)(r.sumB2 >> 64);
+        rec.sumMB[0] = (unsigned long long)r.sumMB; rec.sumMB[1] = (unsigned long long)(r.sumMB >> 64);
+        a.recs[k] = rec;
+        r.n_meas = 0; r.sumM = 0; r.sumAbsM = 0; r.sumB = 0;
+        r.sumM2 = 0; r.sumB2 = 0; r.sumMB = 0;
+    }
+    if (a.trace && a.trace_begin + t < a.trace_cap) {
+        a.trace[2 * (a.trace_begin + t)] = M;
+        a.trace[2 * (a.trace_begin + t) + 1] = B;
+    }
+}
+
+// Block-wide sum of (dM, dB); the result is valid in thread 0.  red: 64 long longs of smem.
+__device__ __forceinline__ void block_sum2(long long& dM, long long& dB, long long* red) {
+    dM = warp_sum(dM);
+    dB = warp_sum(dB);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[wid] = dM; red[32 + wid] = dB; }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        dM = lane < nw ? red[lane] : 0;
+        dB = lane < nw ? red[32 + lane] : 0;
+        dM = warp_sum(dM);
+        dB = warp_sum(dB);
+    }
+}
+
+}  // namespace isf

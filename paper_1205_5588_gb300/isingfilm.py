@@ -14,6 +14,7 @@ import numpy as np
 from . import build as _build
 
 PERIODIC_X, PERIODIC_Y, PERIODIC_Z, PACKED = 1, 2, 4, 8
+PATHS = {"auto": 0, "global": 1, "resident": 2}
 INIT = {"random": 0, "up": 1, "down": 2}
 STATUS = {0: "ISF_OK", -1: "ISF_ERR_ARG", -2: "ISF_ERR_OOM", -3: "ISF_ERR_CUDA", -4: "ISF_ERR_COLOURING",
           -5: "ISF_ERR_SCHEDULE", -6: "ISF_ERR_TIMEOUT", -7: "ISF_ERR_STATE"}
@@ -56,6 +57,8 @@ def _declare(lib):
         "isf_enable_trace": (C.c_int, [vp, C.c_int64]),
         "isf_read_trace": (C.c_int, [vp, i64p, C.c_int64, i64p]),
         "isf_set_launch": (C.c_int, [vp, C.c_int32, C.c_int32]),
+        "isf_set_path": (C.c_int, [vp, C.c_int32]),
+        "isf_launch_info": (C.c_int, [vp, i32p, i32p, i32p]),
         "isf_save": (C.c_int, [vp, C.c_char_p]),
         "isf_load": (C.c_int, [C.c_char_p, vp, C.POINTER(vp)]),
         "isf_lattice_destroy": (None, [vp]),
@@ -240,6 +243,15 @@ class Lattice:
 
     def set_launch(self, ctas=0, threads=0):
         _check(lib.isf_set_launch(self._h, int(ctas), int(threads)), "set_launch")
+
+    def launch_info(self) -> dict:
+        p, c, t = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib.isf_launch_info(self._h, C.byref(p), C.byref(c), C.byref(t)), "launch_info")
+        return {"path": {0: None, 1: "global", 2: "resident"}[p.value], "ctas": c.value, "threads": t.value}
+
+    def set_path(self, path="auto"):
+        """'resident' (film in one cluster's shared memory), 'global', or 'auto'."""
+        _check(lib.isf_set_path(self._h, PATHS[path]), "set_path")
 
     def save(self, path):
         _check(lib.isf_save(self._h, str(path).encode()), "save")

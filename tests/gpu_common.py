@@ -29,10 +29,12 @@ def oracle_flags(spec):
            (4 if spec.get("periodic_z") else 0)
 
 
-def run_gpu(I, spec, sched, *, packed=None, launch=None, chunks=None, trace=True, h_s=0.0):
+def run_gpu(I, spec, sched, *, packed=None, launch=None, chunks=None, trace=True, h_s=0.0, path="auto"):
     packed = spec.get("packed", False) if packed is None else packed
     lat = I.Lattice(spec["heights"], spec["layers"], packed=packed, seed=spec["seed"], init=spec["init"],
                     **spec_flags(spec))
+    if path != "auto":
+        lat.set_path(path)
     if launch:
         lat.set_launch(*launch)
     total = int(sched["eq"].sum() + sched["meas"].sum())

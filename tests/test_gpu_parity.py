@@ -133,14 +133,60 @@ def test_fractal2048_int8_and_packed_identical(I):
     assert_records_equal(a["recs"], b["recs"])
 
 
-@pytest.mark.parametrize("packed", [False, True])
-def test_launch_shape_does_not_change_the_trajectory(I, packed):
+@pytest.mark.parametrize("packed,path", [(False, "global"), (True, "global"), (False, "resident")])
+def test_launch_shape_does_not_change_the_trajectory(I, packed, path):
     spec = film(W.fractal_heights(80, 120, 0.7, 1, 6, seed=5), 6, seed=11)
     sched = W.schedule([2.0, 6.0], [0.5, -0.5], [2, 2], [5, 5])
-    ref = run_gpu(I, spec, sched, packed=packed)
-    for launch in [(1, 256), (2, 64), (7, 128), (3, 32)]:
-        g = run_gpu(I, spec, sched, packed=packed, launch=launch)
+    ref = run_oracle(spec, sched)
+    shapes = [(1, 256), (2, 64), (7, 128), (3, 32)] if path == "global" else \
+             [(1, 1024), (2, 256), (3, 128), (4, 512), (8, 64), (10, 96), (5, 0), (0, 0)]   # 40 colour rows
+    for launch in shapes:
+        g = run_gpu(I, spec, sched, packed=packed, launch=launch, path=path)
         assert np.array_equal(g["trace"], ref["trace"]) and np.array_equal(g["spins"], ref["spins"]), launch
+
+
+@pytest.mark.parametrize("name", ["flat16", "periodic_y_only", "periodic_x_only", "cube4", "ragged", "f256_prefix"])
+def test_resident_path_matches_oracle(I, name):
+    sched = W.schedule([2.0, 8.0, 5.0], [1.0, 0.0, -1.0], [1, 1, 1], [4, 4, 4])
+    if name == "flat16":
+        spec = W.flat16_hysteresis()
+        sched = W.schedule(3.0, spec["schedule"]["h"][:30], 0, 20)
+    elif name == "periodic_y_only":
+        spec = film(np.full((12, 9), 3), 3, seed=4, periodic_y=True)
+    elif name == "periodic_x_only":
+        spec = film(W.fractal_heights(9, 36, 0.7, 1, 4, seed=3), 4, seed=8, periodic_x=True)
+    elif name == "cube4":
+        spec = film(np.full((4, 4), 4), 4, seed=6, periodic_x=True, periodic_y=True, periodic_z=True)
+    elif name == "ragged":
+        spec = film(W.fractal_heights(45, 83, 0.6, 0, 5, seed=10), 5, seed=12)
+    else:
+        spec = W.fractal256_tscan()
+        s = spec["schedule"]
+        sched = W.schedule(s["T"][:3], s["h"][:3], 6, 8)
+    o = run_oracle(spec, sched)
+    # cluster sizes the film fits: the 256x256x6 film needs at least 4 CTAs of shared memory
+    launches = ([0, 0], [4, 0], [8, 512], [16, 256]) if name == "f256_prefix" else ([0, 0], [1, 0], [2, 0], [3, 64])
+    for launch in launches:
+        if launch[0] > (spec["heights"].shape[0] + 1) // 2:
+            continue
+        assert_same_run(run_gpu(I, spec, sched, launch=tuple(launch), path="resident"), o)
+
+
+def test_paths_interleave(I):
+    """Launches of the resident and the global kernel on one film continue each other."""
+    spec = film(W.fractal_heights(64, 96, 0.7, 1, 5, seed=13), 5, seed=14)
+    sched = W.schedule([2.0, 3.0, 4.0], [0.3, 0.0, -0.3], [3, 3, 3], [5, 5, 5])
+    o = run_oracle(spec, sched)
+    lat = I.Lattice(spec["heights"], 5, seed=14)
+    lat.enable_trace(24)
+    lat.set_schedule(sched["T"], sched["h"], sched["eq"], sched["meas"])
+    for n, path in ((5, "resident"), (4, "global"), (7, "resident"), (8, "global")):
+        lat.set_path(path)
+        lat.run(n)
+    assert np.array_equal(lat.trace(), o["trace"])
+    assert np.array_equal(lat.spins(), o["spins"])
+    assert_records_equal(lat.observables(), o["recs"])
+    lat.close()
 
 
 def test_chunked_runs_equal_one_run(I):
