@@ -165,6 +165,12 @@ int isf_set_path(isf_lattice* lat, int32_t path);
  * 1024; the global kernel uses at most 256).  Trajectories do not depend on it. */
 int isf_set_launch(isf_lattice* lat, int32_t ctas, int32_t threads);
 
+/* The resident and batch kernels check every address they derive from a film's description and
+ * skip (and record) an out-of-range access instead of making it.  This returns the first one
+ * recorded in the process as (code, value, value, 0); all zeros when none.  The read functions
+ * also report it as ISF_ERR_STATE. */
+int isf_debug_checks(uint64_t* out4);
+
 /* Shape of the last isf_run_sweeps launch: path (ISF_PATH_GLOBAL / ISF_PATH_RESIDENT, 0 before
  * any launch), CTAs (global) or cluster size (resident), threads per CTA.  No device work. */
 int isf_launch_info(isf_lattice* lat, int32_t* path, int32_t* ctas, int32_t* threads);
@@ -184,6 +190,36 @@ const char* isf_last_error(void);
  * host_out[4b .. 4b+3].  Synchronous. */
 int isf_philox_blocks(uint64_t seed, uint32_t stream, uint64_t sweep, uint32_t q0,
                       int64_t nblocks, uint32_t* host_out);
+
+/* ---- Batched films -------------------------------------------------------------------------
+ * Many independent films (each its own height map, seed and temperature / field schedule: the
+ * paper's scans and loops, Sec. 3, Fig. 3, Fig. 5, for many samples at once) advanced together.
+ * A batch references lattices created with isf_lattice_create (it does not own them); each needs
+ * a schedule.  isf_batch_run advances every member to the end of its schedule: films that fit
+ * one CTA's shared memory are taken from a device queue by a persistent single-CTA kernel, films
+ * that need a cluster by a persistent cluster kernel (cluster size K), concurrently on two forked
+ * streams; films that fit neither (packed, or too large) run after them on the global path.  Each
+ * film's trajectory is the one it has alone.  Asynchronous on cuda_stream; read each film with
+ * isf_read_observables / isf_read_spins afterwards. */
+typedef struct isf_batch isf_batch;
+int isf_batch_create(isf_batch** out);
+int isf_batch_add(isf_batch* batch, isf_lattice* lat);        /* ISF_ERR_STATE: no schedule */
+int isf_batch_clear(isf_batch* batch);
+/* Launch shapes: threads of the single-CTA kernel, cluster size K (1..16) and threads of the
+ * cluster kernel; 0 = tuned or default (256; 16 and 512). */
+int isf_batch_set_launch(isf_batch* batch, int32_t threads_single, int32_t cluster_K, int32_t threads_cluster);
+/* on != 0: capture the queue upload and the two persistent launches in a CUDA graph once and
+ * replay it on later runs with the same shape (the per-film arguments are refreshed each run). */
+int isf_batch_set_graph(isf_batch* batch, int32_t on);
+/* Autotuner: times short probe runs of the largest film of each class (copies, not the members)
+ * over cluster sizes {8, 16} and threads {128, 256, 512, 1024}; keeps the fastest per class,
+ * cached per (device, class, layers, row and column size class) for the process. */
+int isf_batch_tune(isf_batch* batch, void* cuda_stream);
+int isf_batch_run(isf_batch* batch, void* cuda_stream);
+/* Last run: films in the single-CTA / cluster / global classes, CTAs and clusters launched,
+ * cluster size, threads of the two kernels (8 int32). */
+int isf_batch_info(isf_batch* batch, int32_t* out8);
+void isf_batch_destroy(isf_batch* batch);
 
 /* No-allocation run (no counterpart in the paper; it exists for callers of this library).
  * Some callers must not allocate device memory: code living inside a process whose device

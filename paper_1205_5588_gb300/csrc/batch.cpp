@@ -1,0 +1,395 @@
+// batch.cpp — batched films: many independent films, each with its own height map, seed and
+// temperature / field schedule (the paper's temperature scans and hysteresis loops, Sec. 3,
+// Fig. 3, Fig. 5, run for many samples at once), advanced to the end of their schedules by one
+// persistent launch per size class, optionally replayed from a captured CUDA graph.
+//
+// Classes: films whose int8 layout fits one CTA's shared memory go to a single-CTA queue
+// kernel; films that need a cluster go to a cluster queue kernel (K CTAs per film); the two
+// launches run concurrently on two forked streams and every CTA / cluster pulls films from its
+// queue (longest first).  Films that fit neither (packed, or larger than a cluster) run after
+// them on the global-memory path.  Every film keeps its own RNG key and sweep counter, so its
+// trajectory is the one it has alone.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "capi_internal.h"
+
+using namespace isf;
+
+struct isf_batch {
+    std::vector<isf_lattice*> films;
+    int32_t threads_a = 0, K_b = 0, threads_b = 0;   // 0 = tuned or default
+    bool use_graph = false;
+    // device-side queues: class A entries, then class B entries
+    ResArgs* d_desc = nullptr;
+    size_t cap = 0;
+    unsigned* d_next = nullptr;
+    ResArgs* h_desc = nullptr;   // pinned staging
+    cudaStream_t sa = nullptr, sb = nullptr, sc = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_a = nullptr, ev_b = nullptr, ev_done = nullptr;
+    bool pending = false;
+    // graph
+    cudaGraphExec_t gexec = nullptr;
+    int64_t gsig[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // last run
+    int32_t n_a = 0, n_b = 0, n_c = 0, units_a = 0, units_b = 0, used_K = 0, used_ta = 0, used_tb = 0;
+    int device = 0;
+};
+
+namespace {
+
+constexpr int kDefaultThreadsA = 256;
+constexpr int kDefaultK = 16;
+constexpr int kDefaultThreadsB = 512;
+
+int fail(int code, const std::string& msg) { return set_last_error(code, msg.c_str()); }
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(ISF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+#define CUDA_TRY(expr, what)                                  \
+    do {                                                      \
+        cudaError_t e_ = (cudaError_t)(expr);                 \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);    \
+    } while (0)
+
+int ensure_streams(isf_batch* b) {
+    if (b->sa) return ISF_OK;
+    CUDA_TRY(cudaGetDevice(&b->device), "cudaGetDevice");
+    CUDA_TRY(cudaStreamCreateWithFlags(&b->sa, cudaStreamNonBlocking), "stream");
+    CUDA_TRY(cudaStreamCreateWithFlags(&b->sb, cudaStreamNonBlocking), "stream");
+    CUDA_TRY(cudaStreamCreateWithFlags(&b->sc, cudaStreamNonBlocking), "stream");
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "event");
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_a, cudaEventDisableTiming), "event");
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_b, cudaEventDisableTiming), "event");
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming), "event");
+    CUDA_TRY(cudaMalloc(&b->d_next, 2 * sizeof(unsigned)), "cudaMalloc");
+    return ISF_OK;
+}
+
+int ensure_capacity(isf_batch* b, size_t n) {
+    if (n <= b->cap) return ISF_OK;
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->h_desc) cudaFreeHost(b->h_desc);
+    b->d_desc = nullptr;
+    b->h_desc = nullptr;
+    b->cap = 0;
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    CUDA_TRY(cudaMalloc(&b->d_desc, n * sizeof(ResArgs)), "cudaMalloc batch queue");
+    CUDA_TRY(cudaMallocHost(&b->h_desc, n * sizeof(ResArgs)), "cudaMallocHost batch queue");
+    b->cap = n;
+    return ISF_OK;
+}
+
+// The launch sequence: queue upload, counters, fork, the two persistent launches, join.
+int enqueue(isf_batch* b, cudaStream_t s, int n_a, int n_b, int K, int ta, int tb, uint32_t smem_a,
+            uint32_t smem_b, int units_a, int units_b) {
+    const size_t n = (size_t)n_a + n_b;
+    CUDA_TRY(cudaMemcpyAsync(b->d_desc, b->h_desc, n * sizeof(ResArgs), cudaMemcpyHostToDevice, s), "upload queue");
+    CUDA_TRY(cudaMemsetAsync(b->d_next, 0, 2 * sizeof(unsigned), s), "reset queue");
+    CUDA_TRY(cudaEventRecord(b->ev_fork, s), "fork");
+    if (n_a) {
+        CUDA_TRY(cudaStreamWaitEvent(b->sa, b->ev_fork, 0), "fork");
+        int e = launch_batch(b->d_desc, n_a, b->d_next, 1, ta, smem_a, units_a, b->sa);
+        if (e) return cuda_fail((cudaError_t)e, "batch launch (single-CTA films)");
+        CUDA_TRY(cudaEventRecord(b->ev_a, b->sa), "join");
+        CUDA_TRY(cudaStreamWaitEvent(s, b->ev_a, 0), "join");
+    }
+    if (n_b) {
+        CUDA_TRY(cudaStreamWaitEvent(b->sb, b->ev_fork, 0), "fork");
+        int e = launch_batch(b->d_desc + n_a, n_b, b->d_next + 1, K, tb, smem_b, units_b, b->sb);
+        if (e) return cuda_fail((cudaError_t)e, "batch launch (cluster films)");
+        CUDA_TRY(cudaEventRecord(b->ev_b, b->sb), "join");
+        CUDA_TRY(cudaStreamWaitEvent(s, b->ev_b, 0), "join");
+    }
+    return ISF_OK;
+}
+
+struct Item {
+    isf_lattice* L;
+    int64_t nsweeps;
+    ResPlan plan;
+    double work;
+};
+
+// ---- autotuner --------------------------------------------------------------------------------
+struct TuneKey {
+    std::string dev;
+    int cls, L, rh_bucket, ch_bucket;
+    bool operator==(const TuneKey& o) const {
+        return dev == o.dev && cls == o.cls && L == o.L && rh_bucket == o.rh_bucket && ch_bucket == o.ch_bucket;
+    }
+};
+struct TuneVal {
+    int K, threads;
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
+
+int bucket(int v) {
+    int b = 1;
+    while (b < v) b *= 2;
+    return b;
+}
+
+std::string device_name() {
+    int dev = 0;
+    cudaDeviceProp p{};
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+    return p.name;
+}
+
+// Time `sweeps` sweeps of a throw-away copy of film L with the resident kernel at (K, threads).
+double probe(const isf_lattice* L, int K, int threads, int sweeps, cudaStream_t s) {
+    isf_lattice* P = nullptr;
+    if (isf_lattice_create(L->heights.data(), L->lay.R, L->lay.C, L->lay.L, L->lay.flags, L->seed, 0, s, &P)) return -1;
+    const double T = L->nsteps ? L->T[L->nsteps / 2] : 3.0, h = 0.0;
+    const int32_t eq = 0, meas = sweeps;
+    double best = -1;
+    if (!isf_set_schedule(P, 1, &T, &h, &eq, &meas, 1.0, 0.0) && !isf_set_path(P, ISF_PATH_RESIDENT) &&
+        !isf_set_launch(P, K, threads)) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        for (int rep = 0; rep < 2; ++rep) {
+            isf_set_schedule(P, 1, &T, &h, &eq, &meas, 1.0, 0.0);
+            cudaEventRecord(a, s);
+            const int rc = isf_run_sweeps(P, -1, s);
+            cudaEventRecord(b, s);
+            if (rc || cudaEventSynchronize(b) != cudaSuccess) { best = -1; break; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, a, b);
+            if (rep > 0) best = ms;   // the first run warms the path
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+    isf_lattice_destroy(P);
+    cudaGetLastError();
+    return best;
+}
+
+}  // namespace
+
+extern "C" {
+
+int isf_batch_create(isf_batch** out) {
+    if (!out) return fail(ISF_ERR_ARG, "out is NULL");
+    *out = new (std::nothrow) isf_batch();
+    if (!*out) return fail(ISF_ERR_OOM, "host allocation failed");
+    return ISF_OK;
+}
+
+int isf_batch_add(isf_batch* b, isf_lattice* L) {
+    if (!b || !L) return fail(ISF_ERR_ARG, "bad arguments");
+    if (!L->nsteps) return fail(ISF_ERR_STATE, "the film has no schedule");
+    if (std::find(b->films.begin(), b->films.end(), L) != b->films.end()) return fail(ISF_ERR_ARG, "film already in the batch");
+    b->films.push_back(L);
+    return ISF_OK;
+}
+
+int isf_batch_clear(isf_batch* b) {
+    if (!b) return fail(ISF_ERR_ARG, "batch is NULL");
+    b->films.clear();
+    return ISF_OK;
+}
+
+int isf_batch_set_launch(isf_batch* b, int32_t threads_single, int32_t cluster_K, int32_t threads_cluster) {
+    if (!b || threads_single < 0 || cluster_K < 0 || cluster_K > 16 || threads_cluster < 0 ||
+        threads_single % 32 || threads_cluster % 32 || threads_single > 1024 || threads_cluster > 1024)
+        return fail(ISF_ERR_ARG, "threads: 0 or multiples of 32 up to 1024; cluster size 0..16");
+    b->threads_a = threads_single;
+    b->K_b = cluster_K;
+    b->threads_b = threads_cluster;
+    return ISF_OK;
+}
+
+int isf_batch_set_graph(isf_batch* b, int32_t on) {
+    if (!b) return fail(ISF_ERR_ARG, "batch is NULL");
+    b->use_graph = on != 0;
+    return ISF_OK;
+}
+
+int isf_batch_tune(isf_batch* b, void* cuda_stream) {
+    if (!b) return fail(ISF_ERR_ARG, "batch is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const std::string dev = device_name();
+    // representative films: the largest of each class
+    const isf_lattice* rep[2] = {nullptr, nullptr};
+    double rep_work[2] = {0, 0};
+    for (isf_lattice* L : b->films) {
+        if (L->lay.packed) continue;
+        ResPlan p;
+        const int cls = resident_plan(L->f, 1, 0, &p) == 0 ? 0 : (resident_plan(L->f, 16, 0, &p) == 0 ? 1 : -1);
+        cudaGetLastError();
+        if (cls < 0) continue;
+        const double w = (double)L->lay.L * L->lay.Rh * L->lay.Ch;
+        if (w > rep_work[cls]) { rep_work[cls] = w; rep[cls] = L; }
+    }
+    for (int cls = 0; cls < 2; ++cls) {
+        const isf_lattice* L = rep[cls];
+        if (!L) continue;
+        TuneKey key{dev, cls, L->lay.L, bucket(L->lay.Rh), bucket(L->lay.Ch)};
+        TuneVal best{cls ? kDefaultK : 1, cls ? kDefaultThreadsB : kDefaultThreadsA};
+        bool cached = false;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            for (auto& kv : g_tune_cache)
+                if (kv.first == key) { best = kv.second; cached = true; }
+        }
+        if (!cached) {
+            double best_t = 1e300;
+            const int Ks[2] = {8, 16};
+            const int ths[4] = {128, 256, 512, 1024};
+            for (int ki = 0; ki < (cls ? 2 : 1); ++ki)
+                for (int ti = 0; ti < 4; ++ti) {
+                    const int K = cls ? Ks[ki] : 1;
+                    const double t = probe(L, K, ths[ti], 20, s);
+                    if (t > 0 && t < best_t) { best_t = t; best = TuneVal{K, ths[ti]}; }
+                }
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tune_cache.push_back({key, best});
+        }
+        if (cls == 0) b->threads_a = best.threads;
+        else { b->K_b = best.K; b->threads_b = best.threads; }
+    }
+    return set_last_error(ISF_OK, "");
+}
+
+int isf_batch_run(isf_batch* b, void* cuda_stream) {
+    if (!b) return fail(ISF_ERR_ARG, "batch is NULL");
+    int rc = ensure_streams(b);
+    if (rc) return rc;
+    CUDA_TRY(cudaSetDevice(b->device), "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (b->pending) {   // the staging buffer may still be read by the previous run's upload
+        CUDA_TRY(cudaEventSynchronize(b->ev_done), "previous batch");
+        b->pending = false;
+    }
+    const int ta = b->threads_a ? b->threads_a : kDefaultThreadsA;
+    const int K = b->K_b ? b->K_b : kDefaultK;
+    const int tb = b->threads_b ? b->threads_b : kDefaultThreadsB;
+    std::vector<Item> A, B;
+    std::vector<isf_lattice*> C;
+    for (isf_lattice* L : b->films) {
+        if (L->device != b->device) return fail(ISF_ERR_ARG, "all films of a batch must be on one device");
+        const int64_t n = sweeps_remaining(L);
+        if (n <= 0) continue;
+        Item it{L, n, {}, (double)n * L->lay.L * L->lay.Rh * L->lay.Ch};
+        // the queue kernels hold int8 films without periodic columns
+        const bool queueable = !L->lay.packed && !(L->lay.flags & ISF_PERIODIC_X);
+        if (queueable && resident_plan(L->f, 1, ta, &it.plan) == 0) A.push_back(it);
+        else if (queueable && resident_plan(L->f, K, tb, &it.plan) == 0) B.push_back(it);
+        else C.push_back(L);
+        cudaGetLastError();
+    }
+    auto longest_first = [](const Item& x, const Item& y) { return x.work > y.work; };
+    std::sort(A.begin(), A.end(), longest_first);
+    std::sort(B.begin(), B.end(), longest_first);
+    const int n_a = (int)A.size(), n_b = (int)B.size();
+    rc = ensure_capacity(b, (size_t)n_a + n_b + 1);
+    if (rc) return rc;
+    uint32_t smem_a = 0, smem_b = 0;
+    for (int i = 0; i < n_a; ++i) {
+        b->h_desc[i] = make_res_args(sweep_args(A[i].L, A[i].nsweeps), A[i].plan);
+        smem_a = std::max(smem_a, A[i].plan.smem);
+    }
+    for (int i = 0; i < n_b; ++i) {
+        b->h_desc[n_a + i] = make_res_args(sweep_args(B[i].L, B[i].nsweeps), B[i].plan);
+        smem_b = std::max(smem_b, B[i].plan.smem);
+    }
+    int units_a = 0, units_b = 0;
+    if (n_a) {
+        int e = batch_units_possible(1, ta, smem_a, &units_a);
+        if (e || units_a < 1) return fail(ISF_ERR_CUDA, "single-CTA batch kernel cannot be resident");
+        units_a = std::min(units_a, n_a);
+    }
+    if (n_b) {
+        int e = batch_units_possible(K, tb, smem_b, &units_b);
+        if (e || units_b < 1) return fail(ISF_ERR_CUDA, "cluster batch kernel cannot be resident");
+        units_b = std::min(units_b, n_b);
+    }
+    if (n_a || n_b) {
+        const int64_t sig[8] = {n_a, n_b, K, ta, tb, (int64_t)smem_a << 32 | smem_b, units_a, units_b};
+        if (b->use_graph) {
+            if (!b->gexec || std::memcmp(sig, b->gsig, sizeof sig)) {
+                if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+                cudaGraph_t g = nullptr;
+                CUDA_TRY(cudaStreamBeginCapture(b->sc, cudaStreamCaptureModeRelaxed), "begin capture");
+                rc = enqueue(b, b->sc, n_a, n_b, K, ta, tb, smem_a, smem_b, units_a, units_b);
+                cudaError_t ce = cudaStreamEndCapture(b->sc, &g);
+                if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+                if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
+                ce = cudaGraphInstantiate(&b->gexec, g, 0);
+                cudaGraphDestroy(g);
+                if (ce != cudaSuccess) { b->gexec = nullptr; return cuda_fail(ce, "graph instantiate"); }
+                std::memcpy(b->gsig, sig, sizeof sig);
+            }
+            CUDA_TRY(cudaGraphLaunch(b->gexec, s), "graph launch");
+        } else {
+            rc = enqueue(b, s, n_a, n_b, K, ta, tb, smem_a, smem_b, units_a, units_b);
+            if (rc) return rc;
+        }
+        CUDA_TRY(cudaEventRecord(b->ev_done, s), "batch done");
+        b->pending = true;
+    }
+    for (const Item& it : A) {
+        advance_cursor(it.L, it.nsweeps);
+        it.L->last = s;
+        it.L->last_path = ISF_PATH_RESIDENT; it.L->last_ctas = 1; it.L->last_threads = ta;
+    }
+    for (const Item& it : B) {
+        advance_cursor(it.L, it.nsweeps);
+        it.L->last = s;
+        it.L->last_path = ISF_PATH_RESIDENT; it.L->last_ctas = K; it.L->last_threads = tb;
+    }
+    for (isf_lattice* L : C) {
+        const int32_t saved = L->path;
+        L->path = ISF_PATH_GLOBAL;
+        rc = isf_run_sweeps(L, -1, s);
+        L->path = saved;
+        if (rc) return rc;
+    }
+    b->n_a = n_a; b->n_b = n_b; b->n_c = (int)C.size();
+    b->units_a = units_a; b->units_b = units_b;
+    b->used_K = K; b->used_ta = ta; b->used_tb = tb;
+    return set_last_error(ISF_OK, "");
+}
+
+int isf_batch_info(isf_batch* b, int32_t* out8) {
+    if (!b || !out8) return fail(ISF_ERR_ARG, "bad arguments");
+    const int32_t v[8] = {b->n_a, b->n_b, b->n_c, b->units_a, b->units_b, b->used_K, b->used_ta, b->used_tb};
+    std::memcpy(out8, v, sizeof v);
+    return ISF_OK;
+}
+
+void isf_batch_destroy(isf_batch* b) {
+    if (!b) return;
+    if (b->sa) {
+        cudaSetDevice(b->device);
+        if (b->pending) cudaEventSynchronize(b->ev_done);
+        if (b->gexec) cudaGraphExecDestroy(b->gexec);
+        cudaStreamDestroy(b->sa);
+        cudaStreamDestroy(b->sb);
+        cudaStreamDestroy(b->sc);
+        cudaEventDestroy(b->ev_fork);
+        cudaEventDestroy(b->ev_a);
+        cudaEventDestroy(b->ev_b);
+        cudaEventDestroy(b->ev_done);
+        if (b->d_desc) cudaFree(b->d_desc);
+        if (b->h_desc) cudaFreeHost(b->h_desc);
+        if (b->d_next) cudaFree(b->d_next);
+    }
+    delete b;
+}
+
+}  // extern "C"

@@ -9,44 +9,9 @@
 #include <string>
 #include <vector>
 
-#include "isf_internal.h"
-#include "../../include/isingfilm.h"
+#include "capi_internal.h"
 
 using namespace isf;
-
-struct isf_lattice {
-    Layout lay{};
-    uint64_t seed = 0;
-    int32_t init = 0;
-    int device = 0;
-    uint8_t* dev = nullptr;         // film buffer: spins | heights | state
-    bool owns_dev = false;
-    DevFilm f{};
-    FilmState* st = nullptr;
-    std::vector<uint8_t> heights;   // host copy (validation of written spins, save)
-    int64_t n_occ = 0, n_bonds = 0;
-    int64_t sweep = 0;              // Metropolis sweeps done
-    // schedule
-    int32_t nsteps = 0;
-    std::vector<double> T, h;
-    std::vector<int32_t> eq, tot;
-    double J = 1.0, h_s = 0.0;
-    bool use_gate = false;
-    uint8_t* sched = nullptr;       // tables | eq | tot | records
-    uint32_t* d_tables = nullptr;
-    int32_t* d_eq = nullptr;
-    int32_t* d_tot = nullptr;
-    StepRec* d_recs = nullptr;
-    int32_t k = 0, pos = 0;         // cursor: step, sweeps done in it
-    // trace
-    long long* d_trace = nullptr;
-    int64_t trace_cap = 0, trace_n = 0;
-    // launch shape and path
-    int32_t ctas = 0, threads = 0;
-    int32_t path = ISF_PATH_AUTO;
-    int32_t last_path = 0, last_ctas = 0, last_threads = 0;   // shape of the last sweep launch
-    cudaStream_t last = nullptr;
-};
 
 namespace {
 
@@ -82,6 +47,11 @@ void free_schedule(isf_lattice* L) {
 int sync_film(isf_lattice* L) {
     CUDA_TRY(cudaSetDevice(L->device), "cudaSetDevice");
     CUDA_TRY(L->last ? cudaStreamSynchronize(L->last) : cudaDeviceSynchronize(), "synchronise");
+    unsigned long long chk[4];
+    CUDA_TRY((cudaError_t)read_checks(chk), "read checks");
+    if (chk[0])
+        return fail(ISF_ERR_STATE, "a resident kernel skipped an out-of-range access (check " + std::to_string(chk[0]) +
+                                       ": " + std::to_string(chk[1]) + ", " + std::to_string(chk[2]) + ")");
     int err = 0, where = 0;
     CUDA_TRY(cudaMemcpy(&err, &L->st->error, sizeof(int), cudaMemcpyDeviceToHost), "read status");
     if (err) {
@@ -181,6 +151,43 @@ int set_last_error(int code, const char* msg) {
     g_err = msg;
     return code;
 }
+
+int64_t sweeps_remaining(const isf_lattice* L) {
+    int64_t r = 0;
+    for (int32_t k = L->k; k < L->nsteps; ++k) r += L->tot[k];
+    return r - L->pos;
+}
+
+SweepArgs sweep_args(const isf_lattice* L, int64_t nsweeps) {
+    SweepArgs a{};
+    a.f = L->f;
+    a.st = L->st;
+    a.tables = L->d_tables;
+    a.step_eq = L->d_eq;
+    a.step_total = L->d_tot;
+    a.recs = L->d_recs;
+    a.trace = L->d_trace;
+    a.trace_begin = L->trace_n;
+    a.trace_cap = L->trace_cap;
+    a.sweep0 = L->sweep;
+    a.nsweeps = nsweeps;
+    a.k0 = L->k;
+    a.pos0 = L->pos;
+    a.nsteps = L->nsteps;
+    a.use_gate = L->use_gate ? 1 : 0;
+    return a;
+}
+
+void advance_cursor(isf_lattice* L, int64_t nsweeps) {
+    L->sweep += nsweeps;
+    if (L->d_trace) L->trace_n = std::min<int64_t>(L->trace_cap, L->trace_n + nsweeps);
+    int64_t left = nsweeps;
+    while (left > 0) {
+        const int64_t room = L->tot[L->k] - L->pos;
+        if (left >= room) { left -= room; L->k += 1; L->pos = 0; }
+        else { L->pos += (int32_t)left; left = 0; }
+    }
+}
 }  // namespace isf
 
 extern "C" {
@@ -271,30 +278,13 @@ int isf_set_schedule(isf_lattice* L, int32_t nsteps, const double* T, const doub
 int isf_run_sweeps(isf_lattice* L, int64_t nsweeps, void* cuda_stream) {
     if (!L) return fail(ISF_ERR_ARG, "lattice is NULL");
     if (!L->nsteps) return fail(ISF_ERR_STATE, "no schedule set");
-    int64_t remaining = 0;
-    for (int32_t k = L->k; k < L->nsteps; ++k) remaining += L->tot[k];
-    remaining -= L->pos;
+    const int64_t remaining = sweeps_remaining(L);
     if (nsweeps == -1) nsweeps = remaining;
     if (nsweeps < 0) return fail(ISF_ERR_ARG, "nsweeps must be >= 0 or -1");
     if (nsweeps > remaining) return fail(ISF_ERR_SCHEDULE, "past the end of the schedule");
     if (nsweeps == 0) return ISF_OK;
     CUDA_TRY(cudaSetDevice(L->device), "cudaSetDevice");
-    SweepArgs a{};
-    a.f = L->f;
-    a.st = L->st;
-    a.tables = L->d_tables;
-    a.step_eq = L->d_eq;
-    a.step_total = L->d_tot;
-    a.recs = L->d_recs;
-    a.trace = L->d_trace;
-    a.trace_begin = L->trace_n;
-    a.trace_cap = L->trace_cap;
-    a.sweep0 = L->sweep;
-    a.nsweeps = nsweeps;
-    a.k0 = L->k;
-    a.pos0 = L->pos;
-    a.nsteps = L->nsteps;
-    a.use_gate = L->use_gate ? 1 : 0;
+    const SweepArgs a = sweep_args(L, nsweeps);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     bool launched = false;
     if (L->path != ISF_PATH_GLOBAL && !L->lay.packed) {
@@ -328,14 +318,7 @@ int isf_run_sweeps(isf_lattice* L, int64_t nsweeps, void* cuda_stream) {
         L->last_path = ISF_PATH_GLOBAL; L->last_ctas = ctas; L->last_threads = threads;
     }
     L->last = s;
-    L->sweep += nsweeps;
-    if (L->d_trace) L->trace_n = std::min<int64_t>(L->trace_cap, L->trace_n + nsweeps);
-    int64_t left = nsweeps;
-    while (left > 0) {
-        const int64_t room = L->tot[L->k] - L->pos;
-        if (left >= room) { left -= room; L->k += 1; L->pos = 0; }
-        else { L->pos += (int32_t)left; left = 0; }
-    }
+    advance_cursor(L, nsweeps);
     return ISF_OK;
 }
 
@@ -465,6 +448,15 @@ int isf_set_launch(isf_lattice* L, int32_t ctas, int32_t threads) {
         return fail(ISF_ERR_ARG, "threads must be 0 or a multiple of 32 in 32..1024");
     L->ctas = ctas;
     L->threads = threads;
+    return ISF_OK;
+}
+
+int isf_debug_checks(uint64_t* out4) {
+    if (!out4) return fail(ISF_ERR_ARG, "out is NULL");
+    unsigned long long v[4];
+    int e = read_checks(v);
+    if (e) return cuda_fail((cudaError_t)e, "read checks");
+    for (int i = 0; i < 4; ++i) out4[i] = v[i];
     return ISF_OK;
 }
 

@@ -1,0 +1,60 @@
+// capi_internal.h — the library's film object and helpers shared by the C-ABI translation
+// units (capi.cpp, batch.cpp).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "isf_internal.h"
+#include "../../include/isingfilm.h"
+
+using isf::Layout;
+using isf::DevFilm;
+using isf::FilmState;
+using isf::StepRec;
+
+struct isf_lattice {
+    Layout lay{};
+    uint64_t seed = 0;
+    int32_t init = 0;
+    int device = 0;
+    uint8_t* dev = nullptr;         // film buffer: spins | heights | state
+    bool owns_dev = false;
+    DevFilm f{};
+    FilmState* st = nullptr;
+    std::vector<uint8_t> heights;   // host copy (validation of written spins, save)
+    int64_t n_occ = 0, n_bonds = 0;
+    int64_t sweep = 0;              // Metropolis sweeps done
+    // schedule
+    int32_t nsteps = 0;
+    std::vector<double> T, h;
+    std::vector<int32_t> eq, tot;
+    double J = 1.0, h_s = 0.0;
+    bool use_gate = false;
+    uint8_t* sched = nullptr;       // tables | eq | tot | records
+    uint32_t* d_tables = nullptr;
+    int32_t* d_eq = nullptr;
+    int32_t* d_tot = nullptr;
+    StepRec* d_recs = nullptr;
+    int32_t k = 0, pos = 0;         // cursor: step, sweeps done in it
+    // trace
+    long long* d_trace = nullptr;
+    int64_t trace_cap = 0, trace_n = 0;
+    // launch shape and path
+    int32_t ctas = 0, threads = 0;
+    int32_t path = ISF_PATH_AUTO;
+    int32_t last_path = 0, last_ctas = 0, last_threads = 0;   // shape of the last sweep launch
+    cudaStream_t last = nullptr;
+};
+
+
+namespace isf {
+int set_last_error(int code, const char* msg);
+// Sweep arguments for the next nsweeps of the film's schedule (no device work).
+SweepArgs sweep_args(const isf_lattice* L, int64_t nsweeps);
+// Sweeps left in the film's schedule.
+int64_t sweeps_remaining(const isf_lattice* L);
+// Move the film's schedule cursor, sweep counter and trace cursor past nsweeps sweeps.
+void advance_cursor(isf_lattice* L, int64_t nsweeps);
+}  // namespace isf

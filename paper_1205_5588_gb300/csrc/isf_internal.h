@@ -142,6 +142,23 @@ struct ResPlan {
 // Returns 0 and fills out when the film fits, else a nonzero code (no device work).
 int resident_plan(const DevFilm& f, int want_K, int want_threads, ResPlan* out);
 int launch_resident(const SweepArgs& a, const ResPlan& plan, void* stream);
+
+// One film's launch arguments for the resident kernels (also the batch queue's entries).
+struct alignas(16) ResArgs {
+    SweepArgs s;
+    int32_t K, Jb;
+    uint32_t film_off, vac_off, ptr_off, misc_off;
+};
+static_assert(sizeof(ResArgs) % 16 == 0, "ResArgs is copied in 16-byte words");
+ResArgs make_res_args(const SweepArgs& a, const ResPlan& p);
+// First out-of-range access a resident / batch kernel skipped (all zeros when none).
+int read_checks(unsigned long long out[4]);
+
+// Batched films (kernels_resident.cu): a persistent launch of `units` CTAs (K = 1) or clusters
+// of K CTAs, each taking films from the device queue `films[0..n)` via the counter *next.
+int batch_units_possible(int K, int threads, uint32_t smem, int* units);
+int launch_batch(const ResArgs* films, int n, unsigned* next, int K, int threads, uint32_t smem,
+                 int units, void* stream);
 int sweep_items_per_pass(const DevFilm& f);                            // work items per colour pass
 
 }  // namespace isf

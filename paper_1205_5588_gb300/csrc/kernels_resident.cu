@@ -20,21 +20,36 @@
 
 namespace isf {
 
+// The resident and batch kernels check every address they compute from a film's descriptor
+// before using it: an out-of-range access is recorded here (first one: code, two values) and
+// skipped instead of made; the host reports it on its next read of the film.
+__device__ unsigned long long g_isf_check[4];
+#define ISF_CHECK(cond, code, v1, v2)                                                        \
+    ((cond) ? true : (atomicCAS(&g_isf_check[0], 0ull, (unsigned long long)(code)) == 0ull     \
+                          ? (g_isf_check[1] = (unsigned long long)(v1),                        \
+                             g_isf_check[2] = (unsigned long long)(v2), false)                 \
+                          : false))
+
 namespace {
 
 constexpr int kMaxK = 16;
 constexpr uint32_t kMiscBytes = 128 * 4 + 16 + 64 * 8 + 2 * kMaxK * 8 + kMaxK * 8;
 
-struct ResArgs {
-    SweepArgs s;
-    int32_t K, Jb;
-    uint32_t film_off, vac_off, ptr_off, misc_off;
-};
 
 __device__ __forceinline__ unsigned cluster_rank() {
     unsigned r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
     return r;
+}
+__device__ __forceinline__ unsigned dyn_smem_bytes() {
+    unsigned n;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(n));
+    return n;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned n;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+    return n;
 }
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -46,15 +61,18 @@ __device__ __forceinline__ uint8_t* map_rank(uint8_t* p, unsigned rank) {
     return reinterpret_cast<uint8_t*>(out);
 }
 
+__device__ __forceinline__ int64_t film_bytes_or(const DevFilm& f) { return 4 * f.cs8; }
+
 template <bool CLUSTER>
 __device__ __forceinline__ void sync_all() {
     if (CLUSTER) cluster_sync_all();
     else __syncthreads();
 }
 
+// One film on this CTA (CLUSTER = false) or on this cluster: slab in, the launch's sweeps,
+// slab out.  Ends with a barrier over all CTAs that took part.
 template <bool CLUSTER, bool PX>
-__global__ void __launch_bounds__(1024, 1) k_resident(const __grid_constant__ ResArgs a) {
-    extern __shared__ __align__(16) uint8_t sm[];
+__device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
     const SweepArgs& s = a.s;
     const DevFilm& f = s.f;
     const unsigned K = CLUSTER ? (unsigned)a.K : 1u;
@@ -62,7 +80,7 @@ __global__ void __launch_bounds__(1024, 1) k_resident(const __grid_constant__ Re
     const int Jb = a.Jb, L = f.L, Rh = f.Rh, nck = f.nck, Ch = f.Ch;
     const int P = (int)f.P;
     const int j0 = (int)rank * Jb;
-    const int nown = min(Jb, Rh - j0);
+    const int nown = max(0, min(Jb, Rh - j0));      // trailing CTAs may own no rows
     uint8_t* film = sm + a.film_off;
     uint8_t* vac = sm + a.vac_off;
     uint8_t** ptrs = reinterpret_cast<uint8_t**>(sm + a.ptr_off);
@@ -74,12 +92,21 @@ __global__ void __launch_bounds__(1024, 1) k_resident(const __grid_constant__ Re
 
     // slab in, vacancy row, every rank's slab address
     const int words = P / 16;
+    const uint64_t smem_n = dyn_smem_bytes();
+    bool desc_ok = ISF_CHECK(K >= 1 && K <= 16 && Jb >= 1 && (int64_t)Jb * K >= Rh && P % 16 == 0, 1, K, Jb);
+    desc_ok = desc_ok && ISF_CHECK(a.misc_off + 1424 <= smem_n, 2, a.misc_off, smem_n);
+    desc_ok = desc_ok && ISF_CHECK((uint64_t)a.ptr_off + (uint64_t)4 * L * Jb * 96 <= a.misc_off, 3, a.ptr_off, a.misc_off);
+    desc_ok = desc_ok && ISF_CHECK(s.k0 >= 0 && s.k0 < s.nsteps && s.nsteps >= 1, 4, s.k0, s.nsteps);
+    if (!desc_ok) { sync_all<CLUSTER>(); sync_all<CLUSTER>(); return; }
     for (int t = threadIdx.x; t < 4 * L * nown * words; t += blockDim.x) {
         const int w = t % words;
         const int rr = t / words;
         const int jl = rr % nown, cz = rr / nown;
-        const uint4* src = reinterpret_cast<const uint4*>(f.s8 + addr8(f, cz / L, cz % L, j0 + jl, -16));
-        reinterpret_cast<uint4*>(film + ((size_t)cz * Jb + jl) * P)[w] = src[w];
+        const int64_t off = addr8(f, cz / L, cz % L, j0 + jl, -16) + 16 * w;
+        const uint64_t dsm = (uint64_t)a.film_off + ((uint64_t)cz * Jb + jl) * P + 16 * w;
+        if (!ISF_CHECK(off >= 0 && off + 16 <= film_bytes_or(f), 5, off, film_bytes_or(f))) continue;
+        if (!ISF_CHECK(dsm + 16 <= a.vac_off, 6, dsm, a.vac_off)) continue;
+        reinterpret_cast<uint4*>(film + ((size_t)cz * Jb + jl) * P)[w] = *reinterpret_cast<const uint4*>(f.s8 + off);
     }
     for (int t = threadIdx.x; t < P / 4; t += blockDim.x) reinterpret_cast<uint32_t*>(vac)[t] = 0x01010101u;
     if (threadIdx.x < K) base[threadIdx.x] = CLUSTER ? map_rank(film, threadIdx.x) : film;
@@ -111,6 +138,7 @@ __global__ void __launch_bounds__(1024, 1) k_resident(const __grid_constant__ Re
         uint8_t* p = vac;
         if (inside) {
             const int rk = jj / Jb;
+            if (!ISF_CHECK(rk >= 0 && rk < (int)K && nc.c2[k] >= 0 && nc.c2[k] < 4, 7, rk, nc.c2[k])) continue;
             p = base[rk] + ((size_t)(nc.c2[k] * L + zz) * Jb + (jj - rk * Jb)) * P;
         }
         ptrs[((size_t)cz * Jb + jl) * 12 + k] = p;
@@ -119,7 +147,7 @@ __global__ void __launch_bounds__(1024, 1) k_resident(const __grid_constant__ Re
 
     const int items = L * nown * nck;
     ItemWalk walk0;
-    walk0.init(threadIdx.x, blockDim.x, nck, nown);
+    walk0.init(threadIdx.x, blockDim.x, nck, nown > 0 ? nown : 1);
     int k = s.k0, pos = s.pos0;
     const bool folder = rank == 0 && threadIdx.x == 0;
     __shared__ RunState rs;     // touched by the folding thread only
@@ -145,6 +173,7 @@ __global__ void __launch_bounds__(1024, 1) k_resident(const __grid_constant__ Re
             for (int it = threadIdx.x; it < items; it += blockDim.x, w.next()) {
                 const int ck = w.ck, jl = w.jr, z = w.z;
                 const size_t r = (size_t)(c * L + z) * Jb + jl;
+                if (!ISF_CHECK(z >= 0 && z < L && jl >= 0 && jl < nown && ck >= 0 && ck < nck, 8, it, ((uint64_t)z << 32) | (uint32_t)jl)) continue;
                 uint8_t* row = film + r * P;
                 uint8_t* own = row + 16 + 16 * ck;
                 uint8_t* const* pr = ptrs + r * 12;
@@ -170,7 +199,7 @@ __global__ void __launch_bounds__(1024, 1) k_resident(const __grid_constant__ Re
             }
             sync_all<CLUSTER>();
         }
-        if (folder) {
+        if (folder && ISF_CHECK(k >= 0 && k < s.nsteps, 10, k, s.nsteps)) {
             long long sM = 0, sB = 0;
             for (unsigned r = 0; r < K; ++r) { sM += slots[2 * r]; sB += slots[2 * r + 1]; }
             fold_sweep(s, rs, k, pos, k_eq, k_tot, sM, sB, t);
@@ -192,10 +221,44 @@ __global__ void __launch_bounds__(1024, 1) k_resident(const __grid_constant__ Re
             const int b = Ch & 15;
             vw[b >> 2] = (vw[b >> 2] & ~(0xFFu << (8 * (b & 3)))) | (0x01u << (8 * (b & 3)));
         }
-        uint8_t* dst = f.s8 + addr8(f, cz / L, cz % L, j0 + jl, 0);
-        reinterpret_cast<uint4*>(dst)[w] = v;
+        const int64_t off = addr8(f, cz / L, cz % L, j0 + jl, 0) + 16 * w;
+        if (!ISF_CHECK(off >= 16 && off + 16 <= film_bytes_or(f), 9, off, film_bytes_or(f))) continue;
+        *reinterpret_cast<uint4*>(f.s8 + off) = v;
     }
     sync_all<CLUSTER>();    // no CTA leaves while another may still address its shared memory
+}
+
+template <bool CLUSTER, bool PX>
+__global__ void __launch_bounds__(1024, 1) k_resident(const __grid_constant__ ResArgs a) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    run_film<CLUSTER, PX>(a, sm);
+}
+
+// Batched films: every CTA (or cluster) takes the next film of the queue, runs its sweeps with
+// the film resident in its shared memory, and takes another until the queue is empty.  Films
+// are independent Markov chains (each its own seed, schedule and state), so no film waits on
+// another; the queue is a device counter.
+template <bool CLUSTER>
+__global__ void __launch_bounds__(1024, 1) k_batch(const ResArgs* films, int nfilms, unsigned* next) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    __shared__ int film_s;
+    const unsigned rank = CLUSTER ? cluster_rank() : 0u;
+    const unsigned K = CLUSTER ? cluster_size() : 1u;
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) {
+            const int idx = (int)atomicAdd(next, 1u);
+            for (unsigned r = 0; r < K; ++r) {
+                int* dst = CLUSTER ? reinterpret_cast<int*>(map_rank(reinterpret_cast<uint8_t*>(&film_s), r)) : &film_s;
+                *dst = idx;
+            }
+        }
+        sync_all<CLUSTER>();
+        const int idx = film_s;
+        if (idx >= nfilms || !ISF_CHECK(idx >= 0, 11, idx, nfilms)) break;
+        // the descriptor is read in place (it does not change during the launch); films with
+        // periodic columns are not queued here
+        run_film<CLUSTER, false>(films[idx], sm);
+    }
 }
 
 template <bool CLUSTER, bool PX>
@@ -252,8 +315,7 @@ inline uint32_t round16(uint32_t v) { return (v + 15u) & ~15u; }
 
 bool layout_for(const DevFilm& f, int K, int threads, int max_smem, ResPlan* out) {
     if (K < 1 || K > kMaxK || K > f.Rh) return false;
-    const int Jb = (f.Rh + K - 1) / K;
-    if ((K - 1) * Jb >= f.Rh) return false;      // every CTA owns at least one row
+    const int Jb = (f.Rh + K - 1) / K;           // the last CTAs may own fewer rows, or none
     const uint64_t rows = (uint64_t)4 * f.L * Jb;
     ResPlan p{};
     p.K = K;
@@ -316,7 +378,11 @@ int resident_plan(const DevFilm& f, int want_K, int want_threads, ResPlan* out) 
     return 3;
 }
 
-int launch_resident(const SweepArgs& a, const ResPlan& p, void* stream) {
+int read_checks(unsigned long long out[4]) {
+    return (int)cudaMemcpyFromSymbol(out, g_isf_check, 4 * sizeof(unsigned long long));
+}
+
+ResArgs make_res_args(const SweepArgs& a, const ResPlan& p) {
     ResArgs ra{};
     ra.s = a;
     ra.K = p.K;
@@ -325,6 +391,69 @@ int launch_resident(const SweepArgs& a, const ResPlan& p, void* stream) {
     ra.vac_off = p.vac_off;
     ra.ptr_off = p.ptr_off;
     ra.misc_off = p.misc_off;
+    return ra;
+}
+
+namespace {
+template <bool CLUSTER>
+cudaLaunchConfig_t batch_config(int K, int threads, uint32_t smem, int units, cudaStream_t s,
+                                cudaLaunchAttribute* attr, cudaError_t* err) {
+    auto kern = k_batch<CLUSTER>;
+    *err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (*err == cudaSuccess && CLUSTER && K > 8)
+        *err = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(units * (CLUSTER ? K : 1));
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    if (CLUSTER) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = K;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cfg;
+}
+}  // namespace
+
+int batch_units_possible(int K, int threads, uint32_t smem, int* units) {
+    cudaError_t e;
+    cudaLaunchAttribute attr[1];
+    if (K > 1) {
+        cudaLaunchConfig_t cfg = batch_config<true>(K, threads, smem, 1, nullptr, attr, &e);
+        if (e != cudaSuccess) return (int)e;
+        return (int)cudaOccupancyMaxActiveClusters(units, k_batch<true>, &cfg);
+    }
+    cudaLaunchConfig_t cfg = batch_config<false>(1, threads, smem, 1, nullptr, attr, &e);
+    if (e != cudaSuccess) return (int)e;
+    int per = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<false>, threads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    *units = per * sms;
+    return (int)e;
+}
+
+int launch_batch(const ResArgs* films, int n, unsigned* next, int K, int threads, uint32_t smem, int units,
+                 void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    cudaLaunchAttribute attr[1];
+    if (K > 1) {
+        cudaLaunchConfig_t cfg = batch_config<true>(K, threads, smem, units, s, attr, &e);
+        if (e != cudaSuccess) return (int)e;
+        return (int)cudaLaunchKernelEx(&cfg, k_batch<true>, films, n, next);
+    }
+    cudaLaunchConfig_t cfg = batch_config<false>(1, threads, smem, units, s, attr, &e);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaLaunchKernelEx(&cfg, k_batch<false>, films, n, next);
+}
+
+int launch_resident(const SweepArgs& a, const ResPlan& p, void* stream) {
+    ResArgs ra = make_res_args(a, p);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool px = (a.f.flags & 1u) != 0;
     if (p.K > 1) return px ? launch_variant<true, true>(ra, p, s) : launch_variant<true, false>(ra, p, s);

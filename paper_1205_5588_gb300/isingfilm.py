@@ -64,6 +64,15 @@ def _declare(lib):
         "isf_lattice_destroy": (None, [vp]),
         "isf_last_error": (C.c_char_p, []),
         "isf_philox_blocks": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, C.c_int64, u32p]),
+        "isf_batch_create": (C.c_int, [C.POINTER(vp)]),
+        "isf_batch_add": (C.c_int, [vp, vp]),
+        "isf_batch_clear": (C.c_int, [vp]),
+        "isf_batch_set_launch": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_int32]),
+        "isf_batch_set_graph": (C.c_int, [vp, C.c_int32]),
+        "isf_batch_tune": (C.c_int, [vp, vp]),
+        "isf_batch_run": (C.c_int, [vp, vp]),
+        "isf_batch_info": (C.c_int, [vp, i32p]),
+        "isf_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -267,6 +276,58 @@ class Lattice:
             rows, cols, layers, flags = (int(v) for v in hdr[:4])
             heights = np.frombuffer(fp.read(rows * cols), dtype=np.uint8).reshape(rows, cols).copy()
         return cls._wrap(h, rows, cols, layers, flags, heights)
+
+
+class Batch:
+    """Many films advanced together (isf_batch_*); it references, not owns, its lattices."""
+
+    def __init__(self, films=(), graph=False):
+        h = C.c_void_p()
+        _check(lib.isf_batch_create(C.byref(h)), "batch_create")
+        self._h = h
+        self.films = []
+        if graph:
+            self.set_graph(True)
+        for f in films:
+            self.add(f)
+
+    def add(self, lat: Lattice):
+        _check(lib.isf_batch_add(self._h, lat._h), "batch_add")
+        self.films.append(lat)
+
+    def clear(self):
+        _check(lib.isf_batch_clear(self._h), "batch_clear")
+        self.films = []
+
+    def set_launch(self, threads_single=0, cluster_K=0, threads_cluster=0):
+        _check(lib.isf_batch_set_launch(self._h, threads_single, cluster_K, threads_cluster), "batch_set_launch")
+
+    def set_graph(self, on=True):
+        _check(lib.isf_batch_set_graph(self._h, 1 if on else 0), "batch_set_graph")
+
+    def tune(self, stream=None):
+        _check(lib.isf_batch_tune(self._h, _stream_handle(stream)), "batch_tune")
+
+    def run(self, stream=None):
+        _check(lib.isf_batch_run(self._h, _stream_handle(stream)), "batch_run")
+
+    def info(self) -> dict:
+        v = (C.c_int32 * 8)()
+        _check(lib.isf_batch_info(self._h, v), "batch_info")
+        keys = ("single_cta_films", "cluster_films", "global_films", "ctas", "clusters", "cluster_K",
+                "threads_single", "threads_cluster")
+        return dict(zip(keys, list(v)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.isf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def philox_blocks(seed, stream, sweep, q0, n) -> np.ndarray:

@@ -1,0 +1,96 @@
+"""Batched films on the GPU: every film of a mixed batch (single-CTA, cluster and global-path
+films, int8 and packed, open and periodic, different seeds and schedules) ends exactly where the
+oracle and where the film run alone end, with and without graph replay and autotuning."""
+import numpy as np
+import pytest
+
+from paper_1205_5588_gb300 import workloads as W
+from tests.gpu_common import assert_records_equal, gpu_lib, oracle_flags, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def I():
+    return gpu_lib()
+
+
+def mixed_films():
+    rng = np.random.Generator(np.random.PCG64(77))
+    films = []
+    shapes = [(40, 52, 3, {}), (64, 64, 2, {}), (17, 23, 5, {}), (96, 130, 4, {}),
+              (200, 256, 4, {}),                     # needs a cluster
+              (150, 310, 5, {}),                     # needs a cluster
+              (48, 64, 3, {"packed": True}),         # global path
+              (16, 16, 3, {"periodic_x": True, "periodic_y": True}),
+              (8, 12, 2, {}), (33, 65, 6, {})]
+    for i, (R, Cc, L, extra) in enumerate(shapes):
+        if extra.get("periodic_x"):
+            H = np.full((R, Cc), L, dtype=np.uint8)
+        else:
+            H = W.fractal_heights(R, Cc, float(rng.uniform(0.5, 0.9)), 1, L, seed=500 + i)
+        nst = int(rng.integers(2, 5))
+        T = rng.uniform(1.0, 8.0, size=nst)
+        h = rng.uniform(-2.0, 2.0, size=nst)
+        eq = rng.integers(0, 3, size=nst)
+        me = rng.integers(2, 7, size=nst)
+        f = {"heights": H, "layers": L, "seed": 900 + i, "init": "random", "schedule": W.schedule(T, h, eq, me)}
+        f.update(extra)
+        films.append(f)
+    return films
+
+
+def make(I, f):
+    lat = I.Lattice(f["heights"], f["layers"], seed=f["seed"], init=f["init"], packed=f.get("packed", False),
+                    periodic_x=f.get("periodic_x", False), periodic_y=f.get("periodic_y", False))
+    s = f["schedule"]
+    lat.set_schedule(s["T"], s["h"], s["eq"], s["meas"])
+    return lat
+
+
+@pytest.mark.parametrize("graph,tune", [(False, False), (True, False), (False, True)])
+def test_batch_matches_oracle_and_solo(I, graph, tune):
+    films = mixed_films()
+    lats = [make(I, f) for f in films]
+    b = I.Batch(lats, graph=graph)
+    if tune:
+        b.tune()
+    b.run()
+    info = b.info()
+    assert info["single_cta_films"] >= 5 and info["cluster_films"] >= 2 and info["global_films"] >= 1, info
+    for f, lat in zip(films, lats):
+        o = run_oracle(f, f["schedule"])
+        assert_records_equal(lat.observables(), o["recs"])
+        assert np.array_equal(lat.spins(), o["spins"])
+        st = lat.state(recompute=True)
+        assert st["M"] == st["M_full"] and st["B"] == st["B_full"]
+    # replay: new schedules for every film, same batch (graph replay when enabled)
+    for f, lat in zip(films, lats):
+        s = f["schedule"]
+        lat.set_schedule(s["T"][::-1].copy(), s["h"], s["eq"], s["meas"])
+    b.run()
+    for f, lat in zip(films, lats):
+        solo = make(I, f)
+        solo.run(-1)
+        s = f["schedule"]
+        solo.set_schedule(s["T"][::-1].copy(), s["h"], s["eq"], s["meas"])
+        solo.run(-1)
+        assert_records_equal(lat.observables(), solo.observables())
+        assert np.array_equal(lat.spins(), solo.spins())
+        solo.close()
+    b.close()
+    for lat in lats:
+        lat.close()
+
+
+def test_batch_of_one_and_empty(I):
+    f = mixed_films()[0]
+    lat = make(I, f)
+    b = I.Batch([lat])
+    b.run()
+    b.run()            # nothing left: a no-op
+    assert_records_equal(lat.observables(), run_oracle(f, f["schedule"])["recs"])
+    b.clear()
+    b.run()
+    b.close()
+    lat.close()
