@@ -219,12 +219,115 @@ def run_impl(args):
                      "ops_per_attempt": OPS_PER_ATTEMPT},
         "clocks": clk,
     }
+    if rank == 0 and not args.no_batched:
+        line["batched"] = measure_batched(I, n_films=args.batch_films, sweeps_per_step=args.batch_sweeps)
+    if rank == 0 and not args.no_served:
+        line["served"] = measure_served(I, rate=args.serve_rate, duration=args.serve_seconds)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, budget_s=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def measure_batched(I, n_films=128, sweeps_per_step=20, seed=4, plain=True):
+    """Batched films (ragged sizes 64..1024, 1..8 layers, own T and field loop each) advanced to
+    the end of their schedules by isf_batch_run, against the same films run one per launch."""
+    import torch
+    from paper_1205_5588_gb300 import workloads as W
+    films = W.batch_films(n_films, seed=seed, sweeps_per_step=sweeps_per_step)
+    lats = []
+    for f in films:
+        L = I.Lattice(f["heights"], f["layers"], seed=f["seed"])
+        lats.append(L)
+    att = sum(L.info()["n_occ"] * int(f["schedule"]["eq"].sum() + f["schedule"]["meas"].sum())
+              for L, f in zip(lats, films))
+
+    def reset():
+        for L, f in zip(lats, films):
+            sc = f["schedule"]
+            L.set_schedule(sc["T"], sc["h"], sc["eq"], sc["meas"])
+
+    reset()
+    b = I.Batch(lats, graph=True)
+    b.tune()
+    b.run()                       # warm: kernels loaded, graph captured
+    torch.cuda.synchronize()
+    reset()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    b.run()
+    e.record()
+    e.synchronize()
+    t_batch = a.elapsed_time(e) / 1e3
+    out = {"value": att / t_batch, "unit": UNIT, "films": n_films, "attempts": att, "seconds": t_batch,
+           "sweeps_per_step": sweeps_per_step, "launch": b.info(), "graph": True}
+    b.close()
+    if plain:
+        reset()
+        torch.cuda.synchronize()
+        a.record()
+        for L in lats:
+            L.run(-1)
+        e.record()
+        e.synchronize()
+        t_plain = a.elapsed_time(e) / 1e3
+        out["plain_one_film_per_launch"] = {"value": att / t_plain, "unit": UNIT, "seconds": t_plain}
+        out["speedup_vs_plain"] = t_plain / t_batch
+    for L in lats:
+        L.close()
+    return out
+
+
+def measure_served(I, rate=200.0, duration=5.0, seed=5, pool=24, budget_gb=40.0, sweeps_per_tick=50):
+    """Poisson stream of hysteresis-loop and temperature-scan jobs (50/50) on films with
+    log-normal side length (median 256, 64..2048) and 1..8 layers, served with continuous
+    batching; latency is submit -> completion."""
+    import torch
+    from paper_1205_5588_gb300 import workloads as W
+    rng = np.random.Generator(np.random.PCG64(seed))
+    maps = []
+    for i in range(pool):
+        R, Cc = W.lognormal_side(rng), W.lognormal_side(rng)
+        L = int(rng.integers(1, 9))
+        maps.append((W.fractal_heights(R, Cc, float(rng.uniform(0.5, 0.9)), 1, L, seed=5000 + i), L))
+    hyst_h = W.loop_fields(40, 10)                         # +4 -> -4 -> +4 by 0.1, 161 steps
+    arrivals = W.poisson_arrivals(rate, duration, seed=seed)
+    jobs = []
+    for k in range(len(arrivals)):
+        H, L = maps[int(rng.integers(0, pool))]
+        if rng.random() < 0.5:
+            sc = W.schedule(float(rng.uniform(1.0, 10.0)), hyst_h, 0, 50)
+        else:
+            sc = W.schedule(np.linspace(0.5, 12.0, 24), 0.0, 200, 200)
+        jobs.append((H, L, sc, 10000 + k))
+    srv = I.Server(int(budget_gb * (1 << 30)), sweeps_per_tick=sweeps_per_tick)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ids = []
+    for (H, L, sc, sd), t_arr in zip(jobs, arrivals):
+        dt = t0 + t_arr - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(srv.submit(H, L, sc["T"], sc["h"], sc["eq"], sc["meas"], seed=sd))
+    lat = []
+    for jid in ids:
+        state = srv.wait(jid, timeout=600.0)
+        if state != "done":
+            raise RuntimeError(f"served job {jid} ended {state}")
+        _, _, l = srv.result(jid)
+        lat.append(l)
+        srv.release(jid)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {"value": st["attempts_done"] / wall, "unit": UNIT, "jobs": len(ids), "rate_per_s": rate,
+            "arrival_window_s": duration, "wall_s": wall,
+            "offered": st["attempts_done"] / duration, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "ticks": st["ticks"], "sweeps_per_tick": sweeps_per_tick,
+            "gpu_busy_s": st["busy_s"], "peak_device_bytes": st["peak_bytes"], "spins": "int8"}
 
 
 def load_traffic(workload_name):
@@ -335,6 +438,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--batch-films", type=int, default=128)
+    ap.add_argument("--batch-sweeps", type=int, default=20, help="sweeps per schedule step of the batched films")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--ref-sweeps", type=int, default=0)
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling case: one launch of this many sweeps at the first schedule step, no JSON")

@@ -162,7 +162,8 @@ int isf_set_path(isf_lattice* lat, int32_t path);
 
 /* Launch shape override: ctas = CTAs of the global kernel or cluster size (1..16) of the
  * resident kernel (0 = automatic); threads per CTA (0 = automatic; else a multiple of 32 up to
- * 1024; the global kernel uses at most 256).  Trajectories do not depend on it. */
+ * 1024; the global kernel uses at most 256, the resident kernel at most 512).  Trajectories do
+ * not depend on it. */
 int isf_set_launch(isf_lattice* lat, int32_t ctas, int32_t threads);
 
 /* The resident and batch kernels check every address they derive from a film's description and
@@ -206,20 +207,61 @@ int isf_batch_create(isf_batch** out);
 int isf_batch_add(isf_batch* batch, isf_lattice* lat);        /* ISF_ERR_STATE: no schedule */
 int isf_batch_clear(isf_batch* batch);
 /* Launch shapes: threads of the single-CTA kernel, cluster size K (1..16) and threads of the
- * cluster kernel; 0 = tuned or default (256; 16 and 512). */
+ * cluster kernel (multiples of 32 up to 512); 0 = tuned or default (256; 16 and 512). */
 int isf_batch_set_launch(isf_batch* batch, int32_t threads_single, int32_t cluster_K, int32_t threads_cluster);
 /* on != 0: capture the queue upload and the two persistent launches in a CUDA graph once and
  * replay it on later runs with the same shape (the per-film arguments are refreshed each run). */
 int isf_batch_set_graph(isf_batch* batch, int32_t on);
 /* Autotuner: times short probe runs of the largest film of each class (copies, not the members)
- * over cluster sizes {8, 16} and threads {128, 256, 512, 1024}; keeps the fastest per class,
+ * over cluster sizes {8, 16} and threads {128, 256, 384, 512}; keeps the fastest per class,
  * cached per (device, class, layers, row and column size class) for the process. */
 int isf_batch_tune(isf_batch* batch, void* cuda_stream);
 int isf_batch_run(isf_batch* batch, void* cuda_stream);
+/* As isf_batch_run, but every member advances at most max_sweeps sweeps (>= 1; -1 = to the end). */
+int isf_batch_run_sweeps(isf_batch* batch, int64_t max_sweeps, void* cuda_stream);
 /* Last run: films in the single-CTA / cluster / global classes, CTAs and clusters launched,
  * cluster size, threads of the two kernels (8 int32). */
 int isf_batch_info(isf_batch* batch, int32_t* out8);
 void isf_batch_destroy(isf_batch* batch);
+
+/* ---- Serving ---------------------------------------------------------------------------------
+ * Continuous batching of jobs (a hysteresis loop or a temperature scan on one film, Sec. 3,
+ * Fig. 3, Fig. 5).  A worker thread on the device current at isf_server_create admits queued
+ * jobs while their films fit device_budget_bytes (each admitted job holds its film until it
+ * finishes), advances all admitted films by at most sweeps_per_tick sweeps per batched launch,
+ * retires finished ones and admits more; jobs submitted while a tick runs join the next one.  A
+ * job's result equals the result of the same job run alone.  The job's arrays are copied at
+ * submit.  A job whose film alone exceeds the budget fails with ISF_ERR_OOM. */
+enum { ISF_JOB_QUEUED = 0, ISF_JOB_RUNNING = 1, ISF_JOB_DONE = 2, ISF_JOB_FAILED = 3 };
+typedef struct {
+    const uint8_t* heights;                 /* host, rows*cols, as isf_lattice_create */
+    int32_t rows, cols, layers;
+    uint32_t flags;
+    uint64_t seed;
+    int32_t init;
+    int32_t nsteps;                         /* schedule, as isf_set_schedule */
+    const double* T;
+    const double* h;
+    const int32_t* sweeps_eq;
+    const int32_t* sweeps_meas;
+    double J, h_s;
+} isf_job;
+typedef struct isf_server isf_server;
+int isf_server_create(size_t device_budget_bytes, int64_t sweeps_per_tick, isf_server** out);
+int isf_server_submit(isf_server* srv, const isf_job* job, int64_t* id);
+/* Wait up to timeout_s seconds for the job to finish; *state = ISF_JOB_*. */
+int isf_server_wait(isf_server* srv, int64_t id, double timeout_s, int32_t* state);
+/* State; when done, its records (as isf_read_observables, at most max) and the latency from
+ * submit to completion.  A failed job returns its error. */
+int isf_server_poll(isf_server* srv, int64_t id, int32_t* state, isf_step_obs* out, int32_t max,
+                    int32_t* n_out, double* latency_s);
+/* Forget a finished job (frees its records). */
+int isf_server_release(isf_server* srv, int64_t id);
+/* out8: submitted, completed, failed, active, queued, ticks, attempts completed, peak budget
+ * bytes in use; out4: seconds of batched launches, seconds since create, bytes in use, budget. */
+int isf_server_stats(isf_server* srv, int64_t* out8, double* out4);
+/* Finishes the jobs already submitted, then stops the worker and frees everything. */
+void isf_server_destroy(isf_server* srv);
 
 /* No-allocation run (no counterpart in the paper; it exists for callers of this library).
  * Some callers must not allocate device memory: code living inside a process whose device

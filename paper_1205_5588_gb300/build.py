@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["kernels_sweep.cu", "kernels_resident.cu", "kernels_aux.cu", "noalloc.cu"]
-CPP_SOURCES = ["capi.cpp", "batch.cpp", "lattice.cpp", "schedule.cpp"]
+CPP_SOURCES = ["capi.cpp", "batch.cpp", "serve.cpp", "lattice.cpp", "schedule.cpp"]
 HEADERS = ["isf_internal.h", "device_common.cuh", "sweep_core.cuh", "capi_internal.h"]
 
 
@@ -79,7 +79,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
         for l in logs:
             sys.stderr.write(l)
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    _run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *[o for _, o in jobs]])
+    _run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *[o for _, o in jobs], "-lpthread"])
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
 

@@ -205,8 +205,8 @@ int isf_batch_clear(isf_batch* b) {
 
 int isf_batch_set_launch(isf_batch* b, int32_t threads_single, int32_t cluster_K, int32_t threads_cluster) {
     if (!b || threads_single < 0 || cluster_K < 0 || cluster_K > 16 || threads_cluster < 0 ||
-        threads_single % 32 || threads_cluster % 32 || threads_single > 1024 || threads_cluster > 1024)
-        return fail(ISF_ERR_ARG, "threads: 0 or multiples of 32 up to 1024; cluster size 0..16");
+        threads_single % 32 || threads_cluster % 32 || threads_single > 512 || threads_cluster > 512)
+        return fail(ISF_ERR_ARG, "threads: 0 or multiples of 32 up to 512; cluster size 0..16");
     b->threads_a = threads_single;
     b->K_b = cluster_K;
     b->threads_b = threads_cluster;
@@ -249,7 +249,7 @@ int isf_batch_tune(isf_batch* b, void* cuda_stream) {
         if (!cached) {
             double best_t = 1e300;
             const int Ks[2] = {8, 16};
-            const int ths[4] = {128, 256, 512, 1024};
+            const int ths[4] = {128, 256, 384, 512};
             for (int ki = 0; ki < (cls ? 2 : 1); ++ki)
                 for (int ti = 0; ti < 4; ++ti) {
                     const int K = cls ? Ks[ki] : 1;
@@ -265,8 +265,11 @@ int isf_batch_tune(isf_batch* b, void* cuda_stream) {
     return set_last_error(ISF_OK, "");
 }
 
-int isf_batch_run(isf_batch* b, void* cuda_stream) {
+int isf_batch_run(isf_batch* b, void* cuda_stream) { return isf_batch_run_sweeps(b, -1, cuda_stream); }
+
+int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
     if (!b) return fail(ISF_ERR_ARG, "batch is NULL");
+    if (max_sweeps < -1 || max_sweeps == 0) return fail(ISF_ERR_ARG, "max_sweeps must be >= 1 or -1");
     int rc = ensure_streams(b);
     if (rc) return rc;
     CUDA_TRY(cudaSetDevice(b->device), "cudaSetDevice");
@@ -282,7 +285,8 @@ int isf_batch_run(isf_batch* b, void* cuda_stream) {
     std::vector<isf_lattice*> C;
     for (isf_lattice* L : b->films) {
         if (L->device != b->device) return fail(ISF_ERR_ARG, "all films of a batch must be on one device");
-        const int64_t n = sweeps_remaining(L);
+        int64_t n = sweeps_remaining(L);
+        if (max_sweeps > 0 && n > max_sweeps) n = max_sweeps;
         if (n <= 0) continue;
         Item it{L, n, {}, (double)n * L->lay.L * L->lay.Rh * L->lay.Ch};
         // the queue kernels hold int8 films without periodic columns
@@ -355,7 +359,9 @@ int isf_batch_run(isf_batch* b, void* cuda_stream) {
     for (isf_lattice* L : C) {
         const int32_t saved = L->path;
         L->path = ISF_PATH_GLOBAL;
-        rc = isf_run_sweeps(L, -1, s);
+        int64_t n = sweeps_remaining(L);
+        if (max_sweeps > 0 && n > max_sweeps) n = max_sweeps;
+        rc = isf_run_sweeps(L, n, s);
         L->path = saved;
         if (rc) return rc;
     }

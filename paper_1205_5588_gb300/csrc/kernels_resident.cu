@@ -33,6 +33,7 @@ __device__ unsigned long long g_isf_check[4];
 namespace {
 
 constexpr int kMaxK = 16;
+constexpr int kMaxResThreads = 512;     // up to 128 registers per thread
 constexpr uint32_t kMiscBytes = 128 * 4 + 16 + 64 * 8 + 2 * kMaxK * 8 + kMaxK * 8;
 
 
@@ -63,6 +64,59 @@ __device__ __forceinline__ uint8_t* map_rank(uint8_t* p, unsigned rank) {
 
 __device__ __forceinline__ int64_t film_bytes_or(const DevFilm& f) { return 4 * f.cs8; }
 
+// 32-bit shared-window address of a shared-memory pointer, and the same location in CTA `rank`
+// of the cluster (a shared::cluster address; a CTA's own shared::cta addresses are valid there).
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t map_rank_addr(uint32_t a, unsigned rank) {
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(a), "r"(rank));
+    return out;
+}
+template <bool CLUSTER>
+__device__ __forceinline__ uint4 lds16(uint32_t a) {
+    uint4 v;
+    if (CLUSTER)
+        asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a) : "memory");
+    else
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a) : "memory");
+    return v;
+}
+template <bool CLUSTER>
+__device__ __forceinline__ uint32_t lds4(uint32_t a) {
+    uint32_t v;
+    if (CLUSTER) asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    else asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+
+// Neighbour sum of a 16-site chunk from shared::cluster addresses (see neighbour_sum16).
+template <bool CLUSTER>
+__device__ __forceinline__ uint4 neighbour_sum16_sc(const uint32_t* nb, int sgn) {
+    uint4 acc = lds16<CLUSTER>(nb[0]);
+#pragma unroll
+    for (int k = 1; k < 9; ++k) add4(acc, lds16<CLUSTER>(nb[k]));
+    if (sgn < 0) {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) {
+            const uint4 v = lds16<CLUSTER>(nb[k]);
+            const uint32_t e = lds4<CLUSTER>(nb[k] - 4);
+            add4(acc, make_uint4(__funnelshift_l(e, v.x, 8), __funnelshift_l(v.x, v.y, 8),
+                                 __funnelshift_l(v.y, v.z, 8), __funnelshift_l(v.z, v.w, 8)));
+        }
+    } else {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) {
+            const uint4 v = lds16<CLUSTER>(nb[k]);
+            const uint32_t e = lds4<CLUSTER>(nb[k] + 16);
+            add4(acc, make_uint4(__funnelshift_r(v.x, v.y, 8), __funnelshift_r(v.y, v.z, 8),
+                                 __funnelshift_r(v.z, v.w, 8), __funnelshift_r(v.w, e, 8)));
+        }
+    }
+    return acc;
+}
+
 template <bool CLUSTER>
 __device__ __forceinline__ void sync_all() {
     if (CLUSTER) cluster_sync_all();
@@ -83,19 +137,19 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
     const int nown = max(0, min(Jb, Rh - j0));      // trailing CTAs may own no rows
     uint8_t* film = sm + a.film_off;
     uint8_t* vac = sm + a.vac_off;
-    uint8_t** ptrs = reinterpret_cast<uint8_t**>(sm + a.ptr_off);
+    uint32_t* ptrs = reinterpret_cast<uint32_t*>(sm + a.ptr_off);
     uint32_t* tab = reinterpret_cast<uint32_t*>(sm + a.misc_off);
     uint32_t* gate = tab + 128;
     long long* red = reinterpret_cast<long long*>(sm + a.misc_off + 128 * 4 + 16);
     long long* slots = red + 64;
-    uint8_t** base = reinterpret_cast<uint8_t**>(slots + 2 * kMaxK);
+    uint32_t* base = reinterpret_cast<uint32_t*>(slots + 2 * kMaxK);
 
     // slab in, vacancy row, every rank's slab address
     const int words = P / 16;
     const uint64_t smem_n = dyn_smem_bytes();
     bool desc_ok = ISF_CHECK(K >= 1 && K <= 16 && Jb >= 1 && (int64_t)Jb * K >= Rh && P % 16 == 0, 1, K, Jb);
     desc_ok = desc_ok && ISF_CHECK(a.misc_off + 1424 <= smem_n, 2, a.misc_off, smem_n);
-    desc_ok = desc_ok && ISF_CHECK((uint64_t)a.ptr_off + (uint64_t)4 * L * Jb * 96 <= a.misc_off, 3, a.ptr_off, a.misc_off);
+    desc_ok = desc_ok && ISF_CHECK((uint64_t)a.ptr_off + (uint64_t)4 * L * Jb * 48 <= a.misc_off, 3, a.ptr_off, a.misc_off);
     desc_ok = desc_ok && ISF_CHECK(s.k0 >= 0 && s.k0 < s.nsteps && s.nsteps >= 1, 4, s.k0, s.nsteps);
     if (!desc_ok) { sync_all<CLUSTER>(); sync_all<CLUSTER>(); return; }
     for (int t = threadIdx.x; t < 4 * L * nown * words; t += blockDim.x) {
@@ -109,7 +163,7 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
         reinterpret_cast<uint4*>(film + ((size_t)cz * Jb + jl) * P)[w] = *reinterpret_cast<const uint4*>(f.s8 + off);
     }
     for (int t = threadIdx.x; t < P / 4; t += blockDim.x) reinterpret_cast<uint32_t*>(vac)[t] = 0x01010101u;
-    if (threadIdx.x < K) base[threadIdx.x] = CLUSTER ? map_rank(film, threadIdx.x) : film;
+    if (threadIdx.x < K) base[threadIdx.x] = CLUSTER ? map_rank_addr(smem_addr(film), threadIdx.x) : smem_addr(film);
     __syncthreads();
     if (PX) {
         for (int rr = threadIdx.x; rr < 4 * L * nown; rr += blockDim.x) {
@@ -135,11 +189,11 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
             if (f.flags & 2u) jj = (jj + Rh) % Rh;
             else inside = false;
         }
-        uint8_t* p = vac;
+        uint32_t p = smem_addr(vac);
         if (inside) {
             const int rk = jj / Jb;
             if (!ISF_CHECK(rk >= 0 && rk < (int)K && nc.c2[k] >= 0 && nc.c2[k] < 4, 7, rk, nc.c2[k])) continue;
-            p = base[rk] + ((size_t)(nc.c2[k] * L + zz) * Jb + (jj - rk * Jb)) * P;
+            p = base[rk] + (uint32_t)(((nc.c2[k] * L + zz) * Jb + (jj - rk * Jb)) * P);
         }
         ptrs[((size_t)cz * Jb + jl) * 12 + k] = p;
     }
@@ -176,16 +230,41 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
                 if (!ISF_CHECK(z >= 0 && z < L && jl >= 0 && jl < nown && ck >= 0 && ck < nck, 8, it, ((uint64_t)z << 32) | (uint32_t)jl)) continue;
                 uint8_t* row = film + r * P;
                 uint8_t* own = row + 16 + 16 * ck;
-                uint8_t* const* pr = ptrs + r * 12;
-                const uint8_t* nbp[12];
+                const uint32_t* pr = ptrs + r * 12;
+                uint32_t nbp[12];
 #pragma unroll
                 for (int kk = 0; kk < 12; ++kk) nbp[kk] = pr[kk] + 16 + 16 * ck;
                 const uint32_t q0 = block_counter(f, c, z, j0 + jl, 16 * ck);
                 const int sgn = f.nb[c][z & 1].sgn;
-                if (s.use_gate)
-                    update_chunk16<true, PX>(own, nbp, sgn, q0, sweep, tab, gthr, f.key0, f.key1, 16 * ck, Ch, row, dM, dB);
-                else
-                    update_chunk16<false, PX>(own, nbp, sgn, q0, sweep, tab, gthr, f.key0, f.key1, 16 * ck, Ch, row, dM, dB);
+                const uint4 S = *reinterpret_cast<const uint4*>(own);
+                const uint4 acc = neighbour_sum16_sc<CLUSTER>(nbp, sgn);
+                const uint32_t Sw[4] = {S.x, S.y, S.z, S.w};
+                const uint32_t Aw[4] = {acc.x, acc.y, acc.z, acc.w};
+                uint32_t fm[4];
+                const uint32_t any = s.use_gate
+                    ? decide16<true, PX>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, 16 * ck, Ch, fm, dM, dB)
+                    : decide16<false, PX>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, 16 * ck, Ch, fm, dM, dB);
+                if (any) {
+                    if (!PX) {
+                        *reinterpret_cast<uint4*>(own) = make_uint4(Sw[0] ^ fm[0], Sw[1] ^ fm[1], Sw[2] ^ fm[2], Sw[3] ^ fm[3]);
+                    } else {
+                        // byte stores (the row's wrap bytes may share a word), refreshing the
+                        // wrap copies of columns 0 and Ch-1
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            if (!fm[v]) continue;
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) {
+                                if (!((fm[v] >> (8 * b)) & 0xFFu)) continue;
+                                const uint8_t nbyte = (uint8_t)((Sw[v] ^ fm[v]) >> (8 * b));
+                                const int i = 16 * ck + 4 * v + b;
+                                own[4 * v + b] = nbyte;
+                                if (i == 0) row[16 + Ch] = nbyte;
+                                if (i == Ch - 1) row[15] = nbyte;
+                            }
+                        }
+                    }
+                }
             }
             if (c == 3) {
                 long long sM = dM, sB = dB;
@@ -229,7 +308,7 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
 }
 
 template <bool CLUSTER, bool PX>
-__global__ void __launch_bounds__(1024, 1) k_resident(const __grid_constant__ ResArgs a) {
+__global__ void __launch_bounds__(kMaxResThreads, 1) k_resident(const __grid_constant__ ResArgs a) {
     extern __shared__ __align__(16) uint8_t sm[];
     run_film<CLUSTER, PX>(a, sm);
 }
@@ -239,7 +318,7 @@ __global__ void __launch_bounds__(1024, 1) k_resident(const __grid_constant__ Re
 // are independent Markov chains (each its own seed, schedule and state), so no film waits on
 // another; the queue is a device counter.
 template <bool CLUSTER>
-__global__ void __launch_bounds__(1024, 1) k_batch(const ResArgs* films, int nfilms, unsigned* next) {
+__global__ void __launch_bounds__(kMaxResThreads, 1) k_batch(const ResArgs* films, int nfilms, unsigned* next) {
     extern __shared__ __align__(16) uint8_t sm[];
     __shared__ int film_s;
     const unsigned rank = CLUSTER ? cluster_rank() : 0u;
@@ -324,7 +403,7 @@ bool layout_for(const DevFilm& f, int K, int threads, int max_smem, ResPlan* out
     p.film_off = 0;
     p.vac_off = round16((uint32_t)(rows * f.P));
     p.ptr_off = round16(p.vac_off + (uint32_t)f.P);
-    p.misc_off = round16(p.ptr_off + (uint32_t)(rows * 12 * 8));
+    p.misc_off = round16(p.ptr_off + (uint32_t)(rows * 12 * 4));
     p.smem = round16(p.misc_off + kMiscBytes);
     if (rows * f.P > (uint64_t)max_smem || p.smem > (uint32_t)max_smem) return false;
     *out = p;
@@ -355,15 +434,16 @@ int resident_plan(const DevFilm& f, int want_K, int want_threads, ResPlan* out) 
     for (int ci = 0; ci < nc; ++ci) {
         const int K = cand[ci];
         ResPlan p;
-        // threads: one per 16-site chunk of a pass, rounded to whole warps, 64..1024
+        // threads: one per 16-site chunk of a pass, rounded to whole warps, 64..512
         int th = threads;
         if (!th) {
             const int Jb = (f.Rh + K - 1) / K;
             const int64_t items = (int64_t)f.L * Jb * f.nck;
             th = (int)((items + 31) / 32 * 32);
             if (th < 64) th = 64;
-            if (th > 1024) th = 1024;
+            if (th > kMaxResThreads) th = kMaxResThreads;
         }
+        if (th > kMaxResThreads) return 3;
         if (!layout_for(f, K, th, max_smem, &p)) continue;
         int n = 0;
         const bool px = (f.flags & 1u) != 0;

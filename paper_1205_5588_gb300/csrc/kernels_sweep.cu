@@ -74,8 +74,8 @@ __device__ __forceinline__ void chunk_int8(const DevFilm& f, int c, int z, int j
     const uint8_t* nbp[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) nbp[k] = own + nc.off[k];
-    update_chunk16<GATE, false>(own, nbp, nc.sgn, block_counter(f, c, z, j, 16 * ck), sweep, tab, gthr,
-                                f.key0, f.key1, 16 * ck, f.Ch, nullptr, dM, dB);
+    update_chunk16<GATE>(own, nbp, nc.sgn, block_counter(f, c, z, j, 16 * ck), sweep, tab, gthr,
+                         f.key0, f.key1, 16 * ck, f.Ch, dM, dB);
 }
 
 // ---- int8 layout, any boundary (periodic wraps): one thread per 4-site Philox block --------

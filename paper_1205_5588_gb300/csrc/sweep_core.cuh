@@ -58,20 +58,90 @@ __device__ __forceinline__ uint32_t gate_block(uint32_t lanes, uint32_t gthr, ui
     return lanes & keep;
 }
 
-// One 16-site chunk of an int8 colour row.  own: the chunk's 16 bytes.  nb[k]: the same
-// columns' 16 bytes in neighbour row k (k < 9 unshifted; k = 9..11 shifted by sgn columns,
-// completed from the word before / after).  Bytes hold S + 1 (vacancy 1), so 12 word adds give
-// n + 12 per byte.  Per 4-site word: four table lookups, one Philox block when any of the four
-// thresholds is neither 0 nor "always", the flips as a byte mask (0 <-> 2 is XOR 2), and dM, dB
-// from popcounts of that mask and a multiply-add of the masked neighbour sums.  PX (periodic
-// x): lanes past the row end are masked, stores go byte by byte, and column 0 / column Ch-1
-// also refresh their wrap copies at row[16 + Ch] / row[15].
+// Four Philox4x32-10 blocks at consecutive counters, interleaved so that the four dependency
+// chains overlap (same rounds as philox10).
+__device__ __forceinline__ void philox10_x4(uint32_t q0, uint32_t s_lo, uint32_t s_hi, uint32_t stream,
+                                            uint32_t k0, uint32_t k1, uint4 out[4]) {
+    uint32_t c0[4], c1[4], c2[4], c3[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { c0[v] = q0 + v; c1[v] = s_lo; c2[v] = s_hi; c3[v] = stream; }
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const uint32_t lo0 = 0xD2511F53u * c0[v];
+            const uint32_t hi0 = __umulhi(0xD2511F53u, c0[v]);
+            const uint32_t lo1 = 0xCD9E8D57u * c2[v];
+            const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2[v]);
+            c0[v] = hi1 ^ c1[v] ^ k0;
+            c1[v] = lo1;
+            c2[v] = hi0 ^ c3[v] ^ k1;
+            c3[v] = lo0;
+        }
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[v] = make_uint4(c0[v], c1[v], c2[v], c3[v]);
+}
+
+// The Metropolis decisions of one 16-site chunk of an int8 colour row (Eq. 8; Eq. 9 gate).
+// Sw: the chunk's 4 words of stored bytes (S + 1: 0 down, 1 vacancy, 2 up); Aw: per byte the
+// sum of the 12 neighbour bytes, n + 12.  All 16 table lookups first; then, if any lane's
+// threshold is neither 0 nor "always", the chunk's four Philox blocks at once (a real word
+// decides a 0 / "always" lane exactly as no word does, so computing it never changes a
+// result).  The flips come back as a byte mask per word (0 <-> 2 is XOR 2); dM and dB from
+// popcounts of that mask and a multiply-add of the masked neighbour sums.  PX: lanes past the
+// row end (column Ch on) are masked.  Returns the OR of the four masks.
 template <bool GATE, bool PX>
-__device__ __forceinline__ void update_chunk16(uint8_t* own, const uint8_t* const* nb, int sgn, uint32_t q0,
-                                               unsigned long long sweep, const uint32_t* tab, uint32_t gthr,
-                                               uint32_t key0, uint32_t key1, int i0, int Ch, uint8_t* row,
-                                               int& dM, int& dB) {
-    const uint4 S = ld16(own);
+__device__ __forceinline__ uint32_t decide16(const uint32_t Sw[4], const uint32_t Aw[4], uint32_t q0,
+                                             unsigned long long sweep, const uint32_t* tab, uint32_t gthr,
+                                             uint32_t key0, uint32_t key1, int i0, int Ch, uint32_t fm[4],
+                                             int& dM, int& dB) {
+    uint32_t thr[16];
+    bool need = false;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const uint32_t iw = (Sw[v] << 5) + Aw[v];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            uint32_t t = tab[(iw >> (8 * b)) & 0xFFu];
+            if (PX && i0 + 4 * v + b >= Ch) t = 0u;
+            thr[4 * v + b] = t;
+            need |= needs_word(t);
+        }
+    }
+    uint4 u[4] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+    if (need) philox10_x4(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, key0, key1, u);
+    uint32_t any = 0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        uint32_t m = (metropolis_accept(u[v].x, thr[4 * v + 0]) ? 0x00000002u : 0u) |
+                     (metropolis_accept(u[v].y, thr[4 * v + 1]) ? 0x00000200u : 0u) |
+                     (metropolis_accept(u[v].z, thr[4 * v + 2]) ? 0x00020000u : 0u) |
+                     (metropolis_accept(u[v].w, thr[4 * v + 3]) ? 0x02000000u : 0u);
+        if (GATE && m) {
+            uint32_t lanes = ((m >> 1) & 1u) | ((m >> 8) & 2u) | ((m >> 15) & 4u) | ((m >> 22) & 8u);
+            lanes = gate_block(lanes, gthr, q0 + v, sweep, key0, key1);
+            m = ((lanes & 1u) << 1) | ((lanes & 2u) << 8) | ((lanes & 4u) << 15) | ((lanes & 8u) << 22);
+        }
+        // flipped from up (byte 2) and from down (byte 0); dM = -2 (n_up - n_down),
+        // dB = -2 [sum over up-flips of n - sum over down-flips of n], n = byte of Aw - 12
+        const uint32_t up = m & Sw[v], dn = m ^ up;
+        const int nu = __popc(up), nd = __popc(dn);
+        const uint32_t xu = ((Aw[v] & ((up >> 1) * 0xFFu)) * 0x01010101u) >> 24;
+        const uint32_t xd = ((Aw[v] & ((dn >> 1) * 0xFFu)) * 0x01010101u) >> 24;
+        dM += 2 * (nd - nu);
+        dB += 2 * (((int)xd - 12 * nd) - ((int)xu - 12 * nu));
+        fm[v] = m;
+        any |= m;
+    }
+    return any;
+}
+
+// Sum of the 12 neighbour words of a 16-site chunk (k < 9 unshifted; k = 9..11 shifted by sgn
+// columns and completed from the word before / after), from generic pointers.
+__device__ __forceinline__ uint4 neighbour_sum16(const uint8_t* const* nb, int sgn) {
     uint4 acc = ld16(nb[0]);
 #pragma unroll
     for (int k = 1; k < 9; ++k) add4(acc, ld16(nb[k]));
@@ -92,60 +162,22 @@ __device__ __forceinline__ void update_chunk16(uint8_t* own, const uint8_t* cons
                                  __funnelshift_r(v.z, v.w, 8), __funnelshift_r(v.w, e, 8)));
         }
     }
+    return acc;
+}
+
+// One 16-site chunk, neighbours through generic pointers (global-memory kernel).
+template <bool GATE>
+__device__ __forceinline__ void update_chunk16(uint8_t* own, const uint8_t* const* nb, int sgn, uint32_t q0,
+                                               unsigned long long sweep, const uint32_t* tab, uint32_t gthr,
+                                               uint32_t key0, uint32_t key1, int i0, int Ch,
+                                               int& dM, int& dB) {
+    const uint4 S = ld16(own);
+    const uint4 acc = neighbour_sum16(nb, sgn);
     const uint32_t Sw[4] = {S.x, S.y, S.z, S.w};
     const uint32_t Aw[4] = {acc.x, acc.y, acc.z, acc.w};
-    uint32_t out[4];
-    uint32_t any = 0;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const uint32_t iw = (Sw[v] << 5) + Aw[v];
-        uint32_t thr[4];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            thr[b] = tab[(iw >> (8 * b)) & 0xFFu];
-            if (PX && i0 + 4 * v + b >= Ch) thr[b] = 0u;
-        }
-        const bool need = needs_word(thr[0]) | needs_word(thr[1]) | needs_word(thr[2]) | needs_word(thr[3]);
-        uint4 u = make_uint4(0, 0, 0, 0);
-        if (need) u = philox10(make_uint4(q0 + v, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u), key0, key1);
-        uint32_t fm = (metropolis_accept(u.x, thr[0]) ? 0x00000002u : 0u) |
-                      (metropolis_accept(u.y, thr[1]) ? 0x00000200u : 0u) |
-                      (metropolis_accept(u.z, thr[2]) ? 0x00020000u : 0u) |
-                      (metropolis_accept(u.w, thr[3]) ? 0x02000000u : 0u);
-        if (GATE && fm) {
-            uint32_t lanes = ((fm >> 1) & 1u) | ((fm >> 8) & 2u) | ((fm >> 15) & 4u) | ((fm >> 22) & 8u);
-            lanes = gate_block(lanes, gthr, q0 + v, sweep, key0, key1);
-            fm = ((lanes & 1u) << 1) | ((lanes & 2u) << 8) | ((lanes & 4u) << 15) | ((lanes & 8u) << 22);
-        }
-        // flipped from up (byte 2) and from down (byte 0); dM = -2 (n_up - n_down),
-        // dB = -2 [sum over up-flips of n - sum over down-flips of n], n = byte of Aw - 12
-        const uint32_t up = fm & Sw[v], dn = fm ^ up;
-        const int nu = __popc(up), nd = __popc(dn);
-        const uint32_t xu = ((Aw[v] & ((up >> 1) * 0xFFu)) * 0x01010101u) >> 24;
-        const uint32_t xd = ((Aw[v] & ((dn >> 1) * 0xFFu)) * 0x01010101u) >> 24;
-        dM += 2 * (nd - nu);
-        dB += 2 * (((int)xd - 12 * nd) - ((int)xu - 12 * nu));
-        out[v] = Sw[v] ^ fm;
-        any |= fm;
-    }
-    if (!any) return;
-    if (!PX) {
-        *reinterpret_cast<uint4*>(own) = make_uint4(out[0], out[1], out[2], out[3]);
-        return;
-    }
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        if (out[v] == Sw[v]) continue;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const uint8_t nbyte = (uint8_t)(out[v] >> (8 * b));
-            if (nbyte == (uint8_t)(Sw[v] >> (8 * b))) continue;
-            const int i = i0 + 4 * v + b;
-            own[4 * v + b] = nbyte;
-            if (i == 0) row[16 + Ch] = nbyte;
-            if (i == Ch - 1) row[15] = nbyte;
-        }
-    }
+    uint32_t fm[4];
+    if (decide16<GATE, false>(Sw, Aw, q0, sweep, tab, gthr, key0, key1, i0, Ch, fm, dM, dB))
+        *reinterpret_cast<uint4*>(own) = make_uint4(Sw[0] ^ fm[0], Sw[1] ^ fm[1], Sw[2] ^ fm[2], Sw[3] ^ fm[3]);
 }
 
 // Walks a thread's work items it, it + T, it + 2T, ... of a pass laid out as (z, row, chunk)

@@ -32,6 +32,16 @@ class StepObs(C.Structure):
     ]
 
 
+class IsfJob(C.Structure):
+    _fields_ = [
+        ("heights", C.POINTER(C.c_uint8)), ("rows", C.c_int32), ("cols", C.c_int32), ("layers", C.c_int32),
+        ("flags", C.c_uint32), ("seed", C.c_uint64), ("init", C.c_int32), ("nsteps", C.c_int32),
+        ("T", C.POINTER(C.c_double)), ("h", C.POINTER(C.c_double)),
+        ("sweeps_eq", C.POINTER(C.c_int32)), ("sweeps_meas", C.POINTER(C.c_int32)),
+        ("J", C.c_double), ("h_s", C.c_double),
+    ]
+
+
 class IsfError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
@@ -73,6 +83,14 @@ def _declare(lib):
         "isf_batch_run": (C.c_int, [vp, vp]),
         "isf_batch_info": (C.c_int, [vp, i32p]),
         "isf_batch_destroy": (None, [vp]),
+        "isf_batch_run_sweeps": (C.c_int, [vp, C.c_int64, vp]),
+        "isf_server_create": (C.c_int, [C.c_size_t, C.c_int64, C.POINTER(vp)]),
+        "isf_server_submit": (C.c_int, [vp, C.POINTER(IsfJob), i64p]),
+        "isf_server_wait": (C.c_int, [vp, C.c_int64, C.c_double, i32p]),
+        "isf_server_poll": (C.c_int, [vp, C.c_int64, i32p, C.POINTER(StepObs), C.c_int32, i32p, dp]),
+        "isf_server_release": (C.c_int, [vp, C.c_int64]),
+        "isf_server_stats": (C.c_int, [vp, i64p, dp]),
+        "isf_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -308,8 +326,8 @@ class Batch:
     def tune(self, stream=None):
         _check(lib.isf_batch_tune(self._h, _stream_handle(stream)), "batch_tune")
 
-    def run(self, stream=None):
-        _check(lib.isf_batch_run(self._h, _stream_handle(stream)), "batch_run")
+    def run(self, stream=None, max_sweeps=-1):
+        _check(lib.isf_batch_run_sweeps(self._h, int(max_sweeps), _stream_handle(stream)), "batch_run")
 
     def info(self) -> dict:
         v = (C.c_int32 * 8)()
@@ -321,6 +339,75 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             lib.isf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+
+
+class Server:
+    """Continuous-batching job server (isf_server_*) on the current CUDA device."""
+
+    def __init__(self, budget_bytes, sweeps_per_tick=50):
+        h = C.c_void_p()
+        _check(lib.isf_server_create(int(budget_bytes), int(sweeps_per_tick), C.byref(h)), "server_create")
+        self._h = h
+        self._nsteps = {}
+
+    def submit(self, heights, layers, T, h, sweeps_eq, sweeps_meas, *, seed=1, init="random", packed=False,
+               periodic_x=False, periodic_y=False, J=1.0, h_s=0.0) -> int:
+        H = np.ascontiguousarray(heights, dtype=np.uint8)
+        Ta = np.ascontiguousarray(T, dtype=np.float64)
+        ha = np.ascontiguousarray(h, dtype=np.float64)
+        eq = np.ascontiguousarray(sweeps_eq, dtype=np.int32)
+        me = np.ascontiguousarray(sweeps_meas, dtype=np.int32)
+        job = IsfJob(_ptr(H, C.c_uint8), H.shape[0], H.shape[1], int(layers),
+                     flags_of(periodic_x, periodic_y, False, packed), int(seed),
+                     INIT[init] if isinstance(init, str) else int(init), len(Ta),
+                     _ptr(Ta, C.c_double), _ptr(ha, C.c_double), _ptr(eq, C.c_int32), _ptr(me, C.c_int32),
+                     float(J), float(h_s))
+        jid = C.c_int64()
+        _check(lib.isf_server_submit(self._h, C.byref(job), C.byref(jid)), "server_submit")
+        self._nsteps[jid.value] = len(Ta)
+        return jid.value
+
+    def wait(self, jid, timeout=60.0) -> str:
+        st = C.c_int32()
+        _check(lib.isf_server_wait(self._h, int(jid), float(timeout), C.byref(st)), "server_wait")
+        return JOB_STATES[st.value]
+
+    def result(self, jid):
+        """(state, records as dicts, latency seconds); raises IsfError for a failed job."""
+        n = self._nsteps.get(jid, 0)
+        recs = (StepObs * max(n, 1))()
+        st, got, lat = C.c_int32(), C.c_int32(), C.c_double()
+        _check(lib.isf_server_poll(self._h, int(jid), C.byref(st), recs, n, C.byref(got), C.byref(lat)),
+               "server_poll")
+        return JOB_STATES[st.value], obs_to_dicts(recs[:got.value]), lat.value
+
+    def release(self, jid):
+        _check(lib.isf_server_release(self._h, int(jid)), "server_release")
+        self._nsteps.pop(jid, None)
+
+    def stats(self) -> dict:
+        v8 = (C.c_int64 * 8)()
+        v4 = (C.c_double * 4)()
+        _check(lib.isf_server_stats(self._h, v8, v4), "server_stats")
+        k8 = ("submitted", "completed", "failed", "active", "queued", "ticks", "attempts_done", "peak_bytes")
+        k4 = ("busy_s", "uptime_s", "bytes_in_use", "budget_bytes")
+        d = dict(zip(k8, list(v8)))
+        d.update(zip(k4, list(v4)))
+        return d
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.isf_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -139,7 +139,7 @@ def test_launch_shape_does_not_change_the_trajectory(I, packed, path):
     sched = W.schedule([2.0, 6.0], [0.5, -0.5], [2, 2], [5, 5])
     ref = run_oracle(spec, sched)
     shapes = [(1, 256), (2, 64), (7, 128), (3, 32)] if path == "global" else \
-             [(1, 1024), (2, 256), (3, 128), (4, 512), (8, 64), (10, 96), (5, 0), (0, 0)]   # 40 colour rows
+             [(1, 512), (2, 256), (3, 128), (4, 512), (8, 64), (10, 96), (5, 0), (0, 0)]   # 40 colour rows
     for launch in shapes:
         g = run_gpu(I, spec, sched, packed=packed, launch=launch, path=path)
         assert np.array_equal(g["trace"], ref["trace"]) and np.array_equal(g["spins"], ref["spins"]), launch
