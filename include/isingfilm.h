@@ -129,6 +129,17 @@ int isf_read_observables(isf_lattice* lat, isf_step_obs* out, int32_t max, int32
 /* Spins to host_out (layers*rows*cols int8, [z][y][x], +1 / -1, 0 on vacancies).  Syncs. */
 int isf_read_spins(isf_lattice* lat, int8_t* host_out);
 
+/* Simulated PMOKE image of the film (Sec. 6): only the surface atoms are shown, white for spin
+ * up and black for spin down.  host_out: rows*cols bytes [y][x]; 255 where the pixel's top atom
+ * (z = height - 1) is up, 0 where it is down, 128 where the pixel has no atom.  *n_up (may be
+ * NULL): white pixels.  Synchronises. */
+int isf_read_surface_image(isf_lattice* lat, uint8_t* host_out, int64_t* n_up);
+
+/* Lattice statistics of Sec. 4 / Table 1: concentration p = occupied sites / (rows*cols*layers),
+ * mean coordination zbar = 2 * occupied bonds / occupied sites and the critical concentration
+ * p_c = 2 / zbar of Eq. 2 (inf when there are no bonds).  No device work. */
+int isf_lattice_stats(isf_lattice* lat, double* p, double* zbar, double* p_c);
+
 /* Replace the spins (same layout; must be +-1 exactly on occupied sites, 0 elsewhere) and
  * set the film-local sweep counter (the next sweep draws sweep + 1), e.g. to resume from a
  * state.  Recomputes M and B.  Synchronous.  Errors: ISF_ERR_ARG, ISF_ERR_CUDA. */

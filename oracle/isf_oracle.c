@@ -451,6 +451,26 @@ int or_run(or_film* f, int nsteps, const double* T, const double* h, const int* 
     return OR_OK;
 }
 
+/* ---------------------------------------------------------------- PMOKE image -------- */
+/* Sec. 6: only the surface atoms are shown, white for spin up and black for spin down. */
+int64_t or_surface_image(const or_film* f, uint8_t* out)
+{
+    int64_t up = 0;
+    for (int y = 0; y < f->R; ++y)
+        for (int x = 0; x < f->C; ++x) {
+            int top = -1;
+            for (int z = 0; z < f->L; ++z)
+                if (f->occ[site_of(f, x, y, z)]) top = z;
+            uint8_t v = 128;
+            if (top >= 0) {
+                v = f->spin[site_of(f, x, y, top)] > 0 ? 255 : 0;
+                if (v == 255) ++up;
+            }
+            out[(size_t)y * (size_t)f->C + (size_t)x] = v;
+        }
+    return up;
+}
+
 /* ---------------------------------------------------------------- exact enumeration -- */
 /* Eqs. 4-5: Z = sum over the 2^N configurations of exp(-H/T); each configuration has
  * probability exp(-H/T)/Z.  Weights are taken relative to the lowest energy for range. */

@@ -79,6 +79,11 @@ int  or_run(or_film* f, int nsteps, const double* T, const double* h, const int*
 /* FP64 quantities of one record derived from its integer sums (n_occ sites, J). */
 void or_derive(or_step_obs* r, int64_t n_occ, double J);
 
+/* Simulated PMOKE image (Sec. 6): for every pixel the topmost occupied site z = H(x,y) - 1;
+ * 255 (white) if its spin is up, 0 (black) if down, 128 where the pixel holds no atom.
+ * out: rows*cols bytes, [y][x].  Returns the number of up surface pixels. */
+int64_t or_surface_image(const or_film* f, uint8_t* out);
+
 /* Exact Gibbs averages over all 2^N states of the occupied sites (Eqs. 4-5), N <= 24.
  * out: <M>, <|M|>, <M^2>, <E>, <E^2>, <B>. */
 int  or_exact(const or_film* f, double T, double h, double J, double* out);

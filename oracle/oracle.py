@@ -113,6 +113,8 @@ def _declare(lib):
     lib.or_derive.restype = None
     lib.or_exact.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, dp]
     lib.or_exact.restype = C.c_int
+    lib.or_surface_image.argtypes = [C.c_void_p, C.POINTER(C.c_uint8)]
+    lib.or_surface_image.restype = C.c_int64
 
 
 def _ptr(a: np.ndarray, ct):
@@ -253,6 +255,11 @@ class Film:
         if rc != 0:
             raise OracleError(rc, "run")
         return records_to_dicts(recs[:n]), ser
+
+    def surface_image(self) -> np.ndarray:
+        out = np.zeros((self.rows, self.cols), dtype=np.uint8)
+        self.lib.or_surface_image(self._h, _ptr(out, C.c_uint8))
+        return out
 
     def exact(self, T, h, J=1.0) -> dict:
         out = np.zeros(6, dtype=np.float64)

@@ -361,6 +361,36 @@ int isf_read_spins(isf_lattice* L, int8_t* host_out) {
     return ISF_OK;
 }
 
+int isf_read_surface_image(isf_lattice* L, uint8_t* host_out, int64_t* n_up) {
+    if (!L || !host_out) return fail(ISF_ERR_ARG, "bad arguments");
+    int rc = sync_film(L);
+    if (rc) return rc;
+    const size_t n = (size_t)L->lay.R * L->lay.C;
+    uint8_t* d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, n + 256), "cudaMalloc image buffer");
+    unsigned long long* up = reinterpret_cast<unsigned long long*>(d + ((n + 7) & ~size_t(7)));
+    cudaError_t ce = cudaMemsetAsync(up, 0, sizeof(unsigned long long), L->last);
+    if (ce == cudaSuccess) ce = (cudaError_t)launch_surface(L->f, d, up, L->last);
+    unsigned long long nup = 0;
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(host_out, d, n, cudaMemcpyDeviceToHost, L->last);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&nup, up, sizeof nup, cudaMemcpyDeviceToHost, L->last);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(L->last);
+    cudaFree(d);
+    if (ce != cudaSuccess) return cuda_fail(ce, "surface image");
+    if (n_up) *n_up = (int64_t)nup;
+    return ISF_OK;
+}
+
+int isf_lattice_stats(isf_lattice* L, double* p, double* zbar, double* p_c) {
+    if (!L) return fail(ISF_ERR_ARG, "lattice is NULL");
+    const double sites = (double)L->lay.R * L->lay.C * L->lay.L;
+    const double z = L->n_occ ? 2.0 * (double)L->n_bonds / (double)L->n_occ : 0.0;
+    if (p) *p = (double)L->n_occ / sites;
+    if (zbar) *zbar = z;
+    if (p_c) *p_c = z > 0 ? 2.0 / z : INFINITY;
+    return ISF_OK;
+}
+
 int isf_write_spins(isf_lattice* L, const int8_t* host_in, int64_t sweep) {
     if (!L || !host_in || sweep < 0) return fail(ISF_ERR_ARG, "bad arguments");
     const int R = L->lay.R, C = L->lay.C, Lz = L->lay.L;

@@ -128,6 +128,7 @@ int launch_recompute(const DevFilm& f, FilmState* st, void* stream);  // M, B, n
 int launch_sweeps(const SweepArgs& a, int ctas, int threads, void* stream);
 int launch_unpack(const DevFilm& f, int8_t* dev_out, void* stream);
 int launch_pack(const DevFilm& f, const int8_t* dev_in, void* stream);
+int launch_surface(const DevFilm& f, uint8_t* dev_out, unsigned long long* dev_up, void* stream);
 int launch_philox_blocks(uint64_t seed, uint32_t stream_id, uint64_t sweep, uint32_t q0,
                          int64_t nblocks, uint32_t* dev_out, void* stream);
 int sweep_max_ctas_for(const DevFilm& f, int threads, int* max_ctas);  // co-resident CTAs

@@ -153,6 +153,27 @@ __global__ void k_unpack(DevFilm f, int8_t* out) {
     }
 }
 
+// Simulated PMOKE image (Sec. 6): per pixel the surface atom, which is at z = H(x,y) - 1 since
+// a pixel fills its layers from the substrate up; 255 if its spin is up, 0 if down, 128 where
+// the pixel holds no atom.  *up counts the white pixels.
+__global__ void k_surface(DevFilm f, uint8_t* out, unsigned long long* up) {
+    const int64_t total = (int64_t)f.R * f.C;
+    unsigned long long n = 0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(t % f.C), y = (int)(t / f.C);
+        const int H = f.heights[t];
+        uint8_t v = 128;
+        if (H > 0) {
+            v = site_spin(f, x, y, H - 1) > 0 ? 255 : 0;
+            n += v == 255;
+        }
+        out[t] = v;
+    }
+    n = (unsigned long long)warp_sum((long long)n);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(up, n);
+}
+
 __global__ void k_philox_blocks(uint64_t seed, uint32_t stream_id, uint64_t sweep, uint32_t q0,
                                 int64_t n, uint4* out) {
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n;
@@ -200,6 +221,12 @@ int launch_recompute(const DevFilm& f, FilmState* st, void* stream) {
 int launch_unpack(const DevFilm& f, int8_t* dev_out, void* stream) {
     const int64_t total = (int64_t)f.L * f.R * f.C;
     k_unpack<<<grid_for(total), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(f, dev_out);
+    return (int)cudaGetLastError();
+}
+
+int launch_surface(const DevFilm& f, uint8_t* dev_out, unsigned long long* dev_up, void* stream) {
+    const int64_t total = (int64_t)f.R * f.C;
+    k_surface<<<grid_for(total), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(f, dev_out, dev_up);
     return (int)cudaGetLastError();
 }
 

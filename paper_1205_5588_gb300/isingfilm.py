@@ -68,6 +68,8 @@ def _declare(lib):
         "isf_read_trace": (C.c_int, [vp, i64p, C.c_int64, i64p]),
         "isf_set_launch": (C.c_int, [vp, C.c_int32, C.c_int32]),
         "isf_set_path": (C.c_int, [vp, C.c_int32]),
+        "isf_read_surface_image": (C.c_int, [vp, u8p, i64p]),
+        "isf_lattice_stats": (C.c_int, [vp, dp, dp, dp]),
         "isf_launch_info": (C.c_int, [vp, i32p, i32p, i32p]),
         "isf_save": (C.c_int, [vp, C.c_char_p]),
         "isf_load": (C.c_int, [C.c_char_p, vp, C.POINTER(vp)]),
@@ -237,6 +239,19 @@ class Lattice:
         _check(lib.isf_read_spins(self._h, _ptr(out, C.c_int8)), "read_spins")
         return out
 
+    def surface_image(self) -> np.ndarray:
+        """Simulated PMOKE image (255 up, 0 down, 128 no atom), rows x cols uint8."""
+        out = np.zeros((self.rows, self.cols), dtype=np.uint8)
+        n = C.c_int64()
+        _check(lib.isf_read_surface_image(self._h, _ptr(out, C.c_uint8), C.byref(n)), "read_surface_image")
+        return out
+
+    def stats(self) -> dict:
+        """Concentration p, mean coordination zbar and critical concentration p_c = 2/zbar (Eq. 2)."""
+        p, z, pc = C.c_double(), C.c_double(), C.c_double()
+        _check(lib.isf_lattice_stats(self._h, C.byref(p), C.byref(z), C.byref(pc)), "lattice_stats")
+        return {"p": p.value, "zbar": z.value, "p_c": pc.value}
+
     def write_spins(self, s, sweep):
         s = np.ascontiguousarray(s, dtype=np.int8)
         _check(lib.isf_write_spins(self._h, _ptr(s, C.c_int8), int(sweep)), "write_spins")
@@ -346,6 +361,14 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def estimate_tc(records) -> float:
+    """Curie-temperature estimate of a temperature scan: the T of the largest susceptibility
+    chi' = (<M^2> - <|M|>^2) / (N T) among the scan's records (a finite film has no sharp
+    transition; this is the position of its susceptibility peak)."""
+    best = max((r for r in records if r["n_meas"] > 0), key=lambda r: r["chi_abs"])
+    return float(best["T"])
 
 
 JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}

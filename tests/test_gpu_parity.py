@@ -293,3 +293,38 @@ def test_runs_on_a_side_stream(I):
     lat.run(-1, stream=s)
     assert_records_equal(lat.observables(), run_oracle(spec, sched)["recs"])
     lat.close()
+
+
+@pytest.mark.parametrize("packed", [False, True])
+def test_surface_image_and_stats_match_oracle(I, packed):
+    """PMOKE frames (Sec. 6) along a hysteresis loop and the Table 1 statistics (Sec. 4)."""
+    from oracle import oracle
+    spec = film(W.fractal_heights(37, 61, 0.7, 0, 4, seed=17), 4, seed=23)
+    lat = I.Lattice(spec["heights"], 4, seed=23, packed=packed)
+    of = oracle.Film(spec["heights"], 4, seed=23)
+    h = W.loop_fields(8, 4)
+    lat.set_schedule(np.full(len(h), 2.5), h, np.zeros(len(h), np.int32), np.full(len(h), 3, np.int32))
+    for k in range(len(h)):
+        lat.run(3)
+        of.run([2.5], [h[k]], [0], [3])
+        img = lat.surface_image()
+        assert np.array_equal(img, of.surface_image()), k
+    st = lat.stats()
+    info = of.info()
+    assert st["zbar"] == 2 * info["n_bonds"] / info["n_occ"]
+    assert st["p_c"] == 2.0 / st["zbar"]
+    assert st["p"] == info["n_occ"] / (37 * 61 * 4)
+    lat.close()
+
+
+def test_curie_estimate_of_a_scan(I):
+    """The susceptibility peak of a scan of a thick periodic film sits below the bulk FCC T_c."""
+    spec = film(np.full((16, 16), 8), 8, seed=3, periodic_x=True, periodic_y=True)
+    T = np.linspace(6.0, 12.0, 13)
+    lat = I.Lattice(spec["heights"], 8, seed=3, periodic_x=True, periodic_y=True)
+    sc = W.schedule(T, 0.0, 300, 600)
+    lat.set_schedule(sc["T"], sc["h"], sc["eq"], sc["meas"])
+    lat.run(-1)
+    tc = I.estimate_tc(lat.observables())
+    assert 7.0 <= tc <= 10.0
+    lat.close()

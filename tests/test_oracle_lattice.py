@@ -135,3 +135,47 @@ def test_occupancy_rule_and_init(olib):
                 assert s[z, y, x] in vals
             else:
                 assert s[z, y, x] == 0
+
+
+def _table1():
+    import os
+    rows = []
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_critical_concentration.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            rows.append([float(v) for v in line.split()])
+    return rows
+
+
+def test_table1_rows_obey_eq2():
+    """The paper's Table 1: p_c = 2 / z-bar (Eq. 2) on every row, to the printed precision; and
+    the concentration is the monolayer count over a 4-layer film, up to rounding of image data."""
+    for ml, zbar, tc, p, pc in _table1():
+        assert round(2.0 / zbar, 2) == pytest.approx(pc, abs=0.011)
+        assert p == pytest.approx(ml / 4.0, abs=0.011)
+
+
+def test_mean_coordination_and_critical_concentration(olib):
+    """z-bar = 2 * bonds / sites: 12 for the bulk, 12 - 6/L for a full periodic L-layer film,
+    hence p_c = 2 / z-bar (Eq. 2) = 1/6 in the bulk."""
+    f = oracle.Film(np.full((4, 4), 4, dtype=np.uint8), 4, flags=7, lib=olib)
+    info = f.info()
+    assert 2 * info["n_bonds"] / info["n_occ"] == 12.0
+    for n in (1, 2, 3, 5):
+        g = oracle.Film(np.full((6, 6), n, dtype=np.uint8), n, flags=3, lib=olib).info()
+        assert 2 * g["n_bonds"] / g["n_occ"] == pytest.approx(12.0 - 6.0 / n)
+
+
+def test_surface_image(olib):
+    """Sec. 6: white where the topmost atom of the pixel is up, black where down, no-atom grey."""
+    H = np.array([[0, 1, 2], [2, 0, 1]], dtype=np.uint8)
+    f = oracle.Film(H, 2, init=oracle.INIT_UP, lib=olib)
+    img = f.surface_image()
+    assert img.tolist() == [[128, 255, 255], [255, 128, 255]]
+    s = f.spins()
+    s[1, 0, 2] = -1                       # the top atom of pixel (x=2, y=0) is at z = 1
+    s[0, 1, 2] = -1                       # the top atom of pixel (x=2, y=1) is at z = 0
+    s[0, 0, 2] = -1                       # below a surface atom: not visible
+    f.set_spins(s)
+    img = f.surface_image()
+    assert img.tolist() == [[128, 255, 0], [255, 128, 0]]
