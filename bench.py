@@ -111,13 +111,11 @@ def attempts_of(spec, n_occ):
 
 def run_impl(args):
     import torch
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+    from paper_1205_5588_gb300 import distributed as D
+    ranks = D.env_ranks()
+    torch.cuda.set_device(ranks.local if ranks.world > 1 else 0)
+    ranks = D.init("nccl")
+    ws, rank = ranks.world, ranks.rank
     dev = torch.cuda.current_device()
     from paper_1205_5588_gb300 import build as B
     B.build()
@@ -125,7 +123,7 @@ def run_impl(args):
 
     spec = workload(args.workload)
     sched = spec["schedule"]
-    seed = spec["seed"] + 1000003 * rank        # each rank: its own replica
+    seed = D.replica_seed(spec["seed"], rank)   # a single film does not shard: one replica per rank
     stream = torch.cuda.current_stream()
     lat = I.Lattice(spec["heights"], spec["layers"], periodic_x=spec["periodic_x"], periodic_y=spec["periodic_y"],
                     packed=spec["packed"], seed=seed, init=spec["init"], stream=stream)
@@ -147,8 +145,7 @@ def run_impl(args):
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
+    D.barrier(ranks)
     clocks = Clocks(dev) if rank == 0 else None
     times = []
     for _ in range(args.steps):
@@ -158,12 +155,8 @@ def run_impl(args):
         times.append(a.elapsed_time(b) / 1e3)
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
-    total = sum(times)
-    if ws > 1:
-        t = torch.tensor([total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
-        torch.distributed.barrier()
+    total = D.max_over_ranks(sum(times), ranks, device="cuda")
+    D.barrier(ranks)
     recs = lat.observables()
     shape = lat.launch_info()
     lat.close()
@@ -219,24 +212,31 @@ def run_impl(args):
                      "ops_per_attempt": OPS_PER_ATTEMPT},
         "clocks": clk,
     }
-    if rank == 0 and not args.no_batched:
-        line["batched"] = measure_batched(I, n_films=args.batch_films, sweeps_per_step=args.batch_sweeps)
+    if not args.no_batched:
+        # independent films: each rank runs its own share of the list (weak scaling)
+        b = measure_batched(I, n_films=args.batch_films, sweeps_per_step=args.batch_sweeps, ranks=ranks,
+                            plain=ranks.world == 1)
+        if rank == 0:
+            line["batched"] = b
     if rank == 0 and not args.no_served:
         line["served"] = measure_served(I, rate=args.serve_rate, duration=args.serve_seconds)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, budget_s=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    D.finish(ranks)
 
 
-def measure_batched(I, n_films=128, sweeps_per_step=20, seed=4, plain=True):
+def measure_batched(I, n_films=128, sweeps_per_step=20, seed=4, plain=True, ranks=None):
     """Batched films (ragged sizes 64..1024, 1..8 layers, own T and field loop each) advanced to
-    the end of their schedules by isf_batch_run, against the same films run one per launch."""
+    the end of their schedules by isf_batch_run, against the same films run one per launch.
+    Under several ranks each rank runs its round-robin share of the films."""
     import torch
+    from paper_1205_5588_gb300 import distributed as D
     from paper_1205_5588_gb300 import workloads as W
+    ranks = ranks or D.env_ranks()
     films = W.batch_films(n_films, seed=seed, sweeps_per_step=sweeps_per_step)
+    films = [films[i] for i in D.shard(len(films), ranks.rank, ranks.world)]
     lats = []
     for f in films:
         L = I.Lattice(f["heights"], f["layers"], seed=f["seed"])
@@ -255,14 +255,17 @@ def measure_batched(I, n_films=128, sweeps_per_step=20, seed=4, plain=True):
     b.run()                       # warm: kernels loaded, graph captured
     torch.cuda.synchronize()
     reset()
+    D.barrier(ranks)
     a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     b.run()
     e.record()
     e.synchronize()
-    t_batch = a.elapsed_time(e) / 1e3
-    out = {"value": att / t_batch, "unit": UNIT, "films": n_films, "attempts": att, "seconds": t_batch,
-           "sweeps_per_step": sweeps_per_step, "launch": b.info(), "graph": True}
+    t_batch = D.max_over_ranks(a.elapsed_time(e) / 1e3, ranks, device="cuda")
+    att_all = int(D.sum_over_ranks(att, ranks, device="cuda"))
+    out = {"value": att_all / t_batch, "unit": UNIT, "films": n_films, "attempts": att_all, "seconds": t_batch,
+           "sweeps_per_step": sweeps_per_step, "launch": b.info(), "graph": True,
+           "ranks": ranks.world, "scaling": "weak (films dealt out across ranks)"}
     b.close()
     if plain:
         reset()
