@@ -177,6 +177,12 @@ int isf_set_path(isf_lattice* lat, int32_t path);
  * not depend on it. */
 int isf_set_launch(isf_lattice* lat, int32_t ctas, int32_t threads);
 
+/* Sites per work item of the resident kernel: 16, 8, or 0 = automatic (8 when a quarter or more
+ * of the sites of 16-site items would be padding past the end of the row, i.e. narrow rows).  An item is one thread's
+ * share of a colour pass: the same row, consecutive columns (Sec. 3's checkerboard update).
+ * Trajectories do not depend on it.  Errors: ISF_ERR_ARG (other values).  No device work. */
+int isf_set_item_sites(isf_lattice* lat, int32_t sites);
+
 /* The resident and batch kernels check every address they derive from a film's description and
  * skip (and record) an out-of-range access instead of making it.  This returns the first one
  * recorded in the process as (code, value, value, 0); all zeros when none.  The read functions
@@ -186,6 +192,9 @@ int isf_debug_checks(uint64_t* out4);
 /* Shape of the last isf_run_sweeps launch: path (ISF_PATH_GLOBAL / ISF_PATH_RESIDENT, 0 before
  * any launch), CTAs (global) or cluster size (resident), threads per CTA.  No device work. */
 int isf_launch_info(isf_lattice* lat, int32_t* path, int32_t* ctas, int32_t* threads);
+/* Sites per work item of the last isf_run_sweeps launch (16 or 8 resident, 16 int8 global, 32
+ * packed global; 0 before any launch).  No device work. */
+int isf_launch_item_sites(isf_lattice* lat, int32_t* sites);
 
 /* Save the film (shape, flags, seed, spins, sweep counter) to a file; load it back onto the
  * current device (schedule not saved).  Errors: ISF_ERR_ARG, ISF_ERR_CUDA, ISF_ERR_OOM. */

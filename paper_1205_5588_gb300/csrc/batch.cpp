@@ -229,7 +229,7 @@ int isf_batch_tune(isf_batch* b, void* cuda_stream) {
     for (isf_lattice* L : b->films) {
         if (L->lay.packed) continue;
         ResPlan p;
-        const int cls = resident_plan(L->f, 1, 0, &p) == 0 ? 0 : (resident_plan(L->f, 16, 0, &p) == 0 ? 1 : -1);
+        const int cls = resident_plan(L->f, 1, 0, 16, &p) == 0 ? 0 : (resident_plan(L->f, 16, 0, 16, &p) == 0 ? 1 : -1);
         cudaGetLastError();
         if (cls < 0) continue;
         const double w = (double)L->lay.L * L->lay.Rh * L->lay.Ch;
@@ -291,8 +291,8 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
         Item it{L, n, {}, (double)n * L->lay.L * L->lay.Rh * L->lay.Ch};
         // the queue kernels hold int8 films without periodic columns
         const bool queueable = !L->lay.packed && !(L->lay.flags & ISF_PERIODIC_X);
-        if (queueable && resident_plan(L->f, 1, ta, &it.plan) == 0) A.push_back(it);
-        else if (queueable && resident_plan(L->f, K, tb, &it.plan) == 0) B.push_back(it);
+        if (queueable && resident_plan(L->f, 1, ta, 16, &it.plan) == 0) A.push_back(it);
+        else if (queueable && resident_plan(L->f, K, tb, 16, &it.plan) == 0) B.push_back(it);
         else C.push_back(L);
         cudaGetLastError();
     }

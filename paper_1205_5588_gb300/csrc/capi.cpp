@@ -290,11 +290,12 @@ int isf_run_sweeps(isf_lattice* L, int64_t nsweeps, void* cuda_stream) {
     if (L->path != ISF_PATH_GLOBAL && !L->lay.packed) {
         ResPlan plan;
         const bool forced = L->path == ISF_PATH_RESIDENT;
-        if (resident_plan(L->f, L->ctas, L->threads, &plan) == 0) {
+        if (resident_plan(L->f, L->ctas, L->threads, L->item_sites, &plan) == 0) {
             int e = launch_resident(a, plan, s);
             if (e) return cuda_fail((cudaError_t)e, "resident sweep kernel launch");
             launched = true;
             L->last_path = ISF_PATH_RESIDENT; L->last_ctas = plan.K; L->last_threads = plan.threads;
+            L->last_sites = plan.item_sites;
         } else {
             cudaGetLastError();
             if (forced) return fail(ISF_ERR_ARG, "film does not fit one cluster's shared memory with this launch shape");
@@ -316,6 +317,7 @@ int isf_run_sweeps(isf_lattice* L, int64_t nsweeps, void* cuda_stream) {
         e = launch_sweeps(a, ctas, threads, s);
         if (e) return cuda_fail((cudaError_t)e, "sweep kernel launch");
         L->last_path = ISF_PATH_GLOBAL; L->last_ctas = ctas; L->last_threads = threads;
+        L->last_sites = L->lay.packed ? 32 : 16;
     }
     L->last = s;
     advance_cursor(L, nsweeps);
@@ -478,6 +480,19 @@ int isf_set_launch(isf_lattice* L, int32_t ctas, int32_t threads) {
         return fail(ISF_ERR_ARG, "threads must be 0 or a multiple of 32 in 32..1024");
     L->ctas = ctas;
     L->threads = threads;
+    return ISF_OK;
+}
+
+int isf_set_item_sites(isf_lattice* L, int32_t sites) {
+    if (!L) return fail(ISF_ERR_ARG, "lattice is NULL");
+    if (sites != 0 && sites != 8 && sites != 16) return fail(ISF_ERR_ARG, "sites per work item must be 0, 8 or 16");
+    L->item_sites = sites;
+    return ISF_OK;
+}
+
+int isf_launch_item_sites(isf_lattice* L, int32_t* sites) {
+    if (!L || !sites) return fail(ISF_ERR_ARG, "bad arguments");
+    *sites = L->last_sites;
     return ISF_OK;
 }
 

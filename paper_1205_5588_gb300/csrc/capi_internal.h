@@ -43,8 +43,10 @@ struct isf_lattice {
     int64_t trace_cap = 0, trace_n = 0;
     // launch shape and path
     int32_t ctas = 0, threads = 0;
+    int32_t item_sites = 0;         // resident kernel's sites per work item (0: automatic)
     int32_t path = ISF_PATH_AUTO;
     int32_t last_path = 0, last_ctas = 0, last_threads = 0;   // shape of the last sweep launch
+    int32_t last_sites = 0;
     cudaStream_t last = nullptr;
 };
 

@@ -138,10 +138,12 @@ int sweep_max_ctas_for(const DevFilm& f, int threads, int* max_ctas);  // co-res
 struct ResPlan {
     int32_t K, Jb, threads;
     uint32_t film_off, vac_off, ptr_off, misc_off, smem;
+    int32_t item_sites;     // 16 or 8 sites per work item
 };
-// Plan for a film: K = want_K (0: automatic), threads = want_threads (0: automatic).
-// Returns 0 and fills out when the film fits, else a nonzero code (no device work).
-int resident_plan(const DevFilm& f, int want_K, int want_threads, ResPlan* out);
+// Plan for a film: K = want_K (0: automatic), threads = want_threads (0: automatic), sites per
+// work item = want_sites (0: automatic, 8 or 16).  Returns 0 and fills out when the film fits,
+// else a nonzero code (no device work).
+int resident_plan(const DevFilm& f, int want_K, int want_threads, int want_sites, ResPlan* out);
 int launch_resident(const SweepArgs& a, const ResPlan& plan, void* stream);
 
 // One film's launch arguments for the resident kernels (also the batch queue's entries).

@@ -33,7 +33,10 @@ __device__ unsigned long long g_isf_check[4];
 namespace {
 
 constexpr int kMaxK = 16;
-constexpr int kMaxResThreads = 512;     // up to 128 registers per thread
+constexpr int kMaxResThreads = 512;     // up to 128 registers per thread (16-site items)
+constexpr int kMaxResThreads8 = 768;    // up to 80 registers per thread (8-site items)
+template <int NW>
+constexpr int max_threads_for() { return NW == 2 ? kMaxResThreads8 : kMaxResThreads; }
 constexpr uint32_t kMiscBytes = 128 * 4 + 16 + 64 * 8 + 2 * kMaxK * 8 + kMaxK * 8;
 
 
@@ -91,6 +94,46 @@ __device__ __forceinline__ uint32_t lds4(uint32_t a) {
     return v;
 }
 
+template <bool CLUSTER>
+__device__ __forceinline__ uint2 lds8(uint32_t a) {
+    uint2 v;
+    if (CLUSTER)
+        asm volatile("ld.shared::cluster.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a) : "memory");
+    else
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a) : "memory");
+    return v;
+}
+
+// Neighbour sum of an 8-site half chunk from shared::cluster addresses.
+template <bool CLUSTER>
+__device__ __forceinline__ uint2 neighbour_sum8_sc(const uint32_t* nb, int sgn) {
+    uint2 acc = lds8<CLUSTER>(nb[0]);
+#pragma unroll
+    for (int k = 1; k < 9; ++k) {
+        const uint2 v = lds8<CLUSTER>(nb[k]);
+        acc.x += v.x;
+        acc.y += v.y;
+    }
+    if (sgn < 0) {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) {
+            const uint2 v = lds8<CLUSTER>(nb[k]);
+            const uint32_t e = lds4<CLUSTER>(nb[k] - 4);
+            acc.x += __funnelshift_l(e, v.x, 8);
+            acc.y += __funnelshift_l(v.x, v.y, 8);
+        }
+    } else {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) {
+            const uint2 v = lds8<CLUSTER>(nb[k]);
+            const uint32_t e = lds4<CLUSTER>(nb[k] + 8);
+            acc.x += __funnelshift_r(v.x, v.y, 8);
+            acc.y += __funnelshift_r(v.y, e, 8);
+        }
+    }
+    return acc;
+}
+
 // Neighbour sum of a 16-site chunk from shared::cluster addresses (see neighbour_sum16).
 template <bool CLUSTER>
 __device__ __forceinline__ uint4 neighbour_sum16_sc(const uint32_t* nb, int sgn) {
@@ -125,8 +168,12 @@ __device__ __forceinline__ void sync_all() {
 
 // One film on this CTA (CLUSTER = false) or on this cluster: slab in, the launch's sweeps,
 // slab out.  Ends with a barrier over all CTAs that took part.
-template <bool CLUSTER, bool PX>
+// NW = 4: 16-site work items; NW = 2: 8-site items (twice the items per pass, for films whose
+// 16-site items would leave the CTA's warps too few to hide the shared-memory latency).
+template <bool CLUSTER, bool PX, int NW = 4>
 __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
+    static_assert(NW == 2 || NW == 4, "work items are 8 or 16 sites");
+    constexpr int W = 4 * NW;   // sites (bytes) per item
     const SweepArgs& s = a.s;
     const DevFilm& f = s.f;
     const unsigned K = CLUSTER ? (unsigned)a.K : 1u;
@@ -199,9 +246,10 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
     }
     sync_all<CLUSTER>();    // every slab loaded before anyone reads a neighbour's
 
-    const int items = L * nown * nck;
+    const int nci = NW == 4 ? nck : (Ch + 7) / 8;     // items per row
+    const int items = L * nown * nci;
     ItemWalk walk0;
-    walk0.init(threadIdx.x, blockDim.x, nck, nown > 0 ? nown : 1);
+    walk0.init(threadIdx.x, blockDim.x, nci, nown > 0 ? nown : 1);
     int k = s.k0, pos = s.pos0;
     const bool folder = rank == 0 && threadIdx.x == 0;
     __shared__ RunState rs;     // touched by the folding thread only
@@ -227,37 +275,48 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
             for (int it = threadIdx.x; it < items; it += blockDim.x, w.next()) {
                 const int ck = w.ck, jl = w.jr, z = w.z;
                 const size_t r = (size_t)(c * L + z) * Jb + jl;
-                if (!ISF_CHECK(z >= 0 && z < L && jl >= 0 && jl < nown && ck >= 0 && ck < nck, 8, it, ((uint64_t)z << 32) | (uint32_t)jl)) continue;
+                if (!ISF_CHECK(z >= 0 && z < L && jl >= 0 && jl < nown && ck >= 0 && ck < nci, 8, it, ((uint64_t)z << 32) | (uint32_t)jl)) continue;
                 uint8_t* row = film + r * P;
-                uint8_t* own = row + 16 + 16 * ck;
+                uint8_t* own = row + 16 + W * ck;
                 const uint32_t* pr = ptrs + r * 12;
                 uint32_t nbp[12];
 #pragma unroll
-                for (int kk = 0; kk < 12; ++kk) nbp[kk] = pr[kk] + 16 + 16 * ck;
-                const uint32_t q0 = block_counter(f, c, z, j0 + jl, 16 * ck);
+                for (int kk = 0; kk < 12; ++kk) nbp[kk] = pr[kk] + 16 + W * ck;
+                const uint32_t q0 = block_counter(f, c, z, j0 + jl, W * ck);
                 const int sgn = f.nb[c][z & 1].sgn;
-                const uint4 S = *reinterpret_cast<const uint4*>(own);
-                const uint4 acc = neighbour_sum16_sc<CLUSTER>(nbp, sgn);
-                const uint32_t Sw[4] = {S.x, S.y, S.z, S.w};
-                const uint32_t Aw[4] = {acc.x, acc.y, acc.z, acc.w};
-                uint32_t fm[4];
+                uint32_t Sw[NW], Aw[NW];
+                if constexpr (NW == 4) {
+                    const uint4 S = *reinterpret_cast<const uint4*>(own);
+                    const uint4 acc = neighbour_sum16_sc<CLUSTER>(nbp, sgn);
+                    Sw[0] = S.x; Sw[1] = S.y; Sw[2] = S.z; Sw[3] = S.w;
+                    Aw[0] = acc.x; Aw[1] = acc.y; Aw[2] = acc.z; Aw[3] = acc.w;
+                } else {
+                    const uint2 S = *reinterpret_cast<const uint2*>(own);
+                    const uint2 acc = neighbour_sum8_sc<CLUSTER>(nbp, sgn);
+                    Sw[0] = S.x; Sw[1] = S.y;
+                    Aw[0] = acc.x; Aw[1] = acc.y;
+                }
+                uint32_t fm[NW];
                 const uint32_t any = s.use_gate
-                    ? decide16<true, PX>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, 16 * ck, Ch, fm, dM, dB)
-                    : decide16<false, PX>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, 16 * ck, Ch, fm, dM, dB);
+                    ? decide16<true, PX, NW>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB)
+                    : decide16<false, PX, NW>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB);
                 if (any) {
                     if (!PX) {
-                        *reinterpret_cast<uint4*>(own) = make_uint4(Sw[0] ^ fm[0], Sw[1] ^ fm[1], Sw[2] ^ fm[2], Sw[3] ^ fm[3]);
+                        if constexpr (NW == 4)
+                            *reinterpret_cast<uint4*>(own) = make_uint4(Sw[0] ^ fm[0], Sw[1] ^ fm[1], Sw[2] ^ fm[2], Sw[3] ^ fm[3]);
+                        else
+                            *reinterpret_cast<uint2*>(own) = make_uint2(Sw[0] ^ fm[0], Sw[1] ^ fm[1]);
                     } else {
                         // byte stores (the row's wrap bytes may share a word), refreshing the
                         // wrap copies of columns 0 and Ch-1
 #pragma unroll
-                        for (int v = 0; v < 4; ++v) {
+                        for (int v = 0; v < NW; ++v) {
                             if (!fm[v]) continue;
 #pragma unroll
                             for (int b = 0; b < 4; ++b) {
                                 if (!((fm[v] >> (8 * b)) & 0xFFu)) continue;
                                 const uint8_t nbyte = (uint8_t)((Sw[v] ^ fm[v]) >> (8 * b));
-                                const int i = 16 * ck + 4 * v + b;
+                                const int i = W * ck + 4 * v + b;
                                 own[4 * v + b] = nbyte;
                                 if (i == 0) row[16 + Ch] = nbyte;
                                 if (i == Ch - 1) row[15] = nbyte;
@@ -307,10 +366,10 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
     sync_all<CLUSTER>();    // no CTA leaves while another may still address its shared memory
 }
 
-template <bool CLUSTER, bool PX>
-__global__ void __launch_bounds__(kMaxResThreads, 1) k_resident(const __grid_constant__ ResArgs a) {
+template <bool CLUSTER, bool PX, int NW>
+__global__ void __launch_bounds__(max_threads_for<NW>(), 1) k_resident(const __grid_constant__ ResArgs a) {
     extern __shared__ __align__(16) uint8_t sm[];
-    run_film<CLUSTER, PX>(a, sm);
+    run_film<CLUSTER, PX, NW>(a, sm);
 }
 
 // Batched films: every CTA (or cluster) takes the next film of the queue, runs its sweeps with
@@ -340,9 +399,9 @@ __global__ void __launch_bounds__(kMaxResThreads, 1) k_batch(const ResArgs* film
     }
 }
 
-template <bool CLUSTER, bool PX>
+template <bool CLUSTER, bool PX, int NW>
 int launch_variant(const ResArgs& ra, const ResPlan& p, cudaStream_t s) {
-    auto kern = k_resident<CLUSTER, PX>;
+    auto kern = k_resident<CLUSTER, PX, NW>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return (int)e;
     cudaLaunchConfig_t cfg{};
@@ -366,9 +425,9 @@ int launch_variant(const ResArgs& ra, const ResPlan& p, cudaStream_t s) {
     return (int)cudaLaunchKernelEx(&cfg, kern, ra);
 }
 
-template <bool CLUSTER, bool PX>
+template <bool CLUSTER, bool PX, int NW>
 int clusters_possible(const ResPlan& p, int* n) {
-    auto kern = k_resident<CLUSTER, PX>;
+    auto kern = k_resident<CLUSTER, PX, NW>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
     if (e != cudaSuccess) return (int)e;
     if (!CLUSTER) { *n = 1; return 0; }
@@ -412,8 +471,9 @@ bool layout_for(const DevFilm& f, int K, int threads, int max_smem, ResPlan* out
 
 }  // namespace
 
-int resident_plan(const DevFilm& f, int want_K, int want_threads, ResPlan* out) {
+int resident_plan(const DevFilm& f, int want_K, int want_threads, int want_sites, ResPlan* out) {
     if (f.packed) return 1;                               // int8 layout only
+    if (want_sites != 0 && want_sites != 8 && want_sites != 16) return 3;
     int dev = 0, max_smem = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 2;
     if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 2;
@@ -433,22 +493,37 @@ int resident_plan(const DevFilm& f, int want_K, int want_threads, ResPlan* out) 
     }
     for (int ci = 0; ci < nc; ++ci) {
         const int K = cand[ci];
-        ResPlan p;
-        // threads: one per 16-site chunk of a pass, rounded to whole warps, 64..512
+        const int Jb = (f.Rh + K - 1) / K;
+        const int64_t items16 = (int64_t)f.L * Jb * f.nck;
+        // 8-site items when a quarter or more of the 16-site items' sites would be padding past
+        // the row's last column (narrow rows); else 16, which costs fewer instructions per site
+        int sites = want_sites;
+        if (!sites) sites = 4 * (16 * f.nck - f.Ch) >= 16 * f.nck ? 8 : 16;
+        const int64_t items = sites == 8 ? (int64_t)f.L * Jb * ((f.Ch + 7) / 8) : items16;
+        const int tmax = sites == 8 ? kMaxResThreads8 : kMaxResThreads;
+        // threads: one per work item of a pass, rounded to whole warps, 64..tmax
         int th = threads;
         if (!th) {
-            const int Jb = (f.Rh + K - 1) / K;
-            const int64_t items = (int64_t)f.L * Jb * f.nck;
             th = (int)((items + 31) / 32 * 32);
             if (th < 64) th = 64;
-            if (th > kMaxResThreads) th = kMaxResThreads;
+            if (th > tmax) th = tmax;
         }
-        if (th > kMaxResThreads) return 3;
+        if (th > tmax) {
+            if (want_sites) return 3;
+            continue;
+        }
+        ResPlan p;
         if (!layout_for(f, K, th, max_smem, &p)) continue;
+        p.item_sites = sites;
         int n = 0;
         const bool px = (f.flags & 1u) != 0;
-        const int e = K > 1 ? (px ? clusters_possible<true, true>(p, &n) : clusters_possible<true, false>(p, &n))
-                            : (px ? clusters_possible<false, true>(p, &n) : clusters_possible<false, false>(p, &n));
+        int e;
+        if (sites == 8)
+            e = K > 1 ? (px ? clusters_possible<true, true, 2>(p, &n) : clusters_possible<true, false, 2>(p, &n))
+                      : (px ? clusters_possible<false, true, 2>(p, &n) : clusters_possible<false, false, 2>(p, &n));
+        else
+            e = K > 1 ? (px ? clusters_possible<true, true, 4>(p, &n) : clusters_possible<true, false, 4>(p, &n))
+                      : (px ? clusters_possible<false, true, 4>(p, &n) : clusters_possible<false, false, 4>(p, &n));
         if (e == 0 && n >= 1) {
             *out = p;
             return 0;
@@ -536,8 +611,12 @@ int launch_resident(const SweepArgs& a, const ResPlan& p, void* stream) {
     ResArgs ra = make_res_args(a, p);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool px = (a.f.flags & 1u) != 0;
-    if (p.K > 1) return px ? launch_variant<true, true>(ra, p, s) : launch_variant<true, false>(ra, p, s);
-    return px ? launch_variant<false, true>(ra, p, s) : launch_variant<false, false>(ra, p, s);
+    if (p.item_sites == 8) {
+        if (p.K > 1) return px ? launch_variant<true, true, 2>(ra, p, s) : launch_variant<true, false, 2>(ra, p, s);
+        return px ? launch_variant<false, true, 2>(ra, p, s) : launch_variant<false, false, 2>(ra, p, s);
+    }
+    if (p.K > 1) return px ? launch_variant<true, true, 4>(ra, p, s) : launch_variant<true, false, 4>(ra, p, s);
+    return px ? launch_variant<false, true, 4>(ra, p, s) : launch_variant<false, false, 4>(ra, p, s);
 }
 
 }  // namespace isf

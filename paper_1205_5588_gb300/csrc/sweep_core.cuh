@@ -58,17 +58,18 @@ __device__ __forceinline__ uint32_t gate_block(uint32_t lanes, uint32_t gthr, ui
     return lanes & keep;
 }
 
-// Four Philox4x32-10 blocks at consecutive counters, interleaved so that the four dependency
-// chains overlap (same rounds as philox10).
-__device__ __forceinline__ void philox10_x4(uint32_t q0, uint32_t s_lo, uint32_t s_hi, uint32_t stream,
-                                            uint32_t k0, uint32_t k1, uint4 out[4]) {
-    uint32_t c0[4], c1[4], c2[4], c3[4];
+// NW Philox4x32-10 blocks at consecutive counters, interleaved so that their dependency chains
+// overlap (same rounds as philox10).
+template <int NW>
+__device__ __forceinline__ void philox10_xn(uint32_t q0, uint32_t s_lo, uint32_t s_hi, uint32_t stream,
+                                            uint32_t k0, uint32_t k1, uint4 out[NW]) {
+    uint32_t c0[NW], c1[NW], c2[NW], c3[NW];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) { c0[v] = q0 + v; c1[v] = s_lo; c2[v] = s_hi; c3[v] = stream; }
+    for (int v = 0; v < NW; ++v) { c0[v] = q0 + v; c1[v] = s_lo; c2[v] = s_hi; c3[v] = stream; }
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
+        for (int v = 0; v < NW; ++v) {
             const uint32_t lo0 = 0xD2511F53u * c0[v];
             const uint32_t hi0 = __umulhi(0xD2511F53u, c0[v]);
             const uint32_t lo1 = 0xCD9E8D57u * c2[v];
@@ -82,26 +83,27 @@ __device__ __forceinline__ void philox10_x4(uint32_t q0, uint32_t s_lo, uint32_t
         k1 += 0xBB67AE85u;
     }
 #pragma unroll
-    for (int v = 0; v < 4; ++v) out[v] = make_uint4(c0[v], c1[v], c2[v], c3[v]);
+    for (int v = 0; v < NW; ++v) out[v] = make_uint4(c0[v], c1[v], c2[v], c3[v]);
 }
 
-// The Metropolis decisions of one 16-site chunk of an int8 colour row (Eq. 8; Eq. 9 gate).
+// The Metropolis decisions of one 4*NW-site chunk (NW words) of an int8 colour row (Eq. 8; Eq. 9
+// gate).
 // Sw: the chunk's 4 words of stored bytes (S + 1: 0 down, 1 vacancy, 2 up); Aw: per byte the
 // sum of the 12 neighbour bytes, n + 12.  All 16 table lookups first; then, if any lane's
-// threshold is neither 0 nor "always", the chunk's four Philox blocks at once (a real word
+// threshold is neither 0 nor "always", the chunk's NW Philox blocks at once (a real word
 // decides a 0 / "always" lane exactly as no word does, so computing it never changes a
 // result).  The flips come back as a byte mask per word (0 <-> 2 is XOR 2); dM and dB from
 // popcounts of that mask and a multiply-add of the masked neighbour sums.  PX: lanes past the
 // row end (column Ch on) are masked.  Returns the OR of the four masks.
-template <bool GATE, bool PX>
-__device__ __forceinline__ uint32_t decide16(const uint32_t Sw[4], const uint32_t Aw[4], uint32_t q0,
+template <bool GATE, bool PX, int NW = 4>
+__device__ __forceinline__ uint32_t decide16(const uint32_t Sw[NW], const uint32_t Aw[NW], uint32_t q0,
                                              unsigned long long sweep, const uint32_t* tab, uint32_t gthr,
-                                             uint32_t key0, uint32_t key1, int i0, int Ch, uint32_t fm[4],
+                                             uint32_t key0, uint32_t key1, int i0, int Ch, uint32_t fm[NW],
                                              int& dM, int& dB) {
-    uint32_t thr[16];
+    uint32_t thr[4 * NW];
     bool need = false;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < NW; ++v) {
         const uint32_t iw = (Sw[v] << 5) + Aw[v];
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
@@ -111,11 +113,13 @@ __device__ __forceinline__ uint32_t decide16(const uint32_t Sw[4], const uint32_
             need |= needs_word(t);
         }
     }
-    uint4 u[4] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
-    if (need) philox10_x4(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, key0, key1, u);
+    uint4 u[NW];
+#pragma unroll
+    for (int v = 0; v < NW; ++v) u[v] = make_uint4(0, 0, 0, 0);
+    if (need) philox10_xn<NW>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, key0, key1, u);
     uint32_t any = 0;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < NW; ++v) {
         uint32_t m = (metropolis_accept(u[v].x, thr[4 * v + 0]) ? 0x00000002u : 0u) |
                      (metropolis_accept(u[v].y, thr[4 * v + 1]) ? 0x00000200u : 0u) |
                      (metropolis_accept(u[v].z, thr[4 * v + 2]) ? 0x00020000u : 0u) |

@@ -71,6 +71,8 @@ def _declare(lib):
         "isf_read_surface_image": (C.c_int, [vp, u8p, i64p]),
         "isf_lattice_stats": (C.c_int, [vp, dp, dp, dp]),
         "isf_launch_info": (C.c_int, [vp, i32p, i32p, i32p]),
+        "isf_set_item_sites": (C.c_int, [vp, C.c_int32]),
+        "isf_launch_item_sites": (C.c_int, [vp, i32p]),
         "isf_save": (C.c_int, [vp, C.c_char_p]),
         "isf_load": (C.c_int, [C.c_char_p, vp, C.POINTER(vp)]),
         "isf_lattice_destroy": (None, [vp]),
@@ -286,10 +288,16 @@ class Lattice:
     def set_launch(self, ctas=0, threads=0):
         _check(lib.isf_set_launch(self._h, int(ctas), int(threads)), "set_launch")
 
+    def set_item_sites(self, sites=0):
+        """Sites per work item of the resident kernel: 16, 8 or 0 (automatic)."""
+        _check(lib.isf_set_item_sites(self._h, int(sites)), "set_item_sites")
+
     def launch_info(self) -> dict:
-        p, c, t = C.c_int32(), C.c_int32(), C.c_int32()
+        p, c, t, w = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         _check(lib.isf_launch_info(self._h, C.byref(p), C.byref(c), C.byref(t)), "launch_info")
-        return {"path": {0: None, 1: "global", 2: "resident"}[p.value], "ctas": c.value, "threads": t.value}
+        _check(lib.isf_launch_item_sites(self._h, C.byref(w)), "launch_item_sites")
+        return {"path": {0: None, 1: "global", 2: "resident"}[p.value], "ctas": c.value, "threads": t.value,
+                "item_sites": w.value}
 
     def set_path(self, path="auto"):
         """'resident' (film in one cluster's shared memory), 'global', or 'auto'."""

@@ -29,7 +29,8 @@ def oracle_flags(spec):
            (4 if spec.get("periodic_z") else 0)
 
 
-def run_gpu(I, spec, sched, *, packed=None, launch=None, chunks=None, trace=True, h_s=0.0, path="auto"):
+def run_gpu(I, spec, sched, *, packed=None, launch=None, chunks=None, trace=True, h_s=0.0, path="auto",
+            sites=0):
     packed = spec.get("packed", False) if packed is None else packed
     lat = I.Lattice(spec["heights"], spec["layers"], packed=packed, seed=spec["seed"], init=spec["init"],
                     **spec_flags(spec))
@@ -37,6 +38,8 @@ def run_gpu(I, spec, sched, *, packed=None, launch=None, chunks=None, trace=True
         lat.set_path(path)
     if launch:
         lat.set_launch(*launch)
+    if sites:
+        lat.set_item_sites(sites)
     total = int(sched["eq"].sum() + sched["meas"].sum())
     if trace:
         lat.enable_trace(total)
@@ -50,7 +53,7 @@ def run_gpu(I, spec, sched, *, packed=None, launch=None, chunks=None, trace=True
             lat.run(total - done)
     else:
         lat.run(-1)
-    out = {"recs": lat.observables(), "spins": lat.spins(), "info": lat.info(),
+    out = {"recs": lat.observables(), "spins": lat.spins(), "info": lat.info(), "launch": lat.launch_info(),
            "trace": lat.trace() if trace else None, "state": lat.state(recompute=True)}
     lat.close()
     return out

@@ -133,20 +133,27 @@ def test_fractal2048_int8_and_packed_identical(I):
     assert_records_equal(a["recs"], b["recs"])
 
 
-@pytest.mark.parametrize("packed,path", [(False, "global"), (True, "global"), (False, "resident")])
-def test_launch_shape_does_not_change_the_trajectory(I, packed, path):
+@pytest.mark.parametrize("packed,path,sites", [(False, "global", 0), (True, "global", 0), (False, "resident", 16),
+                                               (False, "resident", 8)])
+def test_launch_shape_does_not_change_the_trajectory(I, packed, path, sites):
     spec = film(W.fractal_heights(80, 120, 0.7, 1, 6, seed=5), 6, seed=11)
     sched = W.schedule([2.0, 6.0], [0.5, -0.5], [2, 2], [5, 5])
     ref = run_oracle(spec, sched)
     shapes = [(1, 256), (2, 64), (7, 128), (3, 32)] if path == "global" else \
              [(1, 512), (2, 256), (3, 128), (4, 512), (8, 64), (10, 96), (5, 0), (0, 0)]   # 40 colour rows
+    if sites == 8:
+        shapes += [(1, 768), (16, 0), (2, 736)]
     for launch in shapes:
-        g = run_gpu(I, spec, sched, packed=packed, launch=launch, path=path)
+        g = run_gpu(I, spec, sched, packed=packed, launch=launch, path=path, sites=sites)
         assert np.array_equal(g["trace"], ref["trace"]) and np.array_equal(g["spins"], ref["spins"]), launch
+        if sites:
+            assert g["launch"]["item_sites"] == sites
 
 
-@pytest.mark.parametrize("name", ["flat16", "periodic_y_only", "periodic_x_only", "cube4", "ragged", "f256_prefix"])
-def test_resident_path_matches_oracle(I, name):
+@pytest.mark.parametrize("sites", [16, 8])
+@pytest.mark.parametrize("name", ["flat16", "periodic_y_only", "periodic_x_only", "cube4", "ragged", "f256_prefix",
+                                  "ragged_x9"])
+def test_resident_path_matches_oracle(I, name, sites):
     sched = W.schedule([2.0, 8.0, 5.0], [1.0, 0.0, -1.0], [1, 1, 1], [4, 4, 4])
     if name == "flat16":
         spec = W.flat16_hysteresis()
@@ -159,6 +166,9 @@ def test_resident_path_matches_oracle(I, name):
         spec = film(np.full((4, 4), 4), 4, seed=6, periodic_x=True, periodic_y=True, periodic_z=True)
     elif name == "ragged":
         spec = film(W.fractal_heights(45, 83, 0.6, 0, 5, seed=10), 5, seed=12)
+    elif name == "ragged_x9":
+        # 9 columns per colour row: an 8-site item and a 1-site one, periodic columns
+        spec = film(W.fractal_heights(10, 18, 0.6, 1, 3, seed=15), 3, seed=16, periodic_x=True)
     else:
         spec = W.fractal256_tscan()
         s = spec["schedule"]
@@ -169,7 +179,17 @@ def test_resident_path_matches_oracle(I, name):
     for launch in launches:
         if launch[0] > (spec["heights"].shape[0] + 1) // 2:
             continue
-        assert_same_run(run_gpu(I, spec, sched, launch=tuple(launch), path="resident"), o)
+        g = run_gpu(I, spec, sched, launch=tuple(launch), path="resident", sites=sites)
+        assert g["launch"]["item_sites"] == sites
+        assert_same_run(g, o)
+
+
+@pytest.mark.parametrize("sites", [16, 8])
+def test_resident_gate_parity(I, sites):
+    spec = film(W.fractal_heights(30, 70, 0.7, 1, 4, seed=9), 4, seed=5)
+    sched = W.schedule([2.0, 4.0, 6.0], [2.0, -2.0, 0.5], [2, 2, 2], [4, 4, 4])
+    o = run_oracle(spec, sched, h_s=4.0)
+    assert_same_run(run_gpu(I, spec, sched, h_s=4.0, path="resident", sites=sites), o)
 
 
 def test_paths_interleave(I):
@@ -280,6 +300,10 @@ def test_errors_are_reported(I):
     with pytest.raises(I.IsfError) as e:
         lat.set_schedule([2.0], [0.0], [0], [0])
     assert e.value.code == -5
+    for bad in (4, 12, 32, -8):
+        with pytest.raises(I.IsfError) as e:
+            lat.set_item_sites(bad)
+        assert e.value.code == -1
     lat.close()
 
 
