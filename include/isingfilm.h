@@ -173,8 +173,9 @@ int isf_set_path(isf_lattice* lat, int32_t path);
 
 /* Launch shape override: ctas = CTAs of the global kernel or cluster size (1..16) of the
  * resident kernel (0 = automatic); threads per CTA (0 = automatic; else a multiple of 32 up to
- * 1024; the global kernel uses at most 256, the resident kernel at most 512).  Trajectories do
- * not depend on it. */
+ * 1024; the global kernel uses at most 256; the resident kernel 64..512 with 16-site items and
+ * 64..768 with 8-site items, one warp of which folds the observables and takes no sites).
+ * Trajectories do not depend on it. */
 int isf_set_launch(isf_lattice* lat, int32_t ctas, int32_t threads);
 
 /* Sites per work item of the resident kernel: 16, 8, or 0 = automatic (8 when a quarter or more
@@ -227,7 +228,8 @@ int isf_batch_create(isf_batch** out);
 int isf_batch_add(isf_batch* batch, isf_lattice* lat);        /* ISF_ERR_STATE: no schedule */
 int isf_batch_clear(isf_batch* batch);
 /* Launch shapes: threads of the single-CTA kernel, cluster size K (1..16) and threads of the
- * cluster kernel (multiples of 32 up to 512); 0 = tuned or default (256; 16 and 512). */
+ * cluster kernel (multiples of 32 in 64..512, one warp folding); 0 = tuned or default (256; 16
+ * and 512). */
 int isf_batch_set_launch(isf_batch* batch, int32_t threads_single, int32_t cluster_K, int32_t threads_cluster);
 /* on != 0: capture the queue upload and the two persistent launches in a CUDA graph once and
  * replay it on later runs with the same shape (the per-film arguments are refreshed each run). */

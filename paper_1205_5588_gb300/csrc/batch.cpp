@@ -156,7 +156,7 @@ double probe(const isf_lattice* L, int K, int threads, int sweeps, cudaStream_t 
     const int32_t eq = 0, meas = sweeps;
     double best = -1;
     if (!isf_set_schedule(P, 1, &T, &h, &eq, &meas, 1.0, 0.0) && !isf_set_path(P, ISF_PATH_RESIDENT) &&
-        !isf_set_launch(P, K, threads)) {
+        !isf_set_launch(P, K, threads) && !isf_set_item_sites(P, 16)) {
         cudaEvent_t a, b;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
@@ -204,9 +204,9 @@ int isf_batch_clear(isf_batch* b) {
 }
 
 int isf_batch_set_launch(isf_batch* b, int32_t threads_single, int32_t cluster_K, int32_t threads_cluster) {
-    if (!b || threads_single < 0 || cluster_K < 0 || cluster_K > 16 || threads_cluster < 0 ||
-        threads_single % 32 || threads_cluster % 32 || threads_single > 512 || threads_cluster > 512)
-        return fail(ISF_ERR_ARG, "threads: 0 or multiples of 32 up to 512; cluster size 0..16");
+    auto bad_threads = [](int32_t t) { return t != 0 && (t % 32 || t < 64 || t > 512); };
+    if (!b || cluster_K < 0 || cluster_K > 16 || bad_threads(threads_single) || bad_threads(threads_cluster))
+        return fail(ISF_ERR_ARG, "threads: 0 or multiples of 32 in 64..512; cluster size 0..16");
     b->threads_a = threads_single;
     b->K_b = cluster_K;
     b->threads_b = threads_cluster;

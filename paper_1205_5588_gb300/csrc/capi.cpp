@@ -119,11 +119,22 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
     f.heights = L->dev + lay.heights_off;
     fill_neighbour_classes(lay, &f);
     L->st = reinterpret_cast<FilmState*>(L->dev + lay.state_off);
+    std::vector<uint32_t> items;
+    if (lay.packed && build_word_items(lay, heights, items, f.nitems, &f.item_wbits, &f.item_jbits)) {
+        f.items = reinterpret_cast<const uint32_t*>(L->dev + lay.items_off);
+        f.item_cap = lay.items_cap;
+    }
 
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     auto bail = [&](int code) { isf_lattice_destroy(L); return code; };
     e = cudaMemsetAsync(L->st, 0, sizeof(FilmState), s);
     if (e != cudaSuccess) return bail(cuda_fail(e, "memset state"));
+    if (f.items) {
+        // host vector stays alive until the stream synchronisation at the end of set-up
+        e = cudaMemcpyAsync(L->dev + lay.items_off, items.data(), items.size() * sizeof(uint32_t),
+                            cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "copy word lists"));
+    }
     e = cudaMemcpyAsync(L->dev + lay.heights_off, heights, n_px, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return bail(cuda_fail(e, "copy heights"));
     int ke = launch_init(f, init, s);
@@ -302,14 +313,32 @@ int isf_run_sweeps(isf_lattice* L, int64_t nsweeps, void* cuda_stream) {
         }
     }
     if (!launched) {
-        int threads = L->threads ? std::min(L->threads, 256) : 256;
+        const bool listed = L->f.packed && L->f.items;
+        int threads = L->threads ? std::min(L->threads, 256) : (listed ? 128 : 256);
         int maxc = 0;
         int e = sweep_max_ctas_for(L->f, threads, &maxc);
         if (e) return cuda_fail((cudaError_t)e, "occupancy query");
         if (maxc < 1) return fail(ISF_ERR_CUDA, "sweep kernel cannot be resident with this block size");
         int ctas = L->ctas;
-        if (ctas <= 0) {
-            const int64_t items = sweep_items_per_pass(L->f);
+        const int64_t items = sweep_items_per_pass(L->f);
+        if (ctas <= 0 && listed) {
+            // a whole number of CTAs per SM, the fewest that reach the smallest count of words
+            // per thread (every thread then takes that count or one less)
+            int dev = 0, sms = 1;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int64_t one_each = (items + threads - 1) / threads;
+            if (one_each <= sms) {
+                ctas = (int)std::max<int64_t>(1, one_each);     // small film: one word per thread
+            } else {
+                int64_t best_k = -1;
+                for (int g = sms; g <= maxc; g += sms) {
+                    const int64_t k = (items + (int64_t)g * threads - 1) / ((int64_t)g * threads);
+                    if (best_k < 0 || k < best_k) { best_k = k; ctas = g; }
+                }
+                if (ctas <= 0) ctas = maxc;
+            }
+        } else if (ctas <= 0) {
             int64_t want = (items + threads - 1) / threads;   // about one work item per thread
             ctas = (int)(want < 1 ? 1 : want);
         }

@@ -18,6 +18,7 @@
 //                 row holds columns 32w..32w+31 and sits at index w+1; Wp = nw + 2.
 #pragma once
 #include <stdint.h>
+#include <vector>
 #include <stddef.h>
 
 #ifdef __CUDACC__
@@ -60,6 +61,12 @@ struct DevFilm {
     int64_t Wp, lsw, csw;         // row pitch, layer stride, colour stride (words)
     int32_t nw;                   // words per row
     int32_t pad_;
+    // packed layout: per colour the words holding at least one occupied site, in (z, row,
+    // word) order, each (z << (jbits + wbits)) | (j << wbits) | w; nullptr when not built
+    const uint32_t* items;        // [4][item_cap]
+    int64_t item_cap;
+    int32_t nitems[4];
+    int32_t item_wbits, item_jbits;
     const uint8_t* heights;       // [y][x]
     NbrClass nb[4][2];            // [colour][layer parity]
 };
@@ -109,11 +116,18 @@ struct Layout {
     int64_t nw, Wp, lsw, csw;
     size_t spin_bytes;            // int8 array, or both bit-plane sets
     size_t heights_off, state_off, total_bytes;
+    size_t items_off;             // packed: occupied-word lists, 4 x items_cap uint32
+    int64_t items_cap;            // packed: L * Rh * nw (0 for int8)
 };
 
 int make_layout(int32_t rows, int32_t cols, int32_t layers, uint32_t flags, Layout* out,
                 const char** why);
 int check_colouring(const Layout& lay, const char** why);
+// Occupied-word lists of a packed film (host, from the height map): out gets 4 * items_cap
+// entries (colour c's list at c * items_cap, n[c] of them); false when an entry's fields do not
+// fit 32 bits (the kernels then walk every word).
+bool build_word_items(const Layout& lay, const uint8_t* heights, std::vector<uint32_t>& out, int32_t n[4],
+                      int32_t* wbits, int32_t* jbits);
 void fill_neighbour_classes(const Layout& lay, DevFilm* f);
 
 // Host threshold table (schedule.cpp): thr[n+12][s'] for one step, plus the gate slot.

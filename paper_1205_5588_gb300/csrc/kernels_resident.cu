@@ -160,6 +160,22 @@ __device__ __forceinline__ uint4 neighbour_sum16_sc(const uint32_t* nb, int sgn)
     return acc;
 }
 
+// Add v to the 64-bit word at a shared::cluster address (another CTA's shared memory, or this
+// CTA's own when CLUSTER is false).
+template <bool CLUSTER>
+__device__ __forceinline__ void red_add64(uint32_t a, long long v) {
+    if (CLUSTER)
+        asm volatile("red.relaxed.cluster.shared::cluster.add.u64 [%0], %1;" :: "r"(a), "l"(v) : "memory");
+    else
+        asm volatile("red.shared.add.u64 [%0], %1;" :: "r"(a), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
 template <bool CLUSTER>
 __device__ __forceinline__ void sync_all() {
     if (CLUSTER) cluster_sync_all();
@@ -167,7 +183,10 @@ __device__ __forceinline__ void sync_all() {
 }
 
 // One film on this CTA (CLUSTER = false) or on this cluster: slab in, the launch's sweeps,
-// slab out.  Ends with a barrier over all CTAs that took part.
+// slab out.  Ends with a barrier over all CTAs that took part.  The last warp of every CTA takes
+// no sites: in CTA 0 its first lane folds each sweep's dM, dB into the step sums while the other
+// warps run the next colour pass; the other warps add their per-sweep dM, dB into CTA 0's
+// accumulator with shared::cluster reductions (no block-wide reduction on the critical path).
 // NW = 4: 16-site work items; NW = 2: 8-site items (twice the items per pass, for films whose
 // 16-site items would leave the CTA's warps too few to hide the shared-memory latency).
 template <bool CLUSTER, bool PX, int NW = 4>
@@ -195,6 +214,7 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
     const int words = P / 16;
     const uint64_t smem_n = dyn_smem_bytes();
     bool desc_ok = ISF_CHECK(K >= 1 && K <= 16 && Jb >= 1 && (int64_t)Jb * K >= Rh && P % 16 == 0, 1, K, Jb);
+    desc_ok = desc_ok && ISF_CHECK(blockDim.x >= 64 && blockDim.x % 32 == 0, 12, blockDim.x, 0);
     desc_ok = desc_ok && ISF_CHECK(a.misc_off + 1424 <= smem_n, 2, a.misc_off, smem_n);
     desc_ok = desc_ok && ISF_CHECK((uint64_t)a.ptr_off + (uint64_t)4 * L * Jb * 48 <= a.misc_off, 3, a.ptr_off, a.misc_off);
     desc_ok = desc_ok && ISF_CHECK(s.k0 >= 0 && s.k0 < s.nsteps && s.nsteps >= 1, 4, s.k0, s.nsteps);
@@ -211,6 +231,8 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
     }
     for (int t = threadIdx.x; t < P / 4; t += blockDim.x) reinterpret_cast<uint32_t*>(vac)[t] = 0x01010101u;
     if (threadIdx.x < K) base[threadIdx.x] = CLUSTER ? map_rank_addr(smem_addr(film), threadIdx.x) : smem_addr(film);
+    unsigned long long* obs = reinterpret_cast<unsigned long long*>(slots);   // CTA 0's: dM, dB of a sweep
+    if (threadIdx.x == 0) { obs[0] = 0; obs[1] = 0; }
     __syncthreads();
     if (PX) {
         for (int rr = threadIdx.x; rr < 4 * L * nown; rr += blockDim.x) {
@@ -247,11 +269,14 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
     sync_all<CLUSTER>();    // every slab loaded before anyone reads a neighbour's
 
     const int nci = NW == 4 ? nck : (Ch + 7) / 8;     // items per row
-    const int items = L * nown * nci;
+    const int ithreads = (int)blockDim.x - 32;       // threads that take sites; the last warp folds
+    const bool fold_warp = (int)threadIdx.x >= ithreads;
+    const int items = fold_warp ? 0 : L * nown * nci;
     ItemWalk walk0;
-    walk0.init(threadIdx.x, blockDim.x, nci, nown > 0 ? nown : 1);
+    walk0.init(threadIdx.x, ithreads, nci, nown > 0 ? nown : 1);
+    const uint32_t obs0 = CLUSTER ? map_rank_addr(smem_addr(obs), 0) : smem_addr(obs);
     int k = s.k0, pos = s.pos0;
-    const bool folder = rank == 0 && threadIdx.x == 0;
+    const bool folder = rank == 0 && (int)threadIdx.x == ithreads;
     __shared__ RunState rs;     // touched by the folding thread only
     int k_eq = 0, k_tot = 0;
     if (folder) {
@@ -272,29 +297,38 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
         int dM = 0, dB = 0;
         for (int c = 0; c < 4; ++c) {
             ItemWalk w = walk0;
-            for (int it = threadIdx.x; it < items; it += blockDim.x, w.next()) {
+            for (int it = threadIdx.x; it < items; it += ithreads, w.next()) {
                 const int ck = w.ck, jl = w.jr, z = w.z;
                 const size_t r = (size_t)(c * L + z) * Jb + jl;
                 if (!ISF_CHECK(z >= 0 && z < L && jl >= 0 && jl < nown && ck >= 0 && ck < nci, 8, it, ((uint64_t)z << 32) | (uint32_t)jl)) continue;
                 uint8_t* row = film + r * P;
                 uint8_t* own = row + 16 + W * ck;
-                const uint32_t* pr = ptrs + r * 12;
-                uint32_t nbp[12];
-#pragma unroll
-                for (int kk = 0; kk < 12; ++kk) nbp[kk] = pr[kk] + 16 + W * ck;
-                const uint32_t q0 = block_counter(f, c, z, j0 + jl, W * ck);
-                const int sgn = f.nb[c][z & 1].sgn;
                 uint32_t Sw[NW], Aw[NW];
                 if constexpr (NW == 4) {
                     const uint4 S = *reinterpret_cast<const uint4*>(own);
-                    const uint4 acc = neighbour_sum16_sc<CLUSTER>(nbp, sgn);
                     Sw[0] = S.x; Sw[1] = S.y; Sw[2] = S.z; Sw[3] = S.w;
-                    Aw[0] = acc.x; Aw[1] = acc.y; Aw[2] = acc.z; Aw[3] = acc.w;
                 } else {
                     const uint2 S = *reinterpret_cast<const uint2*>(own);
-                    const uint2 acc = neighbour_sum8_sc<CLUSTER>(nbp, sgn);
                     Sw[0] = S.x; Sw[1] = S.y;
-                    Aw[0] = acc.x; Aw[1] = acc.y;
+                }
+                uint32_t sites = 0;     // nonzero unless every byte is a vacancy (1)
+#pragma unroll
+                for (int v = 0; v < NW; ++v) sites |= Sw[v] ^ 0x01010101u;
+                if (!sites) continue;   // no site to attempt: no table lookup, no random word
+                // the row's 12 neighbour-row addresses (48 bytes, 16-byte aligned)
+                const uint4* pr = reinterpret_cast<const uint4*>(ptrs + r * 12);
+                const uint4 pa = pr[0], pb = pr[1], pc = pr[2];
+                const uint32_t co = 16 + W * ck;
+                const uint32_t nbp[12] = {pa.x + co, pa.y + co, pa.z + co, pa.w + co, pb.x + co, pb.y + co,
+                                          pb.z + co, pb.w + co, pc.x + co, pc.y + co, pc.z + co, pc.w + co};
+                const uint32_t q0 = block_counter(f, c, z, j0 + jl, W * ck);
+                const int sgn = f.nb[c][z & 1].sgn;
+                if constexpr (NW == 4) {
+                    const uint4 a4 = neighbour_sum16_sc<CLUSTER>(nbp, sgn);
+                    Aw[0] = a4.x; Aw[1] = a4.y; Aw[2] = a4.z; Aw[3] = a4.w;
+                } else {
+                    const uint2 a2 = neighbour_sum8_sc<CLUSTER>(nbp, sgn);
+                    Aw[0] = a2.x; Aw[1] = a2.y;
                 }
                 uint32_t fm[NW];
                 const uint32_t any = s.use_gate
@@ -325,21 +359,19 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
                     }
                 }
             }
-            if (c == 3) {
-                long long sM = dM, sB = dB;
-                block_sum2(sM, sB, red);
-                if (threadIdx.x == 0) {
-                    long long* slot = CLUSTER ? reinterpret_cast<long long*>(map_rank(reinterpret_cast<uint8_t*>(slots + 2 * rank), 0))
-                                              : slots;
-                    slot[0] = sM;
-                    slot[1] = sB;
+            if (c == 3 && !fold_warp) {
+                const int wM = warp_sum_i(dM), wB = warp_sum_i(dB);
+                if ((threadIdx.x & 31) == 0 && (wM | wB)) {
+                    red_add64<CLUSTER>(obs0, (long long)wM);
+                    red_add64<CLUSTER>(obs0 + 8, (long long)wB);
                 }
             }
-            sync_all<CLUSTER>();
-        }
+            sync_all<CLUSTER>();    // orders the reductions before the fold, and the fold's reset
+        }                           // before the next sweep's reductions
         if (folder && ISF_CHECK(k >= 0 && k < s.nsteps, 10, k, s.nsteps)) {
-            long long sM = 0, sB = 0;
-            for (unsigned r = 0; r < K; ++r) { sM += slots[2 * r]; sB += slots[2 * r + 1]; }
+            const long long sM = (long long)obs[0], sB = (long long)obs[1];
+            obs[0] = 0;
+            obs[1] = 0;
             fold_sweep(s, rs, k, pos, k_eq, k_tot, sM, sB, t);
         }
         ++pos;
@@ -501,14 +533,14 @@ int resident_plan(const DevFilm& f, int want_K, int want_threads, int want_sites
         if (!sites) sites = 4 * (16 * f.nck - f.Ch) >= 16 * f.nck ? 8 : 16;
         const int64_t items = sites == 8 ? (int64_t)f.L * Jb * ((f.Ch + 7) / 8) : items16;
         const int tmax = sites == 8 ? kMaxResThreads8 : kMaxResThreads;
-        // threads: one per work item of a pass, rounded to whole warps, 64..tmax
+        // threads: one per work item of a pass, rounded to whole warps, plus the folding warp
         int th = threads;
         if (!th) {
-            th = (int)((items + 31) / 32 * 32);
-            if (th < 64) th = 64;
-            if (th > tmax) th = tmax;
+            int64_t ith = (items + 31) / 32 * 32;
+            if (ith > tmax - 32) ith = tmax - 32;
+            th = (int)ith + 32;
         }
-        if (th > tmax) {
+        if (th > tmax || th < 64) {
             if (want_sites) return 3;
             continue;
         }

@@ -13,6 +13,8 @@
 // last barrier CTA 0 folds the deltas into M and B and into the step's exact sums.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "sweep_core.cuh"
 
 namespace isf {
@@ -181,6 +183,7 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
             vac[k] = ~__funnelshift_r(op[a], op[a + 1], 1);
         }
     }
+    if (!O) return;             // no occupied site in the word (tested after the loads are issued)
     // X = n + 12 = 2 * (#up) + (#vacant) over the 12 neighbours, 5 bit-planes
     uint32_t U0, U1, U2, U3, V0, V1, V2, V3;
     popcount12(up, U0, U1, U2, U3);
@@ -214,23 +217,35 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
     }
     const uint32_t q0 = block_counter(f, c, z, j, 32 * w);
     uint32_t F = 0;
+    // two halves of 16 lanes (4 Philox blocks each): all 16 lookups first, then the half's four
+    // blocks interleaved when any of its lanes needs a word
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
-        uint32_t thr[4];
+    for (int g = 0; g < 2; ++g) {
+        uint32_t thr[16];
         bool need = false;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            thr[b] = tab[(P[4 * (v & 1) + b] >> (8 * (v >> 1))) & 0x7Fu];
-            need |= needs_word(thr[b]);
-        }
-        uint4 u = make_uint4(0, 0, 0, 0);
-        if (need) u = philox10(make_uint4(q0 + v, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u), f.key0, f.key1);
-        uint32_t lanes = 0;
+        for (int vv = 0; vv < 4; ++vv) {
+            const int v = 4 * g + vv;
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-            if (metropolis_accept(word_of(u, b), thr[b])) lanes |= 1u << b;
-        if (GATE) lanes = gate_block(lanes, gthr, q0 + v, sweep, f.key0, f.key1);
-        F |= lanes << (4 * v);
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t t = tab[(P[4 * (v & 1) + b] >> (8 * (v >> 1))) & 0x7Fu];
+                thr[4 * vv + b] = t;
+                need |= needs_word(t);
+            }
+        }
+        uint4 u[4];
+#pragma unroll
+        for (int vv = 0; vv < 4; ++vv) u[vv] = make_uint4(0, 0, 0, 0);
+        if (need) philox10_xn<4>(q0 + 4 * g, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u);
+#pragma unroll
+        for (int vv = 0; vv < 4; ++vv) {
+            uint32_t lanes = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (metropolis_accept(word_of(u[vv], b), thr[4 * vv + b])) lanes |= 1u << b;
+            if (GATE) lanes = gate_block(lanes, gthr, q0 + 4 * g + vv, sweep, f.key0, f.key1);
+            F |= lanes << (4 * (4 * g + vv));
+        }
     }
     if (F) {
         f.sp[base] = S ^ F;
@@ -252,6 +267,19 @@ __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned lo
                                             const uint32_t* tab, uint32_t gthr, int items,
                                             ItemWalk w, int& dM, int& dB) {
     const int stride = gridDim.x * blockDim.x;
+    if (MODE == MODE_PACKED && f.items) {
+        // the colour's occupied words only, thread t taking entries t, t + stride, ...
+        const uint32_t* list = f.items + (int64_t)c * f.item_cap;
+        const int n = f.nitems[c];
+        const int wb = f.item_wbits, jb = f.item_jbits;
+        const uint32_t wmask = (1u << wb) - 1u, jmask = (1u << jb) - 1u;
+        for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += stride) {
+            const uint32_t e = list[it];
+            word_packed<GATE>(f, c, (int)(e >> (jb + wb)), (int)((e >> wb) & jmask), (int)(e & wmask), sweep, tab,
+                              gthr, dM, dB);
+        }
+        return;
+    }
     for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += stride, w.next()) {
         if (MODE == MODE_INT8) chunk_int8<GATE>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
         else if (MODE == MODE_GENERIC) block_generic<GATE>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
@@ -365,6 +393,7 @@ int sweep_max_ctas_for(const DevFilm& f, int threads, int* max_ctas) {
 }
 
 int sweep_items_per_pass(const DevFilm& f) {
+    if (f.packed && f.items) return std::max(std::max(f.nitems[0], f.nitems[1]), std::max(f.nitems[2], f.nitems[3]));
     const int per_row = f.packed ? f.nw : ((f.flags & 7u) ? f.Qw : f.nck);
     return f.L * f.Rh * per_row;
 }

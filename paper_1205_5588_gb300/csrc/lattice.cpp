@@ -69,9 +69,50 @@ int make_layout(int32_t rows, int32_t cols, int32_t layers, uint32_t flags, Layo
     L.spin_bytes = packed ? (size_t)2 * 4 * (size_t)L.csw * 4 : (size_t)4 * (size_t)L.cs8;
     L.heights_off = align256(L.spin_bytes);
     L.state_off = align256(L.heights_off + (size_t)rows * (size_t)cols);
-    L.total_bytes = align256(L.state_off + sizeof(FilmState));
+    L.items_cap = packed ? (int64_t)layers * L.Rh * L.nw : 0;
+    L.items_off = align256(L.state_off + sizeof(FilmState));
+    L.total_bytes = align256(L.items_off + (size_t)4 * (size_t)L.items_cap * sizeof(uint32_t));
     *out = L;
     return ISF_OK;
+}
+
+static int bits_for(int64_t n) {
+    int b = 0;
+    while (((int64_t)1 << b) < n) ++b;
+    return b;
+}
+
+bool build_word_items(const Layout& lay, const uint8_t* heights, std::vector<uint32_t>& out, int32_t n[4],
+                      int32_t* wbits, int32_t* jbits) {
+    const int wb = bits_for(lay.nw), jb = bits_for(lay.Rh), zb = bits_for(lay.L);
+    if (wb + jb + zb > 32) return false;
+    out.assign((size_t)4 * (size_t)lay.items_cap, 0u);
+    // tallest pixel among the 32 columns of each (row y, column parity, word w): a word of
+    // layer z holds an occupied site iff z < that height
+    std::vector<uint8_t> top((size_t)lay.R * 2 * lay.nw, 0);
+    for (int y = 0; y < lay.R; ++y)
+        for (int x = 0; x < lay.C; ++x) {
+            uint8_t& t = top[((size_t)y * 2 + (x & 1)) * lay.nw + ((x >> 1) >> 5)];
+            t = std::max(t, heights[(size_t)y * lay.C + x]);
+        }
+    for (int c = 0; c < 4; ++c) {
+        uint32_t* dst = out.data() + (size_t)c * lay.items_cap;
+        int64_t k = 0;
+        for (int z = 0; z < lay.L; ++z) {
+            const int zp = z & 1, px = (c & 1) ^ zp, py = ((c >> 1) & 1) ^ zp;
+            for (int j = 0; j < lay.Rh; ++j) {
+                const int y = 2 * j + py;
+                if (y >= lay.R) continue;
+                for (int w = 0; w < lay.nw; ++w)
+                    if (z < top[((size_t)y * 2 + px) * lay.nw + w])
+                        dst[k++] = ((uint32_t)z << (jb + wb)) | ((uint32_t)j << wb) | (uint32_t)w;
+            }
+        }
+        n[c] = (int32_t)k;
+    }
+    *wbits = wb;
+    *jbits = jb;
+    return true;
 }
 
 // Proof that no bond joins two sites of one colour on this film.  Away from a wrap the colour

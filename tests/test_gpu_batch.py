@@ -94,3 +94,29 @@ def test_batch_of_one_and_empty(I):
     b.run()
     b.close()
     lat.close()
+
+
+@pytest.mark.parametrize("shape", [(64, 8, 64), (512, 16, 96), (160, 2, 512)])
+def test_batch_launch_shapes(I, shape):
+    """Explicit launch shapes, down to one site-taking warp next to the folding warp."""
+    films = mixed_films()[:6]
+    lats = [make(I, f) for f in films]
+    b = I.Batch(lats)
+    b.set_launch(*shape)
+    b.run()
+    for f, lat in zip(films, lats):
+        o = run_oracle(f, f["schedule"])
+        assert_records_equal(lat.observables(), o["recs"])
+        assert np.array_equal(lat.spins(), o["spins"])
+    b.close()
+    for lat in lats:
+        lat.close()
+
+
+def test_batch_launch_shape_errors(I):
+    b = I.Batch([])
+    for bad in ((32, 0, 0), (0, 8, 32), (544, 0, 0), (0, 17, 0), (70, 0, 0)):
+        with pytest.raises(I.IsfError) as e:
+            b.set_launch(*bad)
+        assert e.value.code == -1
+    b.close()
