@@ -124,6 +124,7 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
         f.items = reinterpret_cast<const uint32_t*>(L->dev + lay.items_off);
         f.item_cap = lay.items_cap;
     }
+    if (lay.packed) f.narrow = (4 * lay.csw + 2 * lay.lsw) < ((int64_t)1 << 31) ? 1 : 0;
 
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     auto bail = [&](int code) { isf_lattice_destroy(L); return code; };
@@ -139,6 +140,7 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
     if (e != cudaSuccess) return bail(cuda_fail(e, "copy heights"));
     int ke = launch_init(f, init, s);
     if (ke) return bail(cuda_fail((cudaError_t)ke, "init kernel"));
+
     long long red[4];
     rc = recompute(L, s, red);
     if (rc) return bail(rc);
@@ -314,7 +316,7 @@ int isf_run_sweeps(isf_lattice* L, int64_t nsweeps, void* cuda_stream) {
     }
     if (!launched) {
         const bool listed = L->f.packed && L->f.items;
-        int threads = L->threads ? std::min(L->threads, 256) : (listed ? 128 : 256);
+        int threads = L->threads ? std::min(L->threads, 512) : (listed ? 512 : 256);
         int maxc = 0;
         int e = sweep_max_ctas_for(L->f, threads, &maxc);
         if (e) return cuda_fail((cudaError_t)e, "occupancy query");

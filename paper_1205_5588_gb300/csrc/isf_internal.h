@@ -67,6 +67,8 @@ struct DevFilm {
     int64_t item_cap;
     int32_t nitems[4];
     int32_t item_wbits, item_jbits;
+    int32_t narrow;               // packed: 1 if every neighbour offset and index fits 32 bits
+    int32_t pad2_;
     const uint8_t* heights;       // [y][x]
     NbrClass nb[4][2];            // [colour][layer parity]
 };

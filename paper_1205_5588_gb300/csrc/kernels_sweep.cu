@@ -22,7 +22,7 @@ namespace isf {
 namespace {
 
 enum { MODE_INT8 = 0, MODE_GENERIC = 1, MODE_PACKED = 2 };
-constexpr int kBlock = 256;
+constexpr int kBlock = 512;      // largest CTA of the global kernel (<= 128 registers per thread)
 constexpr unsigned kSpinLimit = 1u << 22;   // ~ seconds of waiting, then give up
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -153,41 +153,53 @@ __device__ __forceinline__ void popcount12(const uint32_t* x, uint32_t& b0, uint
     full_add(f0, f1, f2, b2, b3);
 }
 
-template <bool GATE>
+// Loads of one packed word position: the own spin and occupancy words and the 12 neighbour
+// spin and occupancy words (three of them shifted by one column, completed from the word before
+// or after), reduced to the neighbours' up bits and their bit-sliced vacancy count V.  NARROW:
+// every offset fits 32 bits, so each address is one 32-bit offset from the own word's pointer.
+template <bool NARROW>
+__device__ __forceinline__ void packed_loads(const DevFilm& f, const NbrClass& nc, int64_t base, uint32_t& S,
+                                             uint32_t& O, uint32_t up[12], uint32_t V[4]) {
+    const uint32_t* spb = f.sp + base;
+    const uint32_t* opb = f.op + base;
+    auto off = [&](int k) -> int64_t { return NARROW ? (int64_t)(int32_t)nc.off[k] : nc.off[k]; };
+    S = spb[0];
+    O = opb[0];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) up[k] = spb[off(k)];
+    if (nc.sgn < 0) {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) up[k] = __funnelshift_l(spb[off(k) - 1], spb[off(k)], 1);
+    } else {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) up[k] = __funnelshift_r(spb[off(k)], spb[off(k) + 1], 1);
+    }
+    uint32_t vac[12];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) vac[k] = ~opb[off(k)];
+    if (nc.sgn < 0) {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) vac[k] = ~__funnelshift_l(opb[off(k) - 1], opb[off(k)], 1);
+    } else {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) vac[k] = ~__funnelshift_r(opb[off(k)], opb[off(k) + 1], 1);
+    }
+    popcount12(vac, V[0], V[1], V[2], V[3]);
+}
+
+template <bool GATE, bool NARROW>
 __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int j, int w,
                                             unsigned long long sweep, const uint32_t* tab,
                                             uint32_t gthr, int& dM, int& dB) {
     const NbrClass& nc = f.nb[c][z & 1];
     const int64_t base = addrw(f, c, z, j, w);
-    const uint32_t* sp = f.sp;
-    const uint32_t* op = f.op;
-    const uint32_t S = sp[base], O = op[base];
-    uint32_t up[12], vac[12];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        up[k] = sp[base + nc.off[k]];
-        vac[k] = ~op[base + nc.off[k]];
-    }
-    if (nc.sgn < 0) {
-#pragma unroll
-        for (int k = 9; k < 12; ++k) {
-            const int64_t a = base + nc.off[k];
-            up[k] = __funnelshift_l(sp[a - 1], sp[a], 1);
-            vac[k] = ~__funnelshift_l(op[a - 1], op[a], 1);
-        }
-    } else {
-#pragma unroll
-        for (int k = 9; k < 12; ++k) {
-            const int64_t a = base + nc.off[k];
-            up[k] = __funnelshift_r(sp[a], sp[a + 1], 1);
-            vac[k] = ~__funnelshift_r(op[a], op[a + 1], 1);
-        }
-    }
+    uint32_t S, O, up[12], V[4];
+    packed_loads<NARROW>(f, nc, base, S, O, up, V);
     if (!O) return;             // no occupied site in the word (tested after the loads are issued)
     // X = n + 12 = 2 * (#up) + (#vacant) over the 12 neighbours, 5 bit-planes
-    uint32_t U0, U1, U2, U3, V0, V1, V2, V3;
+    uint32_t U0, U1, U2, U3;
     popcount12(up, U0, U1, U2, U3);
-    popcount12(vac, V0, V1, V2, V3);
+    const uint32_t V0 = V[0], V1 = V[1], V2 = V[2], V3 = V[3];
     uint32_t X[5], k2, k3;
     X[0] = V0;
     X[1] = U0 ^ V1;
@@ -262,6 +274,14 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
     }
 }
 
+// First work item of this thread in a pass.  Warps are numbered across CTAs first (warp w of
+// CTA b is warp w * G + b), so when a pass has fewer items than two per thread, the threads
+// that take one more item are spread evenly over all CTAs (and SMs); lanes stay consecutive,
+// so a warp still reads consecutive words.
+__device__ __forceinline__ int first_item() {
+    return (((int)(threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x) << 5) + (int)(threadIdx.x & 31);
+}
+
 template <int MODE, bool GATE>
 __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned long long sweep,
                                             const uint32_t* tab, uint32_t gthr, int items,
@@ -273,17 +293,21 @@ __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned lo
         const int n = f.nitems[c];
         const int wb = f.item_wbits, jb = f.item_jbits;
         const uint32_t wmask = (1u << wb) - 1u, jmask = (1u << jb) - 1u;
-        for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += stride) {
+        for (int it = first_item(); it < n; it += stride) {
             const uint32_t e = list[it];
-            word_packed<GATE>(f, c, (int)(e >> (jb + wb)), (int)((e >> wb) & jmask), (int)(e & wmask), sweep, tab,
-                              gthr, dM, dB);
+            if (f.narrow)
+                word_packed<GATE, true>(f, c, (int)(e >> (jb + wb)), (int)((e >> wb) & jmask), (int)(e & wmask), sweep,
+                                        tab, gthr, dM, dB);
+            else
+                word_packed<GATE, false>(f, c, (int)(e >> (jb + wb)), (int)((e >> wb) & jmask), (int)(e & wmask), sweep,
+                                         tab, gthr, dM, dB);
         }
         return;
     }
-    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += stride, w.next()) {
+    for (int it = first_item(); it < items; it += stride, w.next()) {
         if (MODE == MODE_INT8) chunk_int8<GATE>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
         else if (MODE == MODE_GENERIC) block_generic<GATE>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
-        else word_packed<GATE>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
+        else word_packed<GATE, false>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
     }
 }
 
@@ -300,7 +324,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep(const __grid_constant__ SweepA
     const int per_row = MODE == MODE_INT8 ? f.nck : (MODE == MODE_GENERIC ? f.Qw : f.nw);
     const int items = f.L * f.Rh * per_row;
     ItemWalk walk0;
-    walk0.init(blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, per_row, f.Rh);
+    walk0.init(first_item(), gridDim.x * blockDim.x, per_row, f.Rh);
     int k = a.k0, pos = a.pos0;
     const bool folder = blockIdx.x == 0 && threadIdx.x == 0;
     __shared__ RunState rs;     // touched by the folding thread only
@@ -348,6 +372,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep(const __grid_constant__ SweepA
 
 template <int MODE>
 int launch_mode(const SweepArgs& a, int ctas, int threads, cudaStream_t s) {
+    if (threads % 32 || threads < 32 || threads > kBlock) return (int)cudaErrorInvalidValue;   // whole warps
     if (ctas <= 1) {
         k_sweep<MODE><<<1, threads, 0, s>>>(a);
         return (int)cudaGetLastError();
