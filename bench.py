@@ -29,10 +29,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "spin-flip attempts/s and % roofline on 1 GB300, batched/served vs plain"
 UNIT = "attempts/s"
-# Integer work the method needs per attempt: a quarter Philox4x32-10 block
-# (10 rounds x (2 wide multiplies + 2 three-input XORs) / 4 sites = 10), the 12-neighbour sum
-# (3: four sites per 32-bit add) and the acceptance (2: table lookup, compare).
-OPS_PER_ATTEMPT = 15
+# Integer operations the method needs per attempt, counted at source level: a quarter of a
+# Philox4x32-10 block (10 rounds x (2 32x32->64 multiplies + 4 XORs + 2 key adds) / 4 = 25), the
+# 12-neighbour sum (12) and the acceptance test and update (5).
+OPS_PER_ATTEMPT = 40
 SMS, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 ALU_PEAK_TOPS = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12    # 40.3 T int32 lane-ops/s
 
@@ -212,6 +212,10 @@ def run_impl(args):
                      "ops_per_attempt": OPS_PER_ATTEMPT},
         "clocks": clk,
     }
+    if not args.no_multispin and args.workload != "fractal2048":
+        m = measure_multispin(I, ranks)
+        if rank == 0:
+            line["multispin"] = m
     if not args.no_batched:
         # independent films: each rank runs its own share of the list (weak scaling)
         b = measure_batched(I, n_films=args.batch_films, sweeps_per_step=args.batch_sweeps, ranks=ranks,
@@ -225,6 +229,48 @@ def run_impl(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     D.finish(ranks)
+
+
+def measure_multispin(I, ranks, steps=2, warmup=1):
+    """The bit-packed multispin sweep on the 2048x2048x(2..6) film: one timed step is the whole
+    hysteresis loop (641 field steps x 200 sweeps at T = 2), one k_sweep launch, L2 flushed
+    between steps.  Under several ranks each rank runs its own replica."""
+    import torch
+    from paper_1205_5588_gb300 import distributed as D
+    spec = workload("fractal2048")
+    sched = spec["schedule"]
+    lat = I.Lattice(spec["heights"], spec["layers"], packed=True, seed=D.replica_seed(spec["seed"], ranks.rank),
+                    init=spec["init"])
+    n_occ = lat.info()["n_occ"]
+    per_step = attempts_of(spec, n_occ)
+    l2buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    times = []
+    for i in range(warmup + steps):
+        lat.set_schedule(sched["T"], sched["h"], sched["eq"], sched["meas"], J=spec["J"])
+        flush_l2(l2buf)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lat.run(-1, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        if i >= warmup:
+            times.append(a.elapsed_time(b) / 1e3)
+    shape = lat.launch_info()
+    recs = lat.observables()
+    lat.close()
+    del l2buf
+    total = D.max_over_ranks(sum(times), ranks, device="cuda")
+    t_launch = sum(times) / len(times)
+    achieved = OPS_PER_ATTEMPT * per_step / t_launch / 1e12
+    return {"workload": spec["name"], "value": per_step * steps * ranks.world / total, "unit": UNIT,
+            "dtype": "u32 (1 bit/spin)", "occupied_sites": n_occ, "attempts_per_step": per_step,
+            "seconds_per_step": t_launch, "steps": steps, "warmup": warmup,
+            "final_m": recs[-1]["m"] if recs else None,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                         "frac": achieved / ALU_PEAK_TOPS, "traffic": load_traffic("fractal2048"),
+                         "kernel": "k_sweep<packed> (global-memory persistent kernel)", "launch": shape,
+                         "ops_per_attempt": OPS_PER_ATTEMPT}}
 
 
 def measure_batched(I, n_films=128, sweeps_per_step=20, seed=4, plain=True, ranks=None):
@@ -334,19 +380,21 @@ def measure_served(I, rate=200.0, duration=5.0, seed=5, pool=24, budget_gb=40.0,
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one bench launch of the dominant kernel, from
-# the ncu capture summarised in profiles/ (k_resident_fractal256.md), valid while the kernel's
-# sources hash to the recorded value.
+# the ncu captures summarised in profiles/, valid while the kernel's sources hash to the
+# recorded value (None: not captured for the current sources).
 NCU_TRAFFIC = {
-    "fractal256": {"sources_sha256": "8aafcffba79d140da5a89965bd1e63e4de8f1808cd93f9adf4dc5f7bce8eac91",
+    "fractal256": {"sources": ["kernels_resident.cu", "sweep_core.cuh", "device_common.cuh"],
+                   "sources_sha256": "8aafcffba79d140da5a89965bd1e63e4de8f1808cd93f9adf4dc5f7bce8eac91",
                    "bytes_per_launch": 1.25e6},
+    "fractal2048": {"sources": ["kernels_sweep.cu", "sweep_core.cuh", "device_common.cuh"],
+                    "sources_sha256": None, "bytes_per_launch": None},
 }
-KERNEL_SOURCES = ["kernels_resident.cu", "sweep_core.cuh", "device_common.cuh"]
 
 
-def kernel_sources_sha256() -> str:
+def kernel_sources_sha256(names) -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in names:
         with open(os.path.join(ROOT, "paper_1205_5588_gb300", "csrc", name), "rb") as fp:
             h.update(fp.read())
     return h.hexdigest()
@@ -354,7 +402,7 @@ def kernel_sources_sha256() -> str:
 
 def load_traffic(workload_name):
     rec = NCU_TRAFFIC.get(workload_name)
-    if not rec or rec["sources_sha256"] != kernel_sources_sha256():
+    if not rec or rec["sources_sha256"] != kernel_sources_sha256(rec["sources"]):
         return None
     return rec["bytes_per_launch"]
 
@@ -455,6 +503,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-multispin", action="store_true", help="skip the bit-packed 2048^2 loop leg")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--batch-films", type=int, default=128)
     ap.add_argument("--batch-sweeps", type=int, default=20, help="sweeps per schedule step of the batched films")

@@ -4,11 +4,13 @@
 // persistent launch per size class, optionally replayed from a captured CUDA graph.
 //
 // Classes: films whose int8 layout fits one CTA's shared memory go to a single-CTA queue
-// kernel; films that need a cluster go to a cluster queue kernel (K CTAs per film); the two
-// launches run concurrently on two forked streams and every CTA / cluster pulls films from its
-// queue (longest first).  Films that fit neither (packed, or larger than a cluster) run after
-// them on the global-memory path.  Every film keeps its own RNG key and sweep counter, so its
-// trajectory is the one it has alone.
+// kernel (A); films that need a cluster go to a cluster queue kernel (B, K CTAs per film);
+// the remaining films of up to 2^20 lattice sites (bit-packed ones, periodic-column ones, and
+// int8 ones too large for a cluster) go to a queue kernel that runs each on one CTA with its
+// state in global memory (D).  The three launches run concurrently on forked streams and every
+// CTA / cluster pulls films from its queue (longest first).  Larger films (C) run after them
+// on the multi-CTA global-memory path, one launch each.  Every film keeps its own RNG key and
+// sweep counter, so its trajectory is the one it has alone.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,19 +30,23 @@ struct isf_batch {
     std::vector<isf_lattice*> films;
     int32_t threads_a = 0, K_b = 0, threads_b = 0;   // 0 = tuned or default
     bool use_graph = false;
-    // device-side queues: class A entries, then class B entries
+    // device-side queues: class A entries, then class B entries; class D entries
     ResArgs* d_desc = nullptr;
     size_t cap = 0;
-    unsigned* d_next = nullptr;
+    unsigned* d_next = nullptr;  // queue counters of A, B, D
     ResArgs* h_desc = nullptr;   // pinned staging
-    cudaStream_t sa = nullptr, sb = nullptr, sc = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_a = nullptr, ev_b = nullptr, ev_done = nullptr;
+    SweepArgs* d_gdesc = nullptr;
+    SweepArgs* h_gdesc = nullptr;
+    size_t gcap = 0;
+    cudaStream_t sa = nullptr, sb = nullptr, sc = nullptr, sd = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_a = nullptr, ev_b = nullptr, ev_d = nullptr, ev_done = nullptr;
     bool pending = false;
     // graph
     cudaGraphExec_t gexec = nullptr;
-    int64_t gsig[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t gsig[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     // last run
     int32_t n_a = 0, n_b = 0, n_c = 0, units_a = 0, units_b = 0, used_K = 0, used_ta = 0, used_tb = 0;
+    int32_t n_d = 0, units_d = 0;
     int device = 0;
 };
 
@@ -49,6 +55,8 @@ namespace {
 constexpr int kDefaultThreadsA = 256;
 constexpr int kDefaultK = 16;
 constexpr int kDefaultThreadsB = 512;
+constexpr int kThreadsD = 256;                      // one CTA per film, state in global memory
+constexpr int64_t kMaxSitesD = (int64_t)1 << 20;    // larger films take the whole GPU (class C)
 
 int fail(int code, const std::string& msg) { return set_last_error(code, msg.c_str()); }
 
@@ -68,11 +76,27 @@ int ensure_streams(isf_batch* b) {
     CUDA_TRY(cudaStreamCreateWithFlags(&b->sa, cudaStreamNonBlocking), "stream");
     CUDA_TRY(cudaStreamCreateWithFlags(&b->sb, cudaStreamNonBlocking), "stream");
     CUDA_TRY(cudaStreamCreateWithFlags(&b->sc, cudaStreamNonBlocking), "stream");
+    CUDA_TRY(cudaStreamCreateWithFlags(&b->sd, cudaStreamNonBlocking), "stream");
     CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "event");
     CUDA_TRY(cudaEventCreateWithFlags(&b->ev_a, cudaEventDisableTiming), "event");
     CUDA_TRY(cudaEventCreateWithFlags(&b->ev_b, cudaEventDisableTiming), "event");
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_d, cudaEventDisableTiming), "event");
     CUDA_TRY(cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming), "event");
-    CUDA_TRY(cudaMalloc(&b->d_next, 2 * sizeof(unsigned)), "cudaMalloc");
+    CUDA_TRY(cudaMalloc(&b->d_next, 3 * sizeof(unsigned)), "cudaMalloc");
+    return ISF_OK;
+}
+
+int ensure_gcapacity(isf_batch* b, size_t n) {
+    if (n <= b->gcap) return ISF_OK;
+    if (b->d_gdesc) cudaFree(b->d_gdesc);
+    if (b->h_gdesc) cudaFreeHost(b->h_gdesc);
+    b->d_gdesc = nullptr;
+    b->h_gdesc = nullptr;
+    b->gcap = 0;
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    CUDA_TRY(cudaMalloc(&b->d_gdesc, n * sizeof(SweepArgs)), "cudaMalloc batch queue");
+    CUDA_TRY(cudaMallocHost(&b->h_gdesc, n * sizeof(SweepArgs)), "cudaMallocHost batch queue");
+    b->gcap = n;
     return ISF_OK;
 }
 
@@ -90,13 +114,24 @@ int ensure_capacity(isf_batch* b, size_t n) {
     return ISF_OK;
 }
 
-// The launch sequence: queue upload, counters, fork, the two persistent launches, join.
+// The launch sequence: queue uploads, counters, fork, the persistent launches, join.
 int enqueue(isf_batch* b, cudaStream_t s, int n_a, int n_b, int K, int ta, int tb, uint32_t smem_a,
-            uint32_t smem_b, int units_a, int units_b) {
+            uint32_t smem_b, int units_a, int units_b, int n_d, int units_d) {
     const size_t n = (size_t)n_a + n_b;
-    CUDA_TRY(cudaMemcpyAsync(b->d_desc, b->h_desc, n * sizeof(ResArgs), cudaMemcpyHostToDevice, s), "upload queue");
-    CUDA_TRY(cudaMemsetAsync(b->d_next, 0, 2 * sizeof(unsigned), s), "reset queue");
+    if (n)
+        CUDA_TRY(cudaMemcpyAsync(b->d_desc, b->h_desc, n * sizeof(ResArgs), cudaMemcpyHostToDevice, s), "upload queue");
+    if (n_d)
+        CUDA_TRY(cudaMemcpyAsync(b->d_gdesc, b->h_gdesc, (size_t)n_d * sizeof(SweepArgs), cudaMemcpyHostToDevice, s),
+                 "upload queue");
+    CUDA_TRY(cudaMemsetAsync(b->d_next, 0, 3 * sizeof(unsigned), s), "reset queue");
     CUDA_TRY(cudaEventRecord(b->ev_fork, s), "fork");
+    if (n_d) {
+        CUDA_TRY(cudaStreamWaitEvent(b->sd, b->ev_fork, 0), "fork");
+        int e = launch_batch_global(b->d_gdesc, n_d, b->d_next + 2, kThreadsD, units_d, b->sd);
+        if (e) return cuda_fail((cudaError_t)e, "batch launch (one CTA per film, global memory)");
+        CUDA_TRY(cudaEventRecord(b->ev_d, b->sd), "join");
+        CUDA_TRY(cudaStreamWaitEvent(s, b->ev_d, 0), "join");
+    }
     if (n_a) {
         CUDA_TRY(cudaStreamWaitEvent(b->sa, b->ev_fork, 0), "fork");
         int e = launch_batch(b->d_desc, n_a, b->d_next, 1, ta, smem_a, units_a, b->sa);
@@ -281,7 +316,7 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
     const int ta = b->threads_a ? b->threads_a : kDefaultThreadsA;
     const int K = b->K_b ? b->K_b : kDefaultK;
     const int tb = b->threads_b ? b->threads_b : kDefaultThreadsB;
-    std::vector<Item> A, B;
+    std::vector<Item> A, B, D;
     std::vector<isf_lattice*> C;
     for (isf_lattice* L : b->films) {
         if (L->device != b->device) return fail(ISF_ERR_ARG, "all films of a batch must be on one device");
@@ -291,17 +326,29 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
         Item it{L, n, {}, (double)n * L->lay.L * L->lay.Rh * L->lay.Ch};
         // the queue kernels hold int8 films without periodic columns
         const bool queueable = !L->lay.packed && !(L->lay.flags & ISF_PERIODIC_X);
+        const int64_t sites = (int64_t)L->lay.L * L->lay.R * L->lay.C;
         if (queueable && resident_plan(L->f, 1, ta, 16, &it.plan) == 0) A.push_back(it);
         else if (queueable && resident_plan(L->f, K, tb, 16, &it.plan) == 0) B.push_back(it);
+        else if (sites <= kMaxSitesD) D.push_back(it);
         else C.push_back(L);
         cudaGetLastError();
     }
     auto longest_first = [](const Item& x, const Item& y) { return x.work > y.work; };
     std::sort(A.begin(), A.end(), longest_first);
     std::sort(B.begin(), B.end(), longest_first);
-    const int n_a = (int)A.size(), n_b = (int)B.size();
+    std::sort(D.begin(), D.end(), longest_first);
+    const int n_a = (int)A.size(), n_b = (int)B.size(), n_d = (int)D.size();
     rc = ensure_capacity(b, (size_t)n_a + n_b + 1);
     if (rc) return rc;
+    rc = ensure_gcapacity(b, (size_t)n_d + 1);
+    if (rc) return rc;
+    for (int i = 0; i < n_d; ++i) b->h_gdesc[i] = sweep_args(D[i].L, D[i].nsweeps);
+    int units_d = 0;
+    if (n_d) {
+        int e = batch_global_units(kThreadsD, &units_d);
+        if (e || units_d < 1) return fail(ISF_ERR_CUDA, "global-memory batch kernel cannot be resident");
+        units_d = std::min(units_d, n_d);
+    }
     uint32_t smem_a = 0, smem_b = 0;
     for (int i = 0; i < n_a; ++i) {
         b->h_desc[i] = make_res_args(sweep_args(A[i].L, A[i].nsweeps), A[i].plan);
@@ -322,14 +369,14 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
         if (e || units_b < 1) return fail(ISF_ERR_CUDA, "cluster batch kernel cannot be resident");
         units_b = std::min(units_b, n_b);
     }
-    if (n_a || n_b) {
-        const int64_t sig[8] = {n_a, n_b, K, ta, tb, (int64_t)smem_a << 32 | smem_b, units_a, units_b};
+    if (n_a || n_b || n_d) {
+        const int64_t sig[10] = {n_a, n_b, K, ta, tb, (int64_t)smem_a << 32 | smem_b, units_a, units_b, n_d, units_d};
         if (b->use_graph) {
             if (!b->gexec || std::memcmp(sig, b->gsig, sizeof sig)) {
                 if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
                 cudaGraph_t g = nullptr;
                 CUDA_TRY(cudaStreamBeginCapture(b->sc, cudaStreamCaptureModeRelaxed), "begin capture");
-                rc = enqueue(b, b->sc, n_a, n_b, K, ta, tb, smem_a, smem_b, units_a, units_b);
+                rc = enqueue(b, b->sc, n_a, n_b, K, ta, tb, smem_a, smem_b, units_a, units_b, n_d, units_d);
                 cudaError_t ce = cudaStreamEndCapture(b->sc, &g);
                 if (rc) { if (g) cudaGraphDestroy(g); return rc; }
                 if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
@@ -340,7 +387,7 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
             }
             CUDA_TRY(cudaGraphLaunch(b->gexec, s), "graph launch");
         } else {
-            rc = enqueue(b, s, n_a, n_b, K, ta, tb, smem_a, smem_b, units_a, units_b);
+            rc = enqueue(b, s, n_a, n_b, K, ta, tb, smem_a, smem_b, units_a, units_b, n_d, units_d);
             if (rc) return rc;
         }
         CUDA_TRY(cudaEventRecord(b->ev_done, s), "batch done");
@@ -356,6 +403,12 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
         it.L->last = s;
         it.L->last_path = ISF_PATH_RESIDENT; it.L->last_ctas = K; it.L->last_threads = tb;
     }
+    for (const Item& it : D) {
+        advance_cursor(it.L, it.nsweeps);
+        it.L->last = s;
+        it.L->last_path = ISF_PATH_GLOBAL; it.L->last_ctas = 1; it.L->last_threads = kThreadsD;
+        it.L->last_sites = it.L->lay.packed ? 32 : 16;
+    }
     for (isf_lattice* L : C) {
         const int32_t saved = L->path;
         L->path = ISF_PATH_GLOBAL;
@@ -365,16 +418,17 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
         L->path = saved;
         if (rc) return rc;
     }
-    b->n_a = n_a; b->n_b = n_b; b->n_c = (int)C.size();
-    b->units_a = units_a; b->units_b = units_b;
+    b->n_a = n_a; b->n_b = n_b; b->n_c = (int)C.size(); b->n_d = n_d;
+    b->units_a = units_a; b->units_b = units_b; b->units_d = units_d;
     b->used_K = K; b->used_ta = ta; b->used_tb = tb;
     return set_last_error(ISF_OK, "");
 }
 
-int isf_batch_info(isf_batch* b, int32_t* out8) {
-    if (!b || !out8) return fail(ISF_ERR_ARG, "bad arguments");
-    const int32_t v[8] = {b->n_a, b->n_b, b->n_c, b->units_a, b->units_b, b->used_K, b->used_ta, b->used_tb};
-    std::memcpy(out8, v, sizeof v);
+int isf_batch_info(isf_batch* b, int32_t* out10) {
+    if (!b || !out10) return fail(ISF_ERR_ARG, "bad arguments");
+    const int32_t v[10] = {b->n_a, b->n_b, b->n_c, b->units_a, b->units_b, b->used_K, b->used_ta, b->used_tb,
+                           b->n_d, b->units_d};
+    std::memcpy(out10, v, sizeof v);
     return ISF_OK;
 }
 
@@ -387,12 +441,16 @@ void isf_batch_destroy(isf_batch* b) {
         cudaStreamDestroy(b->sa);
         cudaStreamDestroy(b->sb);
         cudaStreamDestroy(b->sc);
+        cudaStreamDestroy(b->sd);
         cudaEventDestroy(b->ev_fork);
         cudaEventDestroy(b->ev_a);
         cudaEventDestroy(b->ev_b);
+        cudaEventDestroy(b->ev_d);
         cudaEventDestroy(b->ev_done);
         if (b->d_desc) cudaFree(b->d_desc);
         if (b->h_desc) cudaFreeHost(b->h_desc);
+        if (b->d_gdesc) cudaFree(b->d_gdesc);
+        if (b->h_gdesc) cudaFreeHost(b->h_gdesc);
         if (b->d_next) cudaFree(b->d_next);
     }
     delete b;

@@ -179,5 +179,9 @@ int batch_units_possible(int K, int threads, uint32_t smem, int* units);
 int launch_batch(const ResArgs* films, int n, unsigned* next, int K, int threads, uint32_t smem,
                  int units, void* stream);
 int sweep_items_per_pass(const DevFilm& f);                            // work items per colour pass
+// Batched films one CTA each in global memory (kernels_sweep.cu): `units` persistent CTAs take
+// films from the device queue films[0..n) via the counter *next; any layout and boundary.
+int batch_global_units(int threads, int* units);
+int launch_batch_global(const SweepArgs* films, int n, unsigned* next, int threads, int units, void* stream);
 
 }  // namespace isf

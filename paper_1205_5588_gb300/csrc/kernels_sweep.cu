@@ -278,22 +278,22 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
 // CTA b is warp w * G + b), so when a pass has fewer items than two per thread, the threads
 // that take one more item are spread evenly over all CTAs (and SMs); lanes stay consecutive,
 // so a warp still reads consecutive words.
-__device__ __forceinline__ int first_item() {
-    return (((int)(threadIdx.x >> 5) * (int)gridDim.x + (int)blockIdx.x) << 5) + (int)(threadIdx.x & 31);
+__device__ __forceinline__ int first_item(unsigned G, unsigned cta) {
+    return (((int)(threadIdx.x >> 5) * (int)G + (int)cta) << 5) + (int)(threadIdx.x & 31);
 }
 
 template <int MODE, bool GATE>
 __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned long long sweep,
                                             const uint32_t* tab, uint32_t gthr, int items,
-                                            ItemWalk w, int& dM, int& dB) {
-    const int stride = gridDim.x * blockDim.x;
+                                            ItemWalk w, unsigned G, unsigned cta, int& dM, int& dB) {
+    const int stride = (int)G * blockDim.x;
     if (MODE == MODE_PACKED && f.items) {
         // the colour's occupied words only, thread t taking entries t, t + stride, ...
         const uint32_t* list = f.items + (int64_t)c * f.item_cap;
         const int n = f.nitems[c];
         const int wb = f.item_wbits, jb = f.item_jbits;
         const uint32_t wmask = (1u << wb) - 1u, jmask = (1u << jb) - 1u;
-        for (int it = first_item(); it < n; it += stride) {
+        for (int it = first_item(G, cta); it < n; it += stride) {
             const uint32_t e = list[it];
             if (f.narrow)
                 word_packed<GATE, true>(f, c, (int)(e >> (jb + wb)), (int)((e >> wb) & jmask), (int)(e & wmask), sweep,
@@ -304,29 +304,30 @@ __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned lo
         }
         return;
     }
-    for (int it = first_item(); it < items; it += stride, w.next()) {
+    for (int it = first_item(G, cta); it < items; it += stride, w.next()) {
         if (MODE == MODE_INT8) chunk_int8<GATE>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
         else if (MODE == MODE_GENERIC) block_generic<GATE>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
         else word_packed<GATE, false>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
     }
 }
 
+// The launch's sweeps of one film by G CTAs (this one is number cta), the film in global
+// memory; G = 1 needs no grid barrier.
 template <int MODE>
-__global__ void __launch_bounds__(kBlock) k_sweep(const __grid_constant__ SweepArgs a) {
+__device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsigned cta) {
     __shared__ uint32_t tab[128];
     __shared__ uint32_t gate_s;
     __shared__ long long red[64];
     __shared__ int ok_s;
     const DevFilm& f = a.f;
     FilmState* st = a.st;
-    const unsigned G = gridDim.x;
     unsigned target = 0;
     const int per_row = MODE == MODE_INT8 ? f.nck : (MODE == MODE_GENERIC ? f.Qw : f.nw);
     const int items = f.L * f.Rh * per_row;
     ItemWalk walk0;
-    walk0.init(first_item(), gridDim.x * blockDim.x, per_row, f.Rh);
+    walk0.init(first_item(G, cta), (int)G * blockDim.x, per_row, f.Rh);
     int k = a.k0, pos = a.pos0;
-    const bool folder = blockIdx.x == 0 && threadIdx.x == 0;
+    const bool folder = cta == 0 && threadIdx.x == 0;
     __shared__ RunState rs;     // touched by the folding thread only
     int k_eq = 0, k_tot = 0;
     if (folder) {
@@ -346,8 +347,8 @@ __global__ void __launch_bounds__(kBlock) k_sweep(const __grid_constant__ SweepA
         const uint32_t gthr = gate_s;
         int dM = 0, dB = 0;
         for (int c = 0; c < 4; ++c) {
-            if (a.use_gate) colour_pass<MODE, true>(f, c, sweep, tab, gthr, items, walk0, dM, dB);
-            else colour_pass<MODE, false>(f, c, sweep, tab, gthr, items, walk0, dM, dB);
+            if (a.use_gate) colour_pass<MODE, true>(f, c, sweep, tab, gthr, items, walk0, G, cta, dM, dB);
+            else colour_pass<MODE, false>(f, c, sweep, tab, gthr, items, walk0, G, cta, dM, dB);
             if (c == 3) {
                 long long sM = dM, sB = dB;
                 block_sum2(sM, sB, red);
@@ -368,6 +369,35 @@ __global__ void __launch_bounds__(kBlock) k_sweep(const __grid_constant__ SweepA
         ++pos;
     }
     if (folder) store_run_state(st, rs);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kBlock) k_sweep(const __grid_constant__ SweepArgs a) {
+    sweep_body<MODE>(a, gridDim.x, blockIdx.x);
+}
+
+__device__ __forceinline__ int mode_of_film(const DevFilm& f) {
+    return f.packed ? MODE_PACKED : ((f.flags & 7u) ? MODE_GENERIC : MODE_INT8);
+}
+
+// Batched films one CTA each, with their state in global memory: every CTA takes the next film
+// of the queue (a device counter), runs its sweeps (colour passes separated by __syncthreads
+// only) and takes another until the queue is empty.  Films are independent chains.
+__global__ void __launch_bounds__(kBlock) k_batch_global(const SweepArgs* films, int nfilms, unsigned* next) {
+    __shared__ int film_s;
+    for (;;) {
+        if (threadIdx.x == 0) film_s = (int)atomicAdd(next, 1u);
+        __syncthreads();
+        const int idx = film_s;
+        __syncthreads();        // every thread has the index before thread 0 takes the next one
+        if (idx < 0 || idx >= nfilms) break;
+        const SweepArgs& a = films[idx];
+        switch (mode_of_film(a.f)) {
+            case MODE_INT8: sweep_body<MODE_INT8>(a, 1u, 0u); break;
+            case MODE_GENERIC: sweep_body<MODE_GENERIC>(a, 1u, 0u); break;
+            default: sweep_body<MODE_PACKED>(a, 1u, 0u); break;
+        }
+    }
 }
 
 template <int MODE>
@@ -415,6 +445,21 @@ int sweep_max_ctas_for(const DevFilm& f, int threads, int* max_ctas) {
         case MODE_GENERIC: return max_ctas_mode<MODE_GENERIC>(threads, max_ctas);
         default: return max_ctas_mode<MODE_PACKED>(threads, max_ctas);
     }
+}
+
+int batch_global_units(int threads, int* units) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_global, threads, 0);
+    *units = sms * per;
+    return (int)e;
+}
+
+int launch_batch_global(const SweepArgs* films, int n, unsigned* next, int threads, int units, void* stream) {
+    if (threads % 32 || threads < 32 || threads > kBlock || units < 1) return (int)cudaErrorInvalidValue;
+    k_batch_global<<<units, threads, 0, static_cast<cudaStream_t>(stream)>>>(films, n, next);
+    return (int)cudaGetLastError();
 }
 
 int sweep_items_per_pass(const DevFilm& f) {
