@@ -220,8 +220,11 @@ def run_impl(args):
         # independent films: each rank runs its own share of the list (weak scaling)
         b = measure_batched(I, n_films=args.batch_films, sweeps_per_step=args.batch_sweeps, ranks=ranks,
                             plain=ranks.world == 1)
+        bp = measure_batched(I, n_films=args.batch_films, sweeps_per_step=args.batch_sweeps, ranks=ranks,
+                             plain=ranks.world == 1, packed=True)
         if rank == 0:
             line["batched"] = b
+            line["batched_packed"] = bp
     if rank == 0 and not args.no_served:
         line["served"] = measure_served(I, rate=args.serve_rate, duration=args.serve_seconds)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -273,10 +276,10 @@ def measure_multispin(I, ranks, steps=2, warmup=1):
                          "ops_per_attempt": OPS_PER_ATTEMPT}}
 
 
-def measure_batched(I, n_films=128, sweeps_per_step=20, seed=4, plain=True, ranks=None):
+def measure_batched(I, n_films=128, sweeps_per_step=20, seed=4, plain=True, ranks=None, packed=False):
     """Batched films (ragged sizes 64..1024, 1..8 layers, own T and field loop each) advanced to
-    the end of their schedules by isf_batch_run, against the same films run one per launch.
-    Under several ranks each rank runs its round-robin share of the films."""
+    the end of their schedules by isf_batch_run, against the same films run one per launch; int8
+    or bit-packed spins.  Under several ranks each rank runs its round-robin share of the films."""
     import torch
     from paper_1205_5588_gb300 import distributed as D
     from paper_1205_5588_gb300 import workloads as W
@@ -285,7 +288,7 @@ def measure_batched(I, n_films=128, sweeps_per_step=20, seed=4, plain=True, rank
     films = [films[i] for i in D.shard(len(films), ranks.rank, ranks.world)]
     lats = []
     for f in films:
-        L = I.Lattice(f["heights"], f["layers"], seed=f["seed"])
+        L = I.Lattice(f["heights"], f["layers"], seed=f["seed"], packed=packed)
         lats.append(L)
     att = sum(L.info()["n_occ"] * int(f["schedule"]["eq"].sum() + f["schedule"]["meas"].sum())
               for L, f in zip(lats, films))
@@ -310,6 +313,7 @@ def measure_batched(I, n_films=128, sweeps_per_step=20, seed=4, plain=True, rank
     t_batch = D.max_over_ranks(a.elapsed_time(e) / 1e3, ranks, device="cuda")
     att_all = int(D.sum_over_ranks(att, ranks, device="cuda"))
     out = {"value": att_all / t_batch, "unit": UNIT, "films": n_films, "attempts": att_all, "seconds": t_batch,
+           "spins": "u32 (1 bit/spin)" if packed else "int8",
            "sweeps_per_step": sweeps_per_step, "launch": b.info(), "graph": True,
            "ranks": ranks.world, "scaling": "weak (films dealt out across ranks)"}
     b.close()
@@ -329,10 +333,10 @@ def measure_batched(I, n_films=128, sweeps_per_step=20, seed=4, plain=True, rank
     return out
 
 
-def measure_served(I, rate=200.0, duration=5.0, seed=5, pool=24, budget_gb=40.0, sweeps_per_tick=50):
+def measure_served(I, rate=200.0, duration=5.0, seed=5, pool=24, budget_gb=40.0, sweeps_per_tick=50, packed=True):
     """Poisson stream of hysteresis-loop and temperature-scan jobs (50/50) on films with
-    log-normal side length (median 256, 64..2048) and 1..8 layers, served with continuous
-    batching; latency is submit -> completion."""
+    log-normal side length (median 256, 64..2048) and 1..8 layers, bit-packed spins, served with
+    continuous batching; latency is submit -> completion."""
     import torch
     from paper_1205_5588_gb300 import workloads as W
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -359,7 +363,7 @@ def measure_served(I, rate=200.0, duration=5.0, seed=5, pool=24, budget_gb=40.0,
         dt = t0 + t_arr - time.perf_counter()
         if dt > 0:
             time.sleep(dt)
-        ids.append(srv.submit(H, L, sc["T"], sc["h"], sc["eq"], sc["meas"], seed=sd))
+        ids.append(srv.submit(H, L, sc["T"], sc["h"], sc["eq"], sc["meas"], seed=sd, packed=packed))
     lat = []
     for jid in ids:
         state = srv.wait(jid, timeout=600.0)
@@ -376,7 +380,8 @@ def measure_served(I, rate=200.0, duration=5.0, seed=5, pool=24, budget_gb=40.0,
             "arrival_window_s": duration, "wall_s": wall,
             "offered": st["attempts_done"] / duration, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "ticks": st["ticks"], "sweeps_per_tick": sweeps_per_tick,
-            "gpu_busy_s": st["busy_s"], "peak_device_bytes": st["peak_bytes"], "spins": "int8"}
+            "gpu_busy_s": st["busy_s"], "peak_device_bytes": st["peak_bytes"],
+            "spins": "u32 (1 bit/spin)" if packed else "int8"}
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one bench launch of the dominant kernel, from

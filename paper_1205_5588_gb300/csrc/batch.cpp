@@ -5,11 +5,12 @@
 //
 // Classes: films whose int8 layout fits one CTA's shared memory go to a single-CTA queue
 // kernel (A); films that need a cluster go to a cluster queue kernel (B, K CTAs per film);
-// the remaining films of up to 2^20 lattice sites (bit-packed ones, periodic-column ones, and
-// int8 ones too large for a cluster) go to a queue kernel that runs each on one CTA with its
-// state in global memory (D).  The three launches run concurrently on forked streams and every
-// CTA / cluster pulls films from its queue (longest first).  Larger films (C) run after them
-// on the multi-CTA global-memory path, one launch each.  Every film keeps its own RNG key and
+// the remaining films (bit-packed ones, periodic-column ones, and int8 ones too large for a
+// cluster's shared memory) keep their state in global memory and go to a queue kernel that runs
+// each on one CTA (D, up to 2^20 lattice sites) or on one cluster of 8 CTAs (E, up to 2^24).
+// The four launches run concurrently on forked streams and every CTA / cluster pulls films from
+// its queue (longest first).  Larger films (C) run after them on the multi-CTA global-memory
+// path, one launch each.  Every film keeps its own RNG key and
 // sweep counter, so its trajectory is the one it has alone.
 #include <cuda_runtime.h>
 
@@ -33,20 +34,20 @@ struct isf_batch {
     // device-side queues: class A entries, then class B entries; class D entries
     ResArgs* d_desc = nullptr;
     size_t cap = 0;
-    unsigned* d_next = nullptr;  // queue counters of A, B, D
+    unsigned* d_next = nullptr;  // queue counters of A, B, D, E
     ResArgs* h_desc = nullptr;   // pinned staging
-    SweepArgs* d_gdesc = nullptr;
+    SweepArgs* d_gdesc = nullptr;   // class D entries, then class E entries
     SweepArgs* h_gdesc = nullptr;
     size_t gcap = 0;
-    cudaStream_t sa = nullptr, sb = nullptr, sc = nullptr, sd = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_a = nullptr, ev_b = nullptr, ev_d = nullptr, ev_done = nullptr;
+    cudaStream_t sa = nullptr, sb = nullptr, sc = nullptr, sd = nullptr, se = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_a = nullptr, ev_b = nullptr, ev_d = nullptr, ev_e = nullptr, ev_done = nullptr;
     bool pending = false;
     // graph
     cudaGraphExec_t gexec = nullptr;
-    int64_t gsig[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t gsig[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     // last run
     int32_t n_a = 0, n_b = 0, n_c = 0, units_a = 0, units_b = 0, used_K = 0, used_ta = 0, used_tb = 0;
-    int32_t n_d = 0, units_d = 0;
+    int32_t n_d = 0, units_d = 0, n_e = 0, units_e = 0;
     int device = 0;
 };
 
@@ -56,7 +57,9 @@ constexpr int kDefaultThreadsA = 256;
 constexpr int kDefaultK = 16;
 constexpr int kDefaultThreadsB = 512;
 constexpr int kThreadsD = 256;                      // one CTA per film, state in global memory
-constexpr int64_t kMaxSitesD = (int64_t)1 << 20;    // larger films take the whole GPU (class C)
+constexpr int64_t kMaxSitesD = (int64_t)1 << 20;    // larger films take a cluster (class E)
+constexpr int kKE = 8, kThreadsE = 256;             // one cluster of 8 CTAs per film, global memory
+constexpr int64_t kMaxSitesE = (int64_t)1 << 24;    // larger films take the whole GPU (class C)
 
 int fail(int code, const std::string& msg) { return set_last_error(code, msg.c_str()); }
 
@@ -77,12 +80,14 @@ int ensure_streams(isf_batch* b) {
     CUDA_TRY(cudaStreamCreateWithFlags(&b->sb, cudaStreamNonBlocking), "stream");
     CUDA_TRY(cudaStreamCreateWithFlags(&b->sc, cudaStreamNonBlocking), "stream");
     CUDA_TRY(cudaStreamCreateWithFlags(&b->sd, cudaStreamNonBlocking), "stream");
+    CUDA_TRY(cudaStreamCreateWithFlags(&b->se, cudaStreamNonBlocking), "stream");
     CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "event");
     CUDA_TRY(cudaEventCreateWithFlags(&b->ev_a, cudaEventDisableTiming), "event");
     CUDA_TRY(cudaEventCreateWithFlags(&b->ev_b, cudaEventDisableTiming), "event");
     CUDA_TRY(cudaEventCreateWithFlags(&b->ev_d, cudaEventDisableTiming), "event");
+    CUDA_TRY(cudaEventCreateWithFlags(&b->ev_e, cudaEventDisableTiming), "event");
     CUDA_TRY(cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming), "event");
-    CUDA_TRY(cudaMalloc(&b->d_next, 3 * sizeof(unsigned)), "cudaMalloc");
+    CUDA_TRY(cudaMalloc(&b->d_next, 4 * sizeof(unsigned)), "cudaMalloc");
     return ISF_OK;
 }
 
@@ -116,14 +121,14 @@ int ensure_capacity(isf_batch* b, size_t n) {
 
 // The launch sequence: queue uploads, counters, fork, the persistent launches, join.
 int enqueue(isf_batch* b, cudaStream_t s, int n_a, int n_b, int K, int ta, int tb, uint32_t smem_a,
-            uint32_t smem_b, int units_a, int units_b, int n_d, int units_d) {
+            uint32_t smem_b, int units_a, int units_b, int n_d, int units_d, int n_e, int units_e) {
     const size_t n = (size_t)n_a + n_b;
     if (n)
         CUDA_TRY(cudaMemcpyAsync(b->d_desc, b->h_desc, n * sizeof(ResArgs), cudaMemcpyHostToDevice, s), "upload queue");
-    if (n_d)
-        CUDA_TRY(cudaMemcpyAsync(b->d_gdesc, b->h_gdesc, (size_t)n_d * sizeof(SweepArgs), cudaMemcpyHostToDevice, s),
-                 "upload queue");
-    CUDA_TRY(cudaMemsetAsync(b->d_next, 0, 3 * sizeof(unsigned), s), "reset queue");
+    if (n_d + n_e)
+        CUDA_TRY(cudaMemcpyAsync(b->d_gdesc, b->h_gdesc, (size_t)(n_d + n_e) * sizeof(SweepArgs),
+                                 cudaMemcpyHostToDevice, s), "upload queue");
+    CUDA_TRY(cudaMemsetAsync(b->d_next, 0, 4 * sizeof(unsigned), s), "reset queue");
     CUDA_TRY(cudaEventRecord(b->ev_fork, s), "fork");
     if (n_d) {
         CUDA_TRY(cudaStreamWaitEvent(b->sd, b->ev_fork, 0), "fork");
@@ -131,6 +136,13 @@ int enqueue(isf_batch* b, cudaStream_t s, int n_a, int n_b, int K, int ta, int t
         if (e) return cuda_fail((cudaError_t)e, "batch launch (one CTA per film, global memory)");
         CUDA_TRY(cudaEventRecord(b->ev_d, b->sd), "join");
         CUDA_TRY(cudaStreamWaitEvent(s, b->ev_d, 0), "join");
+    }
+    if (n_e) {
+        CUDA_TRY(cudaStreamWaitEvent(b->se, b->ev_fork, 0), "fork");
+        int e = launch_batch_cluster_global(b->d_gdesc + n_d, n_e, b->d_next + 3, kKE, kThreadsE, units_e, b->se);
+        if (e) return cuda_fail((cudaError_t)e, "batch launch (one cluster per film, global memory)");
+        CUDA_TRY(cudaEventRecord(b->ev_e, b->se), "join");
+        CUDA_TRY(cudaStreamWaitEvent(s, b->ev_e, 0), "join");
     }
     if (n_a) {
         CUDA_TRY(cudaStreamWaitEvent(b->sa, b->ev_fork, 0), "fork");
@@ -316,7 +328,7 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
     const int ta = b->threads_a ? b->threads_a : kDefaultThreadsA;
     const int K = b->K_b ? b->K_b : kDefaultK;
     const int tb = b->threads_b ? b->threads_b : kDefaultThreadsB;
-    std::vector<Item> A, B, D;
+    std::vector<Item> A, B, D, E;
     std::vector<isf_lattice*> C;
     for (isf_lattice* L : b->films) {
         if (L->device != b->device) return fail(ISF_ERR_ARG, "all films of a batch must be on one device");
@@ -330,6 +342,7 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
         if (queueable && resident_plan(L->f, 1, ta, 16, &it.plan) == 0) A.push_back(it);
         else if (queueable && resident_plan(L->f, K, tb, 16, &it.plan) == 0) B.push_back(it);
         else if (sites <= kMaxSitesD) D.push_back(it);
+        else if (sites <= kMaxSitesE) E.push_back(it);
         else C.push_back(L);
         cudaGetLastError();
     }
@@ -337,12 +350,20 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
     std::sort(A.begin(), A.end(), longest_first);
     std::sort(B.begin(), B.end(), longest_first);
     std::sort(D.begin(), D.end(), longest_first);
-    const int n_a = (int)A.size(), n_b = (int)B.size(), n_d = (int)D.size();
+    std::sort(E.begin(), E.end(), longest_first);
+    const int n_a = (int)A.size(), n_b = (int)B.size(), n_d = (int)D.size(), n_e = (int)E.size();
     rc = ensure_capacity(b, (size_t)n_a + n_b + 1);
     if (rc) return rc;
-    rc = ensure_gcapacity(b, (size_t)n_d + 1);
+    rc = ensure_gcapacity(b, (size_t)n_d + n_e + 1);
     if (rc) return rc;
     for (int i = 0; i < n_d; ++i) b->h_gdesc[i] = sweep_args(D[i].L, D[i].nsweeps);
+    for (int i = 0; i < n_e; ++i) b->h_gdesc[n_d + i] = sweep_args(E[i].L, E[i].nsweeps);
+    int units_e = 0;
+    if (n_e) {
+        int e = batch_cluster_global_units(kKE, kThreadsE, &units_e);
+        if (e || units_e < 1) return fail(ISF_ERR_CUDA, "cluster global-memory batch kernel cannot be resident");
+        units_e = std::min(units_e, n_e);
+    }
     int units_d = 0;
     if (n_d) {
         int e = batch_global_units(kThreadsD, &units_d);
@@ -369,14 +390,15 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
         if (e || units_b < 1) return fail(ISF_ERR_CUDA, "cluster batch kernel cannot be resident");
         units_b = std::min(units_b, n_b);
     }
-    if (n_a || n_b || n_d) {
-        const int64_t sig[10] = {n_a, n_b, K, ta, tb, (int64_t)smem_a << 32 | smem_b, units_a, units_b, n_d, units_d};
+    if (n_a || n_b || n_d || n_e) {
+        const int64_t sig[12] = {n_a, n_b, K, ta, tb, (int64_t)smem_a << 32 | smem_b, units_a, units_b, n_d, units_d,
+                                 n_e, units_e};
         if (b->use_graph) {
             if (!b->gexec || std::memcmp(sig, b->gsig, sizeof sig)) {
                 if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
                 cudaGraph_t g = nullptr;
                 CUDA_TRY(cudaStreamBeginCapture(b->sc, cudaStreamCaptureModeRelaxed), "begin capture");
-                rc = enqueue(b, b->sc, n_a, n_b, K, ta, tb, smem_a, smem_b, units_a, units_b, n_d, units_d);
+                rc = enqueue(b, b->sc, n_a, n_b, K, ta, tb, smem_a, smem_b, units_a, units_b, n_d, units_d, n_e, units_e);
                 cudaError_t ce = cudaStreamEndCapture(b->sc, &g);
                 if (rc) { if (g) cudaGraphDestroy(g); return rc; }
                 if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
@@ -387,7 +409,7 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
             }
             CUDA_TRY(cudaGraphLaunch(b->gexec, s), "graph launch");
         } else {
-            rc = enqueue(b, s, n_a, n_b, K, ta, tb, smem_a, smem_b, units_a, units_b, n_d, units_d);
+            rc = enqueue(b, s, n_a, n_b, K, ta, tb, smem_a, smem_b, units_a, units_b, n_d, units_d, n_e, units_e);
             if (rc) return rc;
         }
         CUDA_TRY(cudaEventRecord(b->ev_done, s), "batch done");
@@ -409,6 +431,12 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
         it.L->last_path = ISF_PATH_GLOBAL; it.L->last_ctas = 1; it.L->last_threads = kThreadsD;
         it.L->last_sites = it.L->lay.packed ? 32 : 16;
     }
+    for (const Item& it : E) {
+        advance_cursor(it.L, it.nsweeps);
+        it.L->last = s;
+        it.L->last_path = ISF_PATH_GLOBAL; it.L->last_ctas = kKE; it.L->last_threads = kThreadsE;
+        it.L->last_sites = it.L->lay.packed ? 32 : 16;
+    }
     for (isf_lattice* L : C) {
         const int32_t saved = L->path;
         L->path = ISF_PATH_GLOBAL;
@@ -418,17 +446,17 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
         L->path = saved;
         if (rc) return rc;
     }
-    b->n_a = n_a; b->n_b = n_b; b->n_c = (int)C.size(); b->n_d = n_d;
-    b->units_a = units_a; b->units_b = units_b; b->units_d = units_d;
+    b->n_a = n_a; b->n_b = n_b; b->n_c = (int)C.size(); b->n_d = n_d; b->n_e = n_e;
+    b->units_a = units_a; b->units_b = units_b; b->units_d = units_d; b->units_e = units_e;
     b->used_K = K; b->used_ta = ta; b->used_tb = tb;
     return set_last_error(ISF_OK, "");
 }
 
-int isf_batch_info(isf_batch* b, int32_t* out10) {
-    if (!b || !out10) return fail(ISF_ERR_ARG, "bad arguments");
-    const int32_t v[10] = {b->n_a, b->n_b, b->n_c, b->units_a, b->units_b, b->used_K, b->used_ta, b->used_tb,
-                           b->n_d, b->units_d};
-    std::memcpy(out10, v, sizeof v);
+int isf_batch_info(isf_batch* b, int32_t* out12) {
+    if (!b || !out12) return fail(ISF_ERR_ARG, "bad arguments");
+    const int32_t v[12] = {b->n_a, b->n_b, b->n_c, b->units_a, b->units_b, b->used_K, b->used_ta, b->used_tb,
+                           b->n_d, b->units_d, b->n_e, b->units_e};
+    std::memcpy(out12, v, sizeof v);
     return ISF_OK;
 }
 
@@ -442,10 +470,12 @@ void isf_batch_destroy(isf_batch* b) {
         cudaStreamDestroy(b->sb);
         cudaStreamDestroy(b->sc);
         cudaStreamDestroy(b->sd);
+        cudaStreamDestroy(b->se);
         cudaEventDestroy(b->ev_fork);
         cudaEventDestroy(b->ev_a);
         cudaEventDestroy(b->ev_b);
         cudaEventDestroy(b->ev_d);
+        cudaEventDestroy(b->ev_e);
         cudaEventDestroy(b->ev_done);
         if (b->d_desc) cudaFree(b->d_desc);
         if (b->h_desc) cudaFreeHost(b->h_desc);

@@ -86,6 +86,18 @@ __device__ __forceinline__ bool neighbour_of(const DevFilm& f, int x, int y, int
     return true;
 }
 
+// Thread-block cluster: this CTA's rank, and a barrier over every thread of the cluster whose
+// release / acquire orders all earlier memory operations (shared, distributed shared and
+// global) before everything after it in the other CTAs.
+__device__ __forceinline__ unsigned cluster_ctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ long long warp_sum(long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);

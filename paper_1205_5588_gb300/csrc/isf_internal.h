@@ -183,5 +183,9 @@ int sweep_items_per_pass(const DevFilm& f);                            // work i
 // films from the device queue films[0..n) via the counter *next; any layout and boundary.
 int batch_global_units(int threads, int* units);
 int launch_batch_global(const SweepArgs* films, int n, unsigned* next, int threads, int units, void* stream);
+// The same with one thread-block cluster of K (2, 4 or 8) CTAs per film.
+int batch_cluster_global_units(int K, int threads, int* units);
+int launch_batch_cluster_global(const SweepArgs* films, int n, unsigned* next, int K, int threads, int units,
+                                void* stream);
 
 }  // namespace isf

@@ -311,9 +311,13 @@ __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned lo
     }
 }
 
+// Barrier between colour passes: over a cooperative grid (counter in the film's state), or
+// over the CTAs of one thread-block cluster (hardware barrier).
+enum { BAR_GRID = 0, BAR_CLUSTER = 1 };
+
 // The launch's sweeps of one film by G CTAs (this one is number cta), the film in global
-// memory; G = 1 needs no grid barrier.
-template <int MODE>
+// memory; G = 1 needs no barrier beyond __syncthreads.
+template <int MODE, int BAR = BAR_GRID>
 __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsigned cta) {
     __shared__ uint32_t tab[128];
     __shared__ uint32_t gate_s;
@@ -358,7 +362,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
                     atomicAdd(acc + 1, (unsigned long long)sB);
                 }
             }
-            if (!grid_barrier(st, G, target, &ok_s)) return;
+            if (BAR == BAR_CLUSTER) {
+                if (G > 1) cluster_barrier();
+                else __syncthreads();
+            } else if (!grid_barrier(st, G, target, &ok_s)) {
+                return;
+            }
         }
         if (folder) {
             unsigned long long* acc = reinterpret_cast<unsigned long long*>(&st->acc[sweep & 1][0]);
@@ -374,6 +383,38 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
 template <int MODE>
 __global__ void __launch_bounds__(kBlock) k_sweep(const __grid_constant__ SweepArgs a) {
     sweep_body<MODE>(a, gridDim.x, blockIdx.x);
+}
+
+__device__ __forceinline__ int mode_of_film(const DevFilm& f);
+
+// Batched films one thread-block cluster of K CTAs each, with their state in global memory:
+// every cluster takes the next film of the queue and runs its sweeps, colour passes separated
+// by the cluster barrier.
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_batch_cluster_global(const SweepArgs* films, int nfilms,
+                                                                 unsigned* next) {
+    __shared__ int film_s;
+    const unsigned rank = cluster_ctarank();
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) {
+            const int idx = (int)atomicAdd(next, 1u);
+            for (unsigned r = 0; r < (unsigned)K; ++r) {
+                uint64_t p;
+                asm volatile("mapa.u64 %0, %1, %2;" : "=l"(p) : "l"(reinterpret_cast<uint64_t>(&film_s)), "r"(r));
+                *reinterpret_cast<int*>(p) = idx;
+            }
+        }
+        cluster_barrier();
+        const int idx = film_s;
+        cluster_barrier();      // every CTA has the index before CTA 0 writes the next one
+        if (idx < 0 || idx >= nfilms) break;
+        const SweepArgs& a = films[idx];
+        switch (mode_of_film(a.f)) {
+            case MODE_INT8: sweep_body<MODE_INT8, BAR_CLUSTER>(a, (unsigned)K, rank); break;
+            case MODE_GENERIC: sweep_body<MODE_GENERIC, BAR_CLUSTER>(a, (unsigned)K, rank); break;
+            default: sweep_body<MODE_PACKED, BAR_CLUSTER>(a, (unsigned)K, rank); break;
+        }
+    }
 }
 
 __device__ __forceinline__ int mode_of_film(const DevFilm& f) {
@@ -460,6 +501,57 @@ int launch_batch_global(const SweepArgs* films, int n, unsigned* next, int threa
     if (threads % 32 || threads < 32 || threads > kBlock || units < 1) return (int)cudaErrorInvalidValue;
     k_batch_global<<<units, threads, 0, static_cast<cudaStream_t>(stream)>>>(films, n, next);
     return (int)cudaGetLastError();
+}
+
+namespace {
+template <int K>
+cudaLaunchConfig_t cluster_global_config(int threads, int units, cudaStream_t s, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(units * K);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = K;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+template <int K>
+int cluster_global_units_k(int threads, int* units) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_global_config<K>(threads, 1, nullptr, attr);
+    return (int)cudaOccupancyMaxActiveClusters(units, k_batch_cluster_global<K>, &cfg);
+}
+template <int K>
+int launch_cluster_global_k(const SweepArgs* films, int n, unsigned* next, int threads, int units, cudaStream_t s) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_global_config<K>(threads, units, s, attr);
+    return (int)cudaLaunchKernelEx(&cfg, k_batch_cluster_global<K>, films, n, next);
+}
+}  // namespace
+
+int batch_cluster_global_units(int K, int threads, int* units) {
+    switch (K) {
+        case 2: return cluster_global_units_k<2>(threads, units);
+        case 4: return cluster_global_units_k<4>(threads, units);
+        case 8: return cluster_global_units_k<8>(threads, units);
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+
+int launch_batch_cluster_global(const SweepArgs* films, int n, unsigned* next, int K, int threads, int units,
+                                void* stream) {
+    if (threads % 32 || threads < 32 || threads > kBlock || units < 1) return (int)cudaErrorInvalidValue;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    switch (K) {
+        case 2: return launch_cluster_global_k<2>(films, n, next, threads, units, s);
+        case 4: return launch_cluster_global_k<4>(films, n, next, threads, units, s);
+        case 8: return launch_cluster_global_k<8>(films, n, next, threads, units, s);
+        default: return (int)cudaErrorInvalidValue;
+    }
 }
 
 int sweep_items_per_pass(const DevFilm& f) {

@@ -353,10 +353,11 @@ class Batch:
         _check(lib.isf_batch_run_sweeps(self._h, int(max_sweeps), _stream_handle(stream)), "batch_run")
 
     def info(self) -> dict:
-        v = (C.c_int32 * 10)()
+        v = (C.c_int32 * 12)()
         _check(lib.isf_batch_info(self._h, v), "batch_info")
         keys = ("single_cta_films", "cluster_films", "global_films", "ctas", "clusters", "cluster_K",
-                "threads_single", "threads_cluster", "global_cta_films", "global_ctas")
+                "threads_single", "threads_cluster", "global_cta_films", "global_ctas",
+                "global_cluster_films", "global_clusters")
         return dict(zip(keys, list(v)))
 
     def close(self):

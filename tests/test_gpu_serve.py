@@ -28,7 +28,7 @@ def jobs():
             sched = W.schedule(float(rng.uniform(1.5, 6.0)), h, 0, 3)
         else:          # temperature scan
             sched = W.schedule(np.linspace(1.0, 9.0, 6), 0.0, 4, 4)
-        out.append({"heights": H, "layers": L, "seed": 40 + i, "schedule": sched, "packed": i == 3})
+        out.append({"heights": H, "layers": L, "seed": 40 + i, "schedule": sched, "packed": i % 3 == 0})
     return out
 
 
