@@ -213,6 +213,43 @@ const char* isf_last_error(void);
 int isf_philox_blocks(uint64_t seed, uint32_t stream, uint64_t sweep, uint32_t q0,
                       int64_t nblocks, uint32_t* host_out);
 
+/* ---- Row slabs of one film (several GPUs) ---------------------------------------------------
+ * Sec. 3 splits the film by rows between processes, each updating its own rows and exchanging
+ * the boundary rows with its neighbours.  A slab film holds whole-film rows [y0, y1) (y0 even,
+ * y1 even or the last row, at least two rows) plus one halo row pair on each side (wrapping
+ * when the film is periodic in y; none at an open edge).  Its sites carry the whole film's
+ * Philox counters, so with halos refreshed after every colour pass the slabs together follow
+ * the whole film's trajectory exactly.  It starts from the seed (random, up or down) with its
+ * halo rows already equal to the neighbours' rows.  A slab advances one colour pass at a time
+ * with isf_run_pass; isf_run_sweeps, batches, isf_write_spins and isf_save refuse it
+ * (ISF_ERR_STATE).  Its trace (isf_enable_trace / isf_read_trace) records its own rows' change
+ * of M and B since creation after each sweep; the whole film's M and B per sweep are the sums
+ * over slabs plus the sums of the slabs' creation shares (isf_slab_info), and isf_fold_series
+ * turns that series into step records.  The heights argument is the whole film's map. */
+int isf_lattice_create_slab(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, uint32_t flags,
+                            uint64_t seed, int32_t init, int32_t y0, int32_t y1, void* cuda_stream,
+                            isf_lattice** out);
+/* out6 = {y0, y1, ya (whole-film row of local row 0; may be negative or past the end when it
+ * wraps), local rows, first own colour-row, end of own colour-rows}; *halo_bytes = bytes of one
+ * colour-row over all layers (the size of an export / import buffer); out3 = {own share of M,
+ * own share of 2B (over own sites, halo neighbours included), own occupied sites} at creation. */
+int isf_slab_info(isf_lattice* lat, int32_t* out6, size_t* halo_bytes, int64_t* out3);
+/* After colour pass `colour`, copy the slab's own boundary colour-row of that colour (all layers)
+ * next to side 0 (low y) or 1 (high y) into dev_buf, or copy dev_buf into the halo row on that
+ * side.  Device buffers of isf_slab_info's halo_bytes; asynchronous on cuda_stream.
+ * Errors: ISF_ERR_ARG (no halo on that side of an open film's edge slab). */
+int isf_slab_export(isf_lattice* lat, int32_t colour, int32_t side, void* dev_buf, void* cuda_stream);
+int isf_slab_import(isf_lattice* lat, int32_t colour, int32_t side, const void* dev_buf, void* cuda_stream);
+/* One colour pass (colours 0, 1, 2, 3 in turn) of the next sweep of the schedule on the slab's
+ * own rows; after colour 3 the sweep is complete.  Asynchronous.  Errors: ISF_ERR_STATE (not a
+ * slab, no schedule, out of order), ISF_ERR_SCHEDULE (schedule done). */
+int isf_run_pass(isf_lattice* lat, int32_t colour, void* cuda_stream);
+/* Host only: step records (as isf_read_observables) of a per-sweep series M[t], B[t] of a whole
+ * film under a schedule, with n_occ occupied sites (Eq. 3 sums and the Fig. 3 estimators). */
+int isf_fold_series(int32_t nsteps, const double* T, const double* h, const int32_t* sweeps_eq,
+                    const int32_t* sweeps_meas, double J, int64_t n_occ, const int64_t* M, const int64_t* B,
+                    isf_step_obs* out);
+
 /* ---- Batched films -------------------------------------------------------------------------
  * Many independent films (each its own height map, seed and temperature / field schedule: the
  * paper's scans and loops, Sec. 3, Fig. 3, Fig. 5, for many samples at once) advanced together.

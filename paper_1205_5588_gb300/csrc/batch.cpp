@@ -239,6 +239,7 @@ int isf_batch_create(isf_batch** out) {
 int isf_batch_add(isf_batch* b, isf_lattice* L) {
     if (!b || !L) return fail(ISF_ERR_ARG, "bad arguments");
     if (!L->nsteps) return fail(ISF_ERR_STATE, "the film has no schedule");
+    if (L->f.slab) return fail(ISF_ERR_STATE, "a slab film advances by isf_run_pass, not in a batch");
     if (std::find(b->films.begin(), b->films.end(), L) != b->films.end()) return fail(ISF_ERR_ARG, "film already in the batch");
     b->films.push_back(L);
     return ISF_OK;

@@ -69,9 +69,14 @@ int recompute(isf_lattice* L, cudaStream_t s, long long red[4]) {
     return ISF_OK;
 }
 
+// A slab's place in its whole film: counter rows, row offset, own colour-rows.
+struct SlabWindow {
+    int32_t cRh, cj0, jlo, jhi;
+};
+
 int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, uint32_t flags,
                   uint64_t seed, int32_t init, void* cuda_stream, void* dev_buf, size_t dev_bytes,
-                  isf_lattice** out) {
+                  isf_lattice** out, const SlabWindow* sw = nullptr) {
     if (!out) return fail(ISF_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!heights) return fail(ISF_ERR_ARG, "heights is NULL");
@@ -119,8 +124,13 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
     f.heights = L->dev + lay.heights_off;
     fill_neighbour_classes(lay, &f);
     L->st = reinterpret_cast<FilmState*>(L->dev + lay.state_off);
+    if (sw) {
+        f.slab = 1;
+        f.cRh = sw->cRh; f.cj0 = sw->cj0; f.jlo = sw->jlo; f.jhi = sw->jhi;
+    }
     std::vector<uint32_t> items;
-    if (lay.packed && build_word_items(lay, heights, items, f.nitems, &f.item_wbits, &f.item_jbits)) {
+    if (lay.packed && build_word_items(lay, heights, items, f.nitems, &f.item_wbits, &f.item_jbits,
+                                       sw ? sw->jlo : 0, sw ? sw->jhi : lay.Rh)) {
         f.items = reinterpret_cast<const uint32_t*>(L->dev + lay.items_off);
         f.item_cap = lay.items_cap;
     }
@@ -147,6 +157,14 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
     L->n_occ = red[2];
     L->n_bonds = red[3] / 2;
     long long mb[2] = {red[0], red[1] / 2};
+    if (sw) {
+        // a slab's running M, B count its own changes from zero; its share of the whole film's
+        // M and 2B (over its own sites, neighbours in the halo included) is kept on the host
+        L->slab_m0 = red[0];
+        L->slab_b2 = red[1];
+        mb[0] = 0;
+        mb[1] = 0;
+    }
     e = cudaMemcpyAsync(&L->st->M, mb, sizeof(mb), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return bail(cuda_fail(e, "write state"));
@@ -226,6 +244,168 @@ int isf_lattice_create_in(const uint8_t* heights, int32_t rows, int32_t cols, in
     return create_common(heights, rows, cols, layers, flags, seed, init, cuda_stream, dev_buf, dev_bytes, out);
 }
 
+int isf_lattice_create_slab(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, uint32_t flags,
+                            uint64_t seed, int32_t init, int32_t y0, int32_t y1, void* cuda_stream,
+                            isf_lattice** out) {
+    if (!out) return fail(ISF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!heights) return fail(ISF_ERR_ARG, "heights is NULL");
+    Layout whole;
+    const char* why = "";
+    int rc = make_layout(rows, cols, layers, flags, &whole, &why);   // the whole film must be valid
+    if (rc) return fail(rc, why);
+    rc = check_colouring(whole, &why);
+    if (rc) return fail(rc, why);
+    const bool py = (flags & ISF_PERIODIC_Y) != 0;
+    if (y0 < 0 || y1 > rows || y1 - y0 < 2 || (y0 & 1) || ((y1 & 1) && y1 != rows))
+        return fail(ISF_ERR_ARG, "slab rows [y0, y1): 0 <= y0 < y1 <= rows, y0 even, y1 even or rows, at least 2 rows");
+    // one halo row pair on each side (whole-film rows wrap when periodic in y)
+    const int32_t ya = (y0 > 0 || py) ? y0 - 2 : y0;
+    const int32_t yb = (y1 < rows || py) ? y1 + 2 : y1;
+    const int32_t lr = yb - ya;
+    std::vector<uint8_t> local((size_t)lr * cols);
+    for (int32_t r = 0; r < lr; ++r) {
+        const int32_t y = ((ya + r) % rows + rows) % rows;
+        std::memcpy(&local[(size_t)r * cols], heights + (size_t)y * cols, (size_t)cols);
+    }
+    SlabWindow sw;
+    sw.cRh = whole.Rh;
+    sw.cj0 = ya / 2;                              // ya is even (possibly -2)
+    sw.jlo = (y0 - ya) / 2;
+    sw.jhi = (yb == y1) ? (lr + 1) / 2 : (y1 - ya) / 2;
+    rc = create_common(local.data(), lr, cols, layers, flags & ~(uint32_t)ISF_PERIODIC_Y, seed, init, cuda_stream,
+                       nullptr, 0, out, &sw);
+    if (rc) return rc;
+    (*out)->slab_y0 = y0; (*out)->slab_y1 = y1; (*out)->slab_ya = ya; (*out)->slab_rows = rows;
+    return ISF_OK;
+}
+
+int isf_slab_info(isf_lattice* L, int32_t* out6, size_t* halo_bytes, int64_t* out3) {
+    if (!L || !out6 || !halo_bytes || !out3) return fail(ISF_ERR_ARG, "bad arguments");
+    if (!L->f.slab) return fail(ISF_ERR_STATE, "not a slab film");
+    const int32_t v[6] = {L->slab_y0, L->slab_y1, L->slab_ya, L->lay.R, L->f.jlo, L->f.jhi};
+    std::memcpy(out6, v, sizeof v);
+    *halo_bytes = (size_t)L->lay.L * (L->lay.packed ? (size_t)L->lay.Wp * 4 : (size_t)L->lay.P);
+    out3[0] = L->slab_m0;
+    out3[1] = L->slab_b2;
+    out3[2] = L->n_occ;
+    return ISF_OK;
+}
+
+// Device address and pitch of colour-row j (local) of colour c, layer 0; layers follow at the
+// returned pitch.  int8: the whole padded row; packed: the spin bit-plane row.
+static void slab_row(const isf_lattice* L, int32_t c, int32_t j, uint8_t** p, size_t* width, size_t* pitch) {
+    const Layout& lay = L->lay;
+    if (lay.packed) {
+        *p = reinterpret_cast<uint8_t*>(L->f.sp + (int64_t)c * lay.csw + lay.lsw + (int64_t)(j + 1) * lay.Wp);
+        *width = (size_t)lay.Wp * 4;
+        *pitch = (size_t)lay.lsw * 4;
+    } else {
+        *p = L->f.s8 + (int64_t)c * lay.cs8 + lay.ls8 + (int64_t)(j + 1) * lay.P;
+        *width = (size_t)lay.P;
+        *pitch = (size_t)lay.ls8;
+    }
+}
+
+int isf_slab_export(isf_lattice* L, int32_t colour, int32_t side, void* dev_buf, void* cuda_stream) {
+    if (!L || !dev_buf || colour < 0 || colour > 3 || (side != 0 && side != 1)) return fail(ISF_ERR_ARG, "bad arguments");
+    if (!L->f.slab) return fail(ISF_ERR_STATE, "not a slab film");
+    uint8_t* p;
+    size_t w, pitch;
+    slab_row(L, colour, side == 0 ? L->f.jlo : L->f.jhi - 1, &p, &w, &pitch);
+    CUDA_TRY(cudaSetDevice(L->device), "cudaSetDevice");
+    CUDA_TRY(cudaMemcpy2DAsync(dev_buf, w, p, pitch, w, (size_t)L->lay.L, cudaMemcpyDeviceToDevice,
+                               static_cast<cudaStream_t>(cuda_stream)), "export halo rows");
+    return ISF_OK;
+}
+
+int isf_slab_import(isf_lattice* L, int32_t colour, int32_t side, const void* dev_buf, void* cuda_stream) {
+    if (!L || !dev_buf || colour < 0 || colour > 3 || (side != 0 && side != 1)) return fail(ISF_ERR_ARG, "bad arguments");
+    if (!L->f.slab) return fail(ISF_ERR_STATE, "not a slab film");
+    const int32_t j = side == 0 ? L->f.jlo - 1 : L->f.jhi;
+    if (j < 0 || j >= L->lay.Rh) return fail(ISF_ERR_ARG, "this slab has no halo on that side (edge of an open film)");
+    uint8_t* p;
+    size_t w, pitch;
+    slab_row(L, colour, j, &p, &w, &pitch);
+    CUDA_TRY(cudaSetDevice(L->device), "cudaSetDevice");
+    CUDA_TRY(cudaMemcpy2DAsync(p, pitch, dev_buf, w, w, (size_t)L->lay.L, cudaMemcpyDeviceToDevice,
+                               static_cast<cudaStream_t>(cuda_stream)), "import halo rows");
+    return ISF_OK;
+}
+
+int isf_run_pass(isf_lattice* L, int32_t colour, void* cuda_stream) {
+    if (!L || colour < 0 || colour > 3) return fail(ISF_ERR_ARG, "bad arguments");
+    if (!L->f.slab) return fail(ISF_ERR_STATE, "isf_run_pass is for slab films (whole films: isf_run_sweeps)");
+    if (!L->nsteps) return fail(ISF_ERR_STATE, "no schedule set");
+    if (colour != L->pass_next) return fail(ISF_ERR_STATE, "colour passes run in the order 0, 1, 2, 3");
+    if (sweeps_remaining(L) < 1) return fail(ISF_ERR_SCHEDULE, "past the end of the schedule");
+    CUDA_TRY(cudaSetDevice(L->device), "cudaSetDevice");
+    SweepArgs a = sweep_args(L, 1);
+    a.pass_plus1 = colour + 1;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int threads = L->threads ? std::min(L->threads, 512) : 256;
+    int maxc = 0;
+    int e = sweep_max_ctas_for(L->f, threads, &maxc);
+    if (e) return cuda_fail((cudaError_t)e, "occupancy query");
+    if (maxc < 1) return fail(ISF_ERR_CUDA, "sweep kernel cannot be resident with this block size");
+    int ctas = L->ctas;
+    if (ctas <= 0) ctas = (int)std::max<int64_t>(1, (sweep_items_per_pass(L->f) + threads - 1) / threads);
+    if (ctas > maxc) ctas = maxc;
+    e = launch_sweeps(a, ctas, threads, s);
+    if (e) return cuda_fail((cudaError_t)e, "sweep kernel launch");
+    L->last_path = ISF_PATH_GLOBAL; L->last_ctas = ctas; L->last_threads = threads;
+    L->last_sites = L->lay.packed ? 32 : 16;
+    L->last = s;
+    if (colour == 3) {
+        advance_cursor(L, 1);
+        L->pass_next = 0;
+    } else {
+        L->pass_next = colour + 1;
+    }
+    return ISF_OK;
+}
+
+int isf_fold_series(int32_t nsteps, const double* T, const double* h, const int32_t* sweeps_eq,
+                    const int32_t* sweeps_meas, double J, int64_t n_occ, const int64_t* M, const int64_t* B,
+                    isf_step_obs* out) {
+    if (nsteps < 1 || !T || !h || !sweeps_eq || !sweeps_meas || !M || !B || !out) return fail(ISF_ERR_ARG, "bad arguments");
+    int64_t t = 0;
+    for (int32_t k = 0; k < nsteps; ++k) {
+        if (sweeps_eq[k] < 0 || sweeps_meas[k] < 0 || sweeps_eq[k] + (int64_t)sweeps_meas[k] < 1)
+            return fail(ISF_ERR_SCHEDULE, "every step needs at least one sweep");
+        StepRec r{};
+        __int128 m2 = 0, b2 = 0, mb = 0;
+        t += sweeps_eq[k];
+        for (int32_t i = 0; i < sweeps_meas[k]; ++i, ++t) {
+            const long long m = M[t], b = B[t];
+            r.n_meas += 1;
+            r.sumM += m;
+            r.sumAbsM += m < 0 ? -m : m;
+            r.sumB += b;
+            m2 += (__int128)m * m;
+            b2 += (__int128)b * b;
+            mb += (__int128)m * b;
+        }
+        r.M_last = M[t - 1];
+        r.B_last = B[t - 1];
+        const unsigned __int128 um2 = (unsigned __int128)m2, ub2 = (unsigned __int128)b2, umb = (unsigned __int128)mb;
+        r.sumM2[0] = (unsigned long long)um2; r.sumM2[1] = (unsigned long long)(um2 >> 64);
+        r.sumB2[0] = (unsigned long long)ub2; r.sumB2[1] = (unsigned long long)(ub2 >> 64);
+        r.sumMB[0] = (unsigned long long)umb; r.sumMB[1] = (unsigned long long)(umb >> 64);
+        isf_step_obs& o = out[k];
+        o.T = T[k]; o.h = h[k];
+        o.M_last = r.M_last; o.B_last = r.B_last; o.n_meas = r.n_meas;
+        o.sumM = r.sumM; o.sumAbsM = r.sumAbsM; o.sumB = r.sumB;
+        std::memcpy(o.sumM2, r.sumM2, sizeof o.sumM2);
+        std::memcpy(o.sumB2, r.sumB2, sizeof o.sumB2);
+        std::memcpy(o.sumMB, r.sumMB, sizeof o.sumMB);
+        double d[6];
+        derive_record(r, T[k], h[k], J, n_occ, d);
+        o.m = d[0]; o.abs_m = d[1]; o.e = d[2]; o.chi = d[3]; o.chi_abs = d[4]; o.C = d[5];
+    }
+    return ISF_OK;
+}
+
 void isf_lattice_destroy(isf_lattice* L) {
     if (!L) return;
     cudaSetDevice(L->device);
@@ -291,6 +471,7 @@ int isf_set_schedule(isf_lattice* L, int32_t nsteps, const double* T, const doub
 int isf_run_sweeps(isf_lattice* L, int64_t nsweeps, void* cuda_stream) {
     if (!L) return fail(ISF_ERR_ARG, "lattice is NULL");
     if (!L->nsteps) return fail(ISF_ERR_STATE, "no schedule set");
+    if (L->f.slab) return fail(ISF_ERR_STATE, "a slab film advances by isf_run_pass, with halo exchanges between passes");
     const int64_t remaining = sweeps_remaining(L);
     if (nsweeps == -1) nsweeps = remaining;
     if (nsweeps < 0) return fail(ISF_ERR_ARG, "nsweeps must be >= 0 or -1");
@@ -426,6 +607,7 @@ int isf_lattice_stats(isf_lattice* L, double* p, double* zbar, double* p_c) {
 
 int isf_write_spins(isf_lattice* L, const int8_t* host_in, int64_t sweep) {
     if (!L || !host_in || sweep < 0) return fail(ISF_ERR_ARG, "bad arguments");
+    if (L->f.slab) return fail(ISF_ERR_STATE, "a slab film's spins come from its seed and the halo exchanges");
     const int R = L->lay.R, C = L->lay.C, Lz = L->lay.L;
     for (int z = 0; z < Lz; ++z)
         for (int y = 0; y < R; ++y)
@@ -553,6 +735,7 @@ int isf_set_path(isf_lattice* L, int32_t path) {
 
 int isf_save(isf_lattice* L, const char* path) {
     if (!L || !path) return fail(ISF_ERR_ARG, "bad arguments");
+    if (L->f.slab) return fail(ISF_ERR_STATE, "slab films are saved as the whole film they belong to");
     const size_t n = (size_t)L->lay.R * L->lay.C * L->lay.L;
     std::vector<int8_t> spins(n);
     int rc = isf_read_spins(L, spins.data());

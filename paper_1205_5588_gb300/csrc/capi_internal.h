@@ -47,6 +47,11 @@ struct isf_lattice {
     int32_t path = ISF_PATH_AUTO;
     int32_t last_path = 0, last_ctas = 0, last_threads = 0;   // shape of the last sweep launch
     int32_t last_sites = 0;
+    // row slab of a larger film (f.slab): whole-film rows [y0, y1) are this film's own rows,
+    // local row 0 is whole-film row ya; the next colour pass isf_run_pass expects
+    int32_t slab_y0 = 0, slab_y1 = 0, slab_ya = 0, slab_rows = 0;
+    int32_t pass_next = 0;
+    int64_t slab_m0 = 0, slab_b2 = 0;   // own share of the whole film's M and 2B at creation
     cudaStream_t last = nullptr;
 };
 

@@ -32,6 +32,11 @@ __device__ __forceinline__ uint32_t word_of(const uint4& v, int b) {
 
 // Philox counter word of the 4-site block holding column i of row (c, z, j).
 __device__ __forceinline__ uint32_t block_counter(const DevFilm& f, int c, int z, int j, int i) {
+    if (f.slab) {               // a slab's rows carry the whole film's counters
+        int jg = (j + f.cj0) % f.cRh;
+        if (jg < 0) jg += f.cRh;
+        return (uint32_t)((((int64_t)c * f.L + z) * f.cRh + jg) * f.Qw + (i >> 2));
+    }
     return (uint32_t)((((int64_t)c * f.L + z) * f.Rh + j) * f.Qw + (i >> 2));
 }
 

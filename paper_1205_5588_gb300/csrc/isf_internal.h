@@ -68,7 +68,11 @@ struct DevFilm {
     int32_t nitems[4];
     int32_t item_wbits, item_jbits;
     int32_t narrow;               // packed: 1 if every neighbour offset and index fits 32 bits
-    int32_t pad2_;
+    // row slab of a larger film (0: a whole film).  Local colour-row j is row (j + cj0) mod cRh
+    // of the whole film (its Philox counters are the whole film's); the sweep kernels update
+    // rows [jlo, jhi) only, the others are halo copies of the neighbouring slabs' rows.
+    int32_t slab;
+    int32_t cRh, cj0, jlo, jhi;
     const uint8_t* heights;       // [y][x]
     NbrClass nb[4][2];            // [colour][layer parity]
 };
@@ -107,6 +111,7 @@ struct SweepArgs {
     int32_t k0, pos0;             // schedule cursor at launch: step, sweeps done in that step
     int32_t nsteps;
     int32_t use_gate;             // any step with a gate threshold != always
+    int32_t pass_plus1;           // 0: whole sweeps; c + 1: colour c of one sweep only (slab mode)
 };
 
 // Host-side layout computation (lattice.cpp).
@@ -129,7 +134,7 @@ int check_colouring(const Layout& lay, const char** why);
 // entries (colour c's list at c * items_cap, n[c] of them); false when an entry's fields do not
 // fit 32 bits (the kernels then walk every word).
 bool build_word_items(const Layout& lay, const uint8_t* heights, std::vector<uint32_t>& out, int32_t n[4],
-                      int32_t* wbits, int32_t* jbits);
+                      int32_t* wbits, int32_t* jbits, int32_t jlo, int32_t jhi);   // rows [jlo, jhi) only
 void fill_neighbour_classes(const Layout& lay, DevFilm* f);
 
 // Host threshold table (schedule.cpp): thr[n+12][s'] for one step, plus the gate slot.

@@ -106,7 +106,8 @@ __global__ void k_init_packed(DevFilm f, int init, const int8_t* src) {
     }
 }
 
-// M = sum S, 2B = sum S * (neighbour sum), occupied sites, 2 * occupied bonds -> st->red[0..3].
+// M = sum S, 2B = sum S * (neighbour sum), occupied sites, 2 * occupied bonds -> st->red[0..3]
+// (a slab: over its own rows, with its halo rows as neighbours).
 __global__ void k_recompute(DevFilm f, FilmState* st) {
     const int64_t total = (int64_t)f.L * f.R * f.C;
     long long m = 0, b2 = 0, occ = 0, nb2 = 0;
@@ -115,6 +116,7 @@ __global__ void k_recompute(DevFilm f, FilmState* st) {
         const int x = (int)(t % f.C);
         const int64_t r = t / f.C;
         const int y = (int)(r % f.R), z = (int)(r / f.R);
+        if (f.slab && (y < 2 * f.jlo || y >= 2 * f.jhi)) continue;   // a slab counts its own rows
         if (!site_occupied(f, x, y, z)) continue;
         const int s = site_spin(f, x, y, z);
         int n = 0, no = 0;

@@ -304,10 +304,11 @@ __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned lo
         }
         return;
     }
+    const int j0 = f.slab ? f.jlo : 0;
     for (int it = first_item(G, cta); it < items; it += stride, w.next()) {
-        if (MODE == MODE_INT8) chunk_int8<GATE>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
-        else if (MODE == MODE_GENERIC) block_generic<GATE>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
-        else word_packed<GATE, false>(f, c, w.z, w.jr, w.ck, sweep, tab, gthr, dM, dB);
+        if (MODE == MODE_INT8) chunk_int8<GATE>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB);
+        else if (MODE == MODE_GENERIC) block_generic<GATE>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB);
+        else word_packed<GATE, false>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB);
     }
 }
 
@@ -327,9 +328,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
     FilmState* st = a.st;
     unsigned target = 0;
     const int per_row = MODE == MODE_INT8 ? f.nck : (MODE == MODE_GENERIC ? f.Qw : f.nw);
-    const int items = f.L * f.Rh * per_row;
+    const int nrows = f.slab ? f.jhi - f.jlo : f.Rh;        // rows this film updates
+    const int items = f.L * nrows * per_row;
     ItemWalk walk0;
-    walk0.init(first_item(G, cta), (int)G * blockDim.x, per_row, f.Rh);
+    walk0.init(first_item(G, cta), (int)G * blockDim.x, per_row, nrows > 0 ? nrows : 1);
+    // colours of this launch: all four, or one colour pass of one sweep
+    const int c_begin = a.pass_plus1 ? a.pass_plus1 - 1 : 0, c_end = a.pass_plus1 ? a.pass_plus1 : 4;
     int k = a.k0, pos = a.pos0;
     const bool folder = cta == 0 && threadIdx.x == 0;
     __shared__ RunState rs;     // touched by the folding thread only
@@ -350,10 +354,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
         const unsigned long long sweep = (unsigned long long)(a.sweep0 + t + 1);
         const uint32_t gthr = gate_s;
         int dM = 0, dB = 0;
-        for (int c = 0; c < 4; ++c) {
+        for (int c = c_begin; c < c_end; ++c) {
             if (a.use_gate) colour_pass<MODE, true>(f, c, sweep, tab, gthr, items, walk0, G, cta, dM, dB);
             else colour_pass<MODE, false>(f, c, sweep, tab, gthr, items, walk0, G, cta, dM, dB);
-            if (c == 3) {
+            if (c == c_end - 1) {
                 long long sM = dM, sB = dB;
                 block_sum2(sM, sB, red);
                 if (threadIdx.x == 0 && (sM | sB)) {
@@ -369,7 +373,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
                 return;
             }
         }
-        if (folder) {
+        if (folder && c_end == 4) {
             unsigned long long* acc = reinterpret_cast<unsigned long long*>(&st->acc[sweep & 1][0]);
             const long long sM = (long long)atomicExch(acc, 0ull);
             const long long sB = (long long)atomicExch(acc + 1, 0ull);

@@ -83,7 +83,7 @@ static int bits_for(int64_t n) {
 }
 
 bool build_word_items(const Layout& lay, const uint8_t* heights, std::vector<uint32_t>& out, int32_t n[4],
-                      int32_t* wbits, int32_t* jbits) {
+                      int32_t* wbits, int32_t* jbits, int32_t jlo, int32_t jhi) {
     const int wb = bits_for(lay.nw), jb = bits_for(lay.Rh), zb = bits_for(lay.L);
     if (wb + jb + zb > 32) return false;
     out.assign((size_t)4 * (size_t)lay.items_cap, 0u);
@@ -100,7 +100,7 @@ bool build_word_items(const Layout& lay, const uint8_t* heights, std::vector<uin
         int64_t k = 0;
         for (int z = 0; z < lay.L; ++z) {
             const int zp = z & 1, px = (c & 1) ^ zp, py = ((c >> 1) & 1) ^ zp;
-            for (int j = 0; j < lay.Rh; ++j) {
+            for (int j = std::max(jlo, 0); j < std::min(jhi, lay.Rh); ++j) {
                 const int y = 2 * j + py;
                 if (y >= lay.R) continue;
                 for (int w = 0; w < lay.nw; ++w)

@@ -72,6 +72,14 @@ def _declare(lib):
         "isf_lattice_stats": (C.c_int, [vp, dp, dp, dp]),
         "isf_launch_info": (C.c_int, [vp, i32p, i32p, i32p]),
         "isf_set_item_sites": (C.c_int, [vp, C.c_int32]),
+        "isf_lattice_create_slab": (C.c_int, [u8p, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, C.c_uint64,
+                                              C.c_int32, C.c_int32, C.c_int32, vp, C.POINTER(vp)]),
+        "isf_slab_info": (C.c_int, [vp, i32p, C.POINTER(C.c_size_t), i64p]),
+        "isf_slab_export": (C.c_int, [vp, C.c_int32, C.c_int32, vp, vp]),
+        "isf_slab_import": (C.c_int, [vp, C.c_int32, C.c_int32, vp, vp]),
+        "isf_run_pass": (C.c_int, [vp, C.c_int32, vp]),
+        "isf_fold_series": (C.c_int, [C.c_int32, dp, dp, i32p, i32p, C.c_double, C.c_int64, i64p, i64p,
+                                      C.POINTER(StepObs)]),
         "isf_launch_item_sites": (C.c_int, [vp, i32p]),
         "isf_save": (C.c_int, [vp, C.c_char_p]),
         "isf_load": (C.c_int, [C.c_char_p, vp, C.POINTER(vp)]),
@@ -155,6 +163,25 @@ def lattice_bytes(rows, cols, layers, flags) -> int:
     return int(lib.isf_lattice_bytes(rows, cols, layers, flags))
 
 
+def fold_series(T, h, sweeps_eq, sweeps_meas, n_occ, M, B, J=1.0) -> list[dict]:
+    """Step records of a whole film's per-sweep M, B series under a schedule (isf_fold_series;
+    host only)."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    eq = np.ascontiguousarray(sweeps_eq, dtype=np.int32)
+    me = np.ascontiguousarray(sweeps_meas, dtype=np.int32)
+    M = np.ascontiguousarray(M, dtype=np.int64)
+    B = np.ascontiguousarray(B, dtype=np.int64)
+    n = len(T)
+    if not (len(h) == len(eq) == len(me) == n) or len(M) != len(B) or len(M) < int(eq.sum() + me.sum()):
+        raise ValueError("schedule arrays differ in length, or the series is shorter than the schedule")
+    out = (StepObs * n)()
+    _check(lib.isf_fold_series(n, _ptr(T, C.c_double), _ptr(h, C.c_double), _ptr(eq, C.c_int32),
+                               _ptr(me, C.c_int32), float(J), int(n_occ), _ptr(M, C.c_int64), _ptr(B, C.c_int64),
+                               out), "fold_series")
+    return obs_to_dicts(out)
+
+
 class Lattice:
     """One film on the current CUDA device (isf_lattice_create / isf_lattice_create_in)."""
 
@@ -188,6 +215,41 @@ class Lattice:
                                         int(seed), initv, s, C.byref(h))
         _check(rc, "lattice_create")
         self._h = h
+
+    @classmethod
+    def slab(cls, heights, layers, y0, y1, *, periodic_x=False, periodic_y=False, packed=False, seed=1,
+             init="random", stream=None):
+        """Rows [y0, y1) of the whole film `heights` (isf_lattice_create_slab)."""
+        H = np.ascontiguousarray(heights, dtype=np.uint8)
+        flags = flags_of(periodic_x, periodic_y, False, packed)
+        h = C.c_void_p()
+        initv = INIT[init] if isinstance(init, str) else int(init)
+        _check(lib.isf_lattice_create_slab(_ptr(H, C.c_uint8), H.shape[0], H.shape[1], int(layers), flags, int(seed),
+                                           initv, int(y0), int(y1), _stream_handle(stream), C.byref(h)),
+               "lattice_create_slab")
+        self = cls._wrap(h, None, H.shape[1], int(layers), flags, H)
+        info = self.slab_info()
+        self.rows = info["local_rows"]
+        return self
+
+    def slab_info(self) -> dict:
+        v = (C.c_int32 * 6)()
+        nb = C.c_size_t()
+        w = (C.c_int64 * 3)()
+        _check(lib.isf_slab_info(self._h, v, C.byref(nb), w), "slab_info")
+        return {"y0": v[0], "y1": v[1], "ya": v[2], "local_rows": v[3], "jlo": v[4], "jhi": v[5],
+                "halo_bytes": nb.value, "M0": w[0], "B2_0": w[1], "n_occ": w[2]}
+
+    def slab_export(self, colour, side, dev_ptr, stream=None):
+        _check(lib.isf_slab_export(self._h, int(colour), int(side), C.c_void_p(dev_ptr), _stream_handle(stream)),
+               "slab_export")
+
+    def slab_import(self, colour, side, dev_ptr, stream=None):
+        _check(lib.isf_slab_import(self._h, int(colour), int(side), C.c_void_p(dev_ptr), _stream_handle(stream)),
+               "slab_import")
+
+    def run_pass(self, colour, stream=None):
+        _check(lib.isf_run_pass(self._h, int(colour), _stream_handle(stream)), "run_pass")
 
     @classmethod
     def _wrap(cls, handle, rows, cols, layers, flags, heights):
