@@ -389,12 +389,12 @@ def measure_served(I, rate=200.0, duration=5.0, seed=5, pool=24, budget_gb=40.0,
 # recorded value (None: not captured for the current sources).
 NCU_TRAFFIC = {
     "fractal256": {"sources": ["kernels_resident.cu", "sweep_core.cuh", "device_common.cuh"],
-                   "sources_sha256": "8aafcffba79d140da5a89965bd1e63e4de8f1808cd93f9adf4dc5f7bce8eac91",
-                   "bytes_per_launch": 1.25e6},
+                   "sources_sha256": "6b514be48eed988dfdd42d1ca2a6a2f2edd023275d287075041396a3bee0dfeb",
+                   "bytes_per_launch": 1457408.0},
     "fractal2048": {"sources": ["kernels_sweep.cu", "sweep_core.cuh", "device_common.cuh"],
-                    "sources_sha256": None, "bytes_per_launch": None},
+                    "sources_sha256": "249dca98ef7013ac3a07be28cbeb52d6ac099df0018ac52658548b0d050e7d21",
+                    "bytes_per_launch": 11528448.0 + 2456576.0},
 }
-
 
 def kernel_sources_sha256(names) -> str:
     import hashlib
