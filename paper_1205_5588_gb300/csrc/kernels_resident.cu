@@ -134,6 +134,33 @@ __device__ __forceinline__ uint2 neighbour_sum8_sc(const uint32_t* nb, int sgn) 
     return acc;
 }
 
+// The 15 loads of a 16-site chunk's neighbour sum (12 rows, and the next or previous word of the
+// three shifted ones), issued together; neighbour_sum16_from adds them up.
+template <bool CLUSTER>
+__device__ __forceinline__ void neighbour_loads16(const uint32_t* nb, int sgn, uint4 v[12], uint32_t e[3]) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = lds16<CLUSTER>(nb[k]);
+#pragma unroll
+    for (int k = 9; k < 12; ++k) e[k - 9] = lds4<CLUSTER>(sgn < 0 ? nb[k] - 4 : nb[k] + 16);
+}
+__device__ __forceinline__ uint4 neighbour_sum16_from(const uint4 v[12], const uint32_t e[3], int sgn) {
+    uint4 acc = v[0];
+#pragma unroll
+    for (int k = 1; k < 9; ++k) add4(acc, v[k]);
+    if (sgn < 0) {
+#pragma unroll
+        for (int k = 9; k < 12; ++k)
+            add4(acc, make_uint4(__funnelshift_l(e[k - 9], v[k].x, 8), __funnelshift_l(v[k].x, v[k].y, 8),
+                                 __funnelshift_l(v[k].y, v[k].z, 8), __funnelshift_l(v[k].z, v[k].w, 8)));
+    } else {
+#pragma unroll
+        for (int k = 9; k < 12; ++k)
+            add4(acc, make_uint4(__funnelshift_r(v[k].x, v[k].y, 8), __funnelshift_r(v[k].y, v[k].z, 8),
+                                 __funnelshift_r(v[k].z, v[k].w, 8), __funnelshift_r(v[k].w, e[k - 9], 8)));
+    }
+    return acc;
+}
+
 // Neighbour sum of a 16-site chunk from shared::cluster addresses (see neighbour_sum16).
 template <bool CLUSTER>
 __device__ __forceinline__ uint4 neighbour_sum16_sc(const uint32_t* nb, int sgn) {
@@ -323,17 +350,28 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
                                           pb.z + co, pb.w + co, pc.x + co, pc.y + co, pc.z + co, pc.w + co};
                 const uint32_t q0 = block_counter(f, c, z, j0 + jl, W * ck);
                 const int sgn = f.nb[c][z & 1].sgn;
+                uint32_t fm[NW];
+                uint32_t any;
                 if constexpr (NW == 4) {
-                    const uint4 a4 = neighbour_sum16_sc<CLUSTER>(nbp, sgn);
+                    // loads first, then the chunk's four Philox blocks while they are in flight
+                    // (every pass starts all warps at once, so nothing else would fill that wait)
+                    uint4 nv[12];
+                    uint32_t ne[3];
+                    neighbour_loads16<CLUSTER>(nbp, sgn, nv, ne);
+                    uint4 u[4];
+                    philox10_xn<4>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u);
+                    const uint4 a4 = neighbour_sum16_from(nv, ne, sgn);
                     Aw[0] = a4.x; Aw[1] = a4.y; Aw[2] = a4.z; Aw[3] = a4.w;
+                    any = s.use_gate
+                        ? decide16<true, PX, 4, true>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB, u)
+                        : decide16<false, PX, 4, true>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB, u);
                 } else {
                     const uint2 a2 = neighbour_sum8_sc<CLUSTER>(nbp, sgn);
                     Aw[0] = a2.x; Aw[1] = a2.y;
+                    any = s.use_gate
+                        ? decide16<true, PX, NW>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB)
+                        : decide16<false, PX, NW>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB);
                 }
-                uint32_t fm[NW];
-                const uint32_t any = s.use_gate
-                    ? decide16<true, PX, NW>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB)
-                    : decide16<false, PX, NW>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB);
                 if (any) {
                     if (!PX) {
                         if constexpr (NW == 4)

@@ -195,6 +195,11 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
     const int64_t base = addrw(f, c, z, j, w);
     uint32_t S, O, up[12], V[4];
     packed_loads<NARROW>(f, nc, base, S, O, up, V);
+    // the first half's four Philox blocks do not depend on the loads: drawn while they are in
+    // flight (every pass starts all warps together, so nothing else would fill that wait)
+    const uint32_t q0 = block_counter(f, c, z, j, 32 * w);
+    uint4 u_first[4];
+    philox10_xn<4>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u_first);
     if (!O) return;             // no occupied site in the word (tested after the loads are issued)
     // X = n + 12 = 2 * (#up) + (#vacant) over the 12 neighbours, 5 bit-planes
     uint32_t U0, U1, U2, U3;
@@ -227,7 +232,6 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
         P[p + 1] ^= t;
         P[p] ^= t << 1;
     }
-    const uint32_t q0 = block_counter(f, c, z, j, 32 * w);
     uint32_t F = 0;
     // two halves of 16 lanes (4 Philox blocks each): all 16 lookups first, then the half's four
     // blocks interleaved when any of its lanes needs a word
@@ -242,13 +246,18 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
             for (int b = 0; b < 4; ++b) {
                 const uint32_t t = tab[(P[4 * (v & 1) + b] >> (8 * (v >> 1))) & 0x7Fu];
                 thr[4 * vv + b] = t;
-                need |= needs_word(t);
+                if (g) need |= needs_word(t);
             }
         }
         uint4 u[4];
+        if (g == 0) {
 #pragma unroll
-        for (int vv = 0; vv < 4; ++vv) u[vv] = make_uint4(0, 0, 0, 0);
-        if (need) philox10_xn<4>(q0 + 4 * g, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u);
+            for (int vv = 0; vv < 4; ++vv) u[vv] = u_first[vv];
+        } else {
+#pragma unroll
+            for (int vv = 0; vv < 4; ++vv) u[vv] = make_uint4(0, 0, 0, 0);
+            if (need) philox10_xn<4>(q0 + 4, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u);
+        }
 #pragma unroll
         for (int vv = 0; vv < 4; ++vv) {
             uint32_t lanes = 0;

@@ -95,11 +95,13 @@ __device__ __forceinline__ void philox10_xn(uint32_t q0, uint32_t s_lo, uint32_t
 // result).  The flips come back as a byte mask per word (0 <-> 2 is XOR 2); dM and dB from
 // popcounts of that mask and a multiply-add of the masked neighbour sums.  PX: lanes past the
 // row end (column Ch on) are masked.  Returns the OR of the four masks.
-template <bool GATE, bool PX, int NW = 4>
+// U_IN: the chunk's NW Philox blocks are already in u_in (drawn before the neighbour sum was
+// available, to fill the wait for its loads); else they are drawn here only if a lane needs one.
+template <bool GATE, bool PX, int NW = 4, bool U_IN = false>
 __device__ __forceinline__ uint32_t decide16(const uint32_t Sw[NW], const uint32_t Aw[NW], uint32_t q0,
                                              unsigned long long sweep, const uint32_t* tab, uint32_t gthr,
                                              uint32_t key0, uint32_t key1, int i0, int Ch, uint32_t fm[NW],
-                                             int& dM, int& dB) {
+                                             int& dM, int& dB, const uint4* u_in = nullptr) {
     uint32_t thr[4 * NW];
     bool need = false;
 #pragma unroll
@@ -110,13 +112,18 @@ __device__ __forceinline__ uint32_t decide16(const uint32_t Sw[NW], const uint32
             uint32_t t = tab[(iw >> (8 * b)) & 0xFFu];
             if (PX && i0 + 4 * v + b >= Ch) t = 0u;
             thr[4 * v + b] = t;
-            need |= needs_word(t);
+            if (!U_IN) need |= needs_word(t);
         }
     }
     uint4 u[NW];
+    if (U_IN) {
 #pragma unroll
-    for (int v = 0; v < NW; ++v) u[v] = make_uint4(0, 0, 0, 0);
-    if (need) philox10_xn<NW>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, key0, key1, u);
+        for (int v = 0; v < NW; ++v) u[v] = u_in[v];
+    } else {
+#pragma unroll
+        for (int v = 0; v < NW; ++v) u[v] = make_uint4(0, 0, 0, 0);
+        if (need) philox10_xn<NW>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, key0, key1, u);
+    }
     uint32_t any = 0;
 #pragma unroll
     for (int v = 0; v < NW; ++v) {
@@ -143,32 +150,6 @@ __device__ __forceinline__ uint32_t decide16(const uint32_t Sw[NW], const uint32
     return any;
 }
 
-// Sum of the 12 neighbour words of a 16-site chunk (k < 9 unshifted; k = 9..11 shifted by sgn
-// columns and completed from the word before / after), from generic pointers.
-__device__ __forceinline__ uint4 neighbour_sum16(const uint8_t* const* nb, int sgn) {
-    uint4 acc = ld16(nb[0]);
-#pragma unroll
-    for (int k = 1; k < 9; ++k) add4(acc, ld16(nb[k]));
-    if (sgn < 0) {
-#pragma unroll
-        for (int k = 9; k < 12; ++k) {
-            const uint4 v = ld16(nb[k]);
-            const uint32_t e = ld4(nb[k] - 4);
-            add4(acc, make_uint4(__funnelshift_l(e, v.x, 8), __funnelshift_l(v.x, v.y, 8),
-                                 __funnelshift_l(v.y, v.z, 8), __funnelshift_l(v.z, v.w, 8)));
-        }
-    } else {
-#pragma unroll
-        for (int k = 9; k < 12; ++k) {
-            const uint4 v = ld16(nb[k]);
-            const uint32_t e = ld4(nb[k] + 16);
-            add4(acc, make_uint4(__funnelshift_r(v.x, v.y, 8), __funnelshift_r(v.y, v.z, 8),
-                                 __funnelshift_r(v.z, v.w, 8), __funnelshift_r(v.w, e, 8)));
-        }
-    }
-    return acc;
-}
-
 // One 16-site chunk, neighbours through generic pointers (global-memory kernel).
 template <bool GATE>
 __device__ __forceinline__ void update_chunk16(uint8_t* own, const uint8_t* const* nb, int sgn, uint32_t q0,
@@ -176,11 +157,33 @@ __device__ __forceinline__ void update_chunk16(uint8_t* own, const uint8_t* cons
                                                uint32_t key0, uint32_t key1, int i0, int Ch,
                                                int& dM, int& dB) {
     const uint4 S = ld16(own);
-    const uint4 acc = neighbour_sum16(nb, sgn);
+    // the 15 neighbour loads first, then the chunk's four Philox blocks while they are in flight
+    uint4 v[12];
+    uint32_t e[3];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = ld16(nb[k]);
+#pragma unroll
+    for (int k = 9; k < 12; ++k) e[k - 9] = ld4(sgn < 0 ? nb[k] - 4 : nb[k] + 16);
+    uint4 u[4];
+    philox10_xn<4>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, key0, key1, u);
+    uint4 acc = v[0];
+#pragma unroll
+    for (int k = 1; k < 9; ++k) add4(acc, v[k]);
+    if (sgn < 0) {
+#pragma unroll
+        for (int k = 9; k < 12; ++k)
+            add4(acc, make_uint4(__funnelshift_l(e[k - 9], v[k].x, 8), __funnelshift_l(v[k].x, v[k].y, 8),
+                                 __funnelshift_l(v[k].y, v[k].z, 8), __funnelshift_l(v[k].z, v[k].w, 8)));
+    } else {
+#pragma unroll
+        for (int k = 9; k < 12; ++k)
+            add4(acc, make_uint4(__funnelshift_r(v[k].x, v[k].y, 8), __funnelshift_r(v[k].y, v[k].z, 8),
+                                 __funnelshift_r(v[k].z, v[k].w, 8), __funnelshift_r(v[k].w, e[k - 9], 8)));
+    }
     const uint32_t Sw[4] = {S.x, S.y, S.z, S.w};
     const uint32_t Aw[4] = {acc.x, acc.y, acc.z, acc.w};
     uint32_t fm[4];
-    if (decide16<GATE, false>(Sw, Aw, q0, sweep, tab, gthr, key0, key1, i0, Ch, fm, dM, dB))
+    if (decide16<GATE, false, 4, true>(Sw, Aw, q0, sweep, tab, gthr, key0, key1, i0, Ch, fm, dM, dB, u))
         *reinterpret_cast<uint4*>(own) = make_uint4(Sw[0] ^ fm[0], Sw[1] ^ fm[1], Sw[2] ^ fm[2], Sw[3] ^ fm[3]);
 }
 
