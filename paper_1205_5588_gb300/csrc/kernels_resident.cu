@@ -203,6 +203,15 @@ __device__ __forceinline__ int warp_sum_i(int v) {
     return v;
 }
 
+// The two halves of the cluster barrier, so that work that needs no other CTA's writes (the
+// next pass's random words) can run while the slowest CTA finishes.
+__device__ __forceinline__ void cluster_arrive() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 template <bool CLUSTER>
 __device__ __forceinline__ void sync_all() {
     if (CLUSTER) cluster_sync_all();
@@ -311,11 +320,32 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
         k_eq = s.step_eq[k];
         k_tot = s.step_total[k];
     }
+    // In a cluster the barrier after each pass is split: a thread arrives when its sites are
+    // done, draws the Philox blocks of its first site chunk of the next pass (they depend only on
+    // counters), and waits only then.  The fold of a sweep follows the wait that ends it.
+    constexpr bool SPLIT = CLUSTER && NW == 4;
+    bool pending = false;                   // arrived, not yet waited
+    uint4 pf_u[4];                          // next pass's first chunk: its Philox blocks
+    bool pf = false;
+    long long fold_t = -1;                  // sweep whose fold waits for the next barrier
+    int fold_k = 0, fold_pos = 0, fold_eq = 0, fold_tot = 0;
+    auto fold_pending = [&]() {
+        if (folder && fold_t >= 0 && ISF_CHECK(fold_k >= 0 && fold_k < s.nsteps, 10, fold_k, s.nsteps)) {
+            const long long sM = (long long)obs[0], sB = (long long)obs[1];
+            obs[0] = 0;
+            obs[1] = 0;
+            fold_sweep(s, rs, fold_k, fold_pos, fold_eq, fold_tot, sM, sB, fold_t);
+        }
+        fold_t = -1;
+    };
     stage_table<false>(s.tables, k, tab, gate);
     for (long long t = 0; t < s.nsweeps; ++t) {
         if (pos == s.step_total[k]) {
             ++k;
             pos = 0;
+            // with the split barrier a thread gets here while others may still read the old
+            // table in the last pass: everyone first
+            if (SPLIT) __syncthreads();
             stage_table<false>(s.tables, k, tab, gate);
             if (folder) { k_eq = s.step_eq[k]; k_tot = s.step_total[k]; }
         }
@@ -323,6 +353,11 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
         const uint32_t gthr = *gate;
         int dM = 0, dB = 0;
         for (int c = 0; c < 4; ++c) {
+            if (SPLIT && pending) {
+                cluster_wait();
+                pending = false;
+                if (c == 0) fold_pending();
+            }
             ItemWalk w = walk0;
             for (int it = threadIdx.x; it < items; it += ithreads, w.next()) {
                 const int ck = w.ck, jl = w.jr, z = w.z;
@@ -359,7 +394,12 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
                     uint32_t ne[3];
                     neighbour_loads16<CLUSTER>(nbp, sgn, nv, ne);
                     uint4 u[4];
-                    philox10_xn<4>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u);
+                    if (SPLIT && pf && it == (int)threadIdx.x) {
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) u[v] = pf_u[v];
+                    } else {
+                        philox10_xn<4>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u);
+                    }
                     const uint4 a4 = neighbour_sum16_from(nv, ne, sgn);
                     Aw[0] = a4.x; Aw[1] = a4.y; Aw[2] = a4.z; Aw[3] = a4.w;
                     any = s.use_gate
@@ -404,15 +444,31 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
                     red_add64<CLUSTER>(obs0 + 8, (long long)wB);
                 }
             }
-            sync_all<CLUSTER>();    // orders the reductions before the fold, and the fold's reset
-        }                           // before the next sweep's reductions
-        if (folder && ISF_CHECK(k >= 0 && k < s.nsteps, 10, k, s.nsteps)) {
-            const long long sM = (long long)obs[0], sB = (long long)obs[1];
-            obs[0] = 0;
-            obs[1] = 0;
-            fold_sweep(s, rs, k, pos, k_eq, k_tot, sM, sB, t);
+            if (SPLIT) {
+                // the barrier orders the reductions before the fold, and the fold's reset before
+                // the next sweep's reductions
+                cluster_arrive();
+                pending = true;
+                pf = false;
+                const int cn = (c + 1) & 3;
+                const long long tn = c == 3 ? t + 1 : t;
+                if ((int)threadIdx.x < items && tn < s.nsweeps) {
+                    const unsigned long long sn = (unsigned long long)(s.sweep0 + tn + 1);
+                    const uint32_t qn = block_counter(f, cn, walk0.z, j0 + walk0.jr, W * walk0.ck);
+                    philox10_xn<4>(qn, (uint32_t)sn, (uint32_t)(sn >> 32), 0u, f.key0, f.key1, pf_u);
+                    pf = true;
+                }
+            } else {
+                sync_all<CLUSTER>();    // orders the reductions before the fold, and the fold's reset
+            }                           // before the next sweep's reductions
         }
+        if (folder) { fold_t = t; fold_k = k; fold_pos = pos; fold_eq = k_eq; fold_tot = k_tot; }
+        if (!SPLIT) fold_pending();
         ++pos;
+    }
+    if (SPLIT && pending) {
+        cluster_wait();
+        fold_pending();
     }
     if (folder) store_run_state(s.st, rs);
 
