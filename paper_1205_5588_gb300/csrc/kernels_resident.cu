@@ -37,7 +37,10 @@ constexpr int kMaxResThreads = 512;     // up to 128 registers per thread (16-si
 constexpr int kMaxResThreads8 = 768;    // up to 80 registers per thread (8-site items)
 template <int NW>
 constexpr int max_threads_for() { return NW == 2 ? kMaxResThreads8 : kMaxResThreads; }
-constexpr uint32_t kMiscBytes = 128 * 4 + 16 + 64 * 8 + 2 * kMaxK * 8 + kMaxK * 8;
+// per-CTA bookkeeping after the film and the row table: the step table (128 words), the gate
+// threshold (16 bytes), the sweep's dM, dB accumulator (2 x 8 bytes, used in CTA 0) and every
+// rank's slab address (kMaxK words)
+constexpr uint32_t kMiscBytes = 128 * 4 + 16 + 2 * 8 + kMaxK * 4;
 
 
 __device__ __forceinline__ unsigned cluster_rank() {
@@ -161,32 +164,6 @@ __device__ __forceinline__ uint4 neighbour_sum16_from(const uint4 v[12], const u
     return acc;
 }
 
-// Neighbour sum of a 16-site chunk from shared::cluster addresses (see neighbour_sum16).
-template <bool CLUSTER>
-__device__ __forceinline__ uint4 neighbour_sum16_sc(const uint32_t* nb, int sgn) {
-    uint4 acc = lds16<CLUSTER>(nb[0]);
-#pragma unroll
-    for (int k = 1; k < 9; ++k) add4(acc, lds16<CLUSTER>(nb[k]));
-    if (sgn < 0) {
-#pragma unroll
-        for (int k = 9; k < 12; ++k) {
-            const uint4 v = lds16<CLUSTER>(nb[k]);
-            const uint32_t e = lds4<CLUSTER>(nb[k] - 4);
-            add4(acc, make_uint4(__funnelshift_l(e, v.x, 8), __funnelshift_l(v.x, v.y, 8),
-                                 __funnelshift_l(v.y, v.z, 8), __funnelshift_l(v.z, v.w, 8)));
-        }
-    } else {
-#pragma unroll
-        for (int k = 9; k < 12; ++k) {
-            const uint4 v = lds16<CLUSTER>(nb[k]);
-            const uint32_t e = lds4<CLUSTER>(nb[k] + 16);
-            add4(acc, make_uint4(__funnelshift_r(v.x, v.y, 8), __funnelshift_r(v.y, v.z, 8),
-                                 __funnelshift_r(v.z, v.w, 8), __funnelshift_r(v.w, e, 8)));
-        }
-    }
-    return acc;
-}
-
 // Add v to the 64-bit word at a shared::cluster address (another CTA's shared memory, or this
 // CTA's own when CLUSTER is false).
 template <bool CLUSTER>
@@ -242,16 +219,15 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
     uint32_t* ptrs = reinterpret_cast<uint32_t*>(sm + a.ptr_off);
     uint32_t* tab = reinterpret_cast<uint32_t*>(sm + a.misc_off);
     uint32_t* gate = tab + 128;
-    long long* red = reinterpret_cast<long long*>(sm + a.misc_off + 128 * 4 + 16);
-    long long* slots = red + 64;
-    uint32_t* base = reinterpret_cast<uint32_t*>(slots + 2 * kMaxK);
+    unsigned long long* obs = reinterpret_cast<unsigned long long*>(sm + a.misc_off + 128 * 4 + 16);  // CTA 0's: dM, dB of a sweep
+    uint32_t* base = reinterpret_cast<uint32_t*>(obs + 2);
 
     // slab in, vacancy row, every rank's slab address
     const int words = P / 16;
     const uint64_t smem_n = dyn_smem_bytes();
     bool desc_ok = ISF_CHECK(K >= 1 && K <= 16 && Jb >= 1 && (int64_t)Jb * K >= Rh && P % 16 == 0, 1, K, Jb);
     desc_ok = desc_ok && ISF_CHECK(blockDim.x >= 64 && blockDim.x % 32 == 0, 12, blockDim.x, 0);
-    desc_ok = desc_ok && ISF_CHECK(a.misc_off + 1424 <= smem_n, 2, a.misc_off, smem_n);
+    desc_ok = desc_ok && ISF_CHECK(a.misc_off + kMiscBytes <= smem_n, 2, a.misc_off, smem_n);
     desc_ok = desc_ok && ISF_CHECK((uint64_t)a.ptr_off + (uint64_t)4 * L * Jb * 48 <= a.misc_off, 3, a.ptr_off, a.misc_off);
     desc_ok = desc_ok && ISF_CHECK(s.k0 >= 0 && s.k0 < s.nsteps && s.nsteps >= 1, 4, s.k0, s.nsteps);
     if (!desc_ok) { sync_all<CLUSTER>(); sync_all<CLUSTER>(); return; }
@@ -267,7 +243,6 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
     }
     for (int t = threadIdx.x; t < P / 4; t += blockDim.x) reinterpret_cast<uint32_t*>(vac)[t] = 0x01010101u;
     if (threadIdx.x < K) base[threadIdx.x] = CLUSTER ? map_rank_addr(smem_addr(film), threadIdx.x) : smem_addr(film);
-    unsigned long long* obs = reinterpret_cast<unsigned long long*>(slots);   // CTA 0's: dM, dB of a sweep
     if (threadIdx.x == 0) { obs[0] = 0; obs[1] = 0; }
     __syncthreads();
     if (PX) {

@@ -1,0 +1,41 @@
+"""bench.py's output contract, on CPU: the reference arm (the oracle on a bounded sample) prints
+one JSON line with the keys the driver reads, and the roofline bookkeeping (the 40-op count,
+the derived integer-issue peak, the traffic record gated on the kernel sources) is consistent."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_json_line(olib):
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1",
+                          "--workload", "flat16", "--ref-sweeps", "20"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["unit"] == "attempts/s" and d["value"] > 0
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["config"]["workload"].startswith("flat16")
+
+
+def test_roofline_constants():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.OPS_PER_ATTEMPT == 40
+    assert abs(bench.ALU_PEAK_TOPS - 152 * 128 * 2070e6 / 1e12) < 1e-9
+    for name, rec in bench.NCU_TRAFFIC.items():
+        assert set(rec) == {"sources", "sources_sha256", "bytes_per_launch"}
+        if rec["sources_sha256"] is not None:
+            assert len(rec["sources_sha256"]) == 64 and rec["bytes_per_launch"] > 0
+        got = bench.load_traffic(name)
+        want = rec["bytes_per_launch"] if rec["sources_sha256"] == bench.kernel_sources_sha256(rec["sources"]) else None
+        assert got == want
