@@ -135,6 +135,14 @@ int isf_read_spins(isf_lattice* lat, int8_t* host_out);
  * NULL): white pixels.  Synchronises. */
 int isf_read_surface_image(isf_lattice* lat, uint8_t* host_out, int64_t* n_up);
 
+/* Domains of the simulated PMOKE image (Sec. 6, Fig. 5): out4 = {white domains, black
+ * domains, pixels of the largest white domain, of the largest black one}.  Two pixels touch when
+ * their columns are in-plane neighbours of the film ((x +- 1, y), (x, y +- 1), (x + 1, y - 1),
+ * (x - 1, y + 1), wrapping on periodic axes); a domain is a connected set of pixels of one colour;
+ * pixels with no atom belong to none.  Synchronises.  Errors: ISF_ERR_ARG, ISF_ERR_CUDA,
+ * ISF_ERR_TIMEOUT (a bounded retry of the device union-find ran out). */
+int isf_surface_domains(isf_lattice* lat, int64_t* out4);
+
 /* Lattice statistics of Sec. 4 / Table 1: concentration p = occupied sites / (rows*cols*layers),
  * mean coordination zbar = 2 * occupied bonds / occupied sites and the critical concentration
  * p_c = 2 / zbar of Eq. 2 (inf when there are no bonds).  No device work. */

@@ -165,6 +165,47 @@ def records_to_dicts(recs) -> list[dict]:
     return out
 
 
+# In-plane neighbours of a pixel (dx, dy): the film's 6 in-plane bonds (Sec. 2).
+PIXEL_NEIGHBOURS = ((1, 0), (-1, 0), (0, 1), (0, -1), (1, -1), (-1, 1))
+
+
+def domain_stats(img, periodic_x=False, periodic_y=False) -> dict:
+    """Domains of a PMOKE image (Sec. 6, Fig. 5): connected sets of white (255) or of black (0)
+    pixels, two pixels touching when their columns are in-plane neighbours; 128 (no atom)
+    belongs to none.  Plain breadth-first search, one pixel at a time."""
+    img = np.asarray(img)
+    R, C = img.shape
+    seen = np.zeros((R, C), dtype=bool)
+    out = {"white": 0, "black": 0, "largest_white": 0, "largest_black": 0}
+    for y0 in range(R):
+        for x0 in range(C):
+            v = int(img[y0, x0])
+            if v == 128 or seen[y0, x0]:
+                continue
+            seen[y0, x0] = True
+            queue, size = [(x0, y0)], 0
+            while queue:
+                x, y = queue.pop()
+                size += 1
+                for dx, dy in PIXEL_NEIGHBOURS:
+                    xx, yy = x + dx, y + dy
+                    if not 0 <= xx < C:
+                        if not periodic_x:
+                            continue
+                        xx %= C
+                    if not 0 <= yy < R:
+                        if not periodic_y:
+                            continue
+                        yy %= R
+                    if not seen[yy, xx] and int(img[yy, xx]) == v:
+                        seen[yy, xx] = True
+                        queue.append((xx, yy))
+            key = "white" if v == 255 else "black"
+            out[key] += 1
+            out["largest_" + key] = max(out["largest_" + key], size)
+    return out
+
+
 class Film:
     """One film in the oracle: heights (rows x cols uint8), layers, flags, seed, init."""
 

@@ -595,6 +595,34 @@ int isf_read_surface_image(isf_lattice* L, uint8_t* host_out, int64_t* n_up) {
     return ISF_OK;
 }
 
+int isf_surface_domains(isf_lattice* L, int64_t* out4) {
+    if (!L || !out4) return fail(ISF_ERR_ARG, "bad arguments");
+    if (L->lay.R * (int64_t)L->lay.C > 0x7FFFFFFFLL) return fail(ISF_ERR_ARG, "image too large for 32-bit labels");
+    int rc = sync_film(L);
+    if (rc) return rc;
+    const size_t n = (size_t)L->lay.R * L->lay.C;
+    const size_t img_bytes = (n + 255) & ~size_t(255);
+    uint8_t* d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, img_bytes + 2 * n * sizeof(int) + 64), "cudaMalloc domain buffers");
+    int* scratch = reinterpret_cast<int*>(d + img_bytes);
+    unsigned long long* out = reinterpret_cast<unsigned long long*>(d + img_bytes + 2 * n * sizeof(int));
+    int* bad = reinterpret_cast<int*>(out + 4);
+    unsigned long long* up = out + 6;     // the image kernel's white count (unused here)
+    unsigned long long h[4] = {0, 0, 0, 0};
+    int hbad = 0;
+    cudaError_t ce = cudaMemsetAsync(up, 0, sizeof(unsigned long long), L->last);
+    if (ce == cudaSuccess) ce = (cudaError_t)launch_surface(L->f, d, up, L->last);
+    if (ce == cudaSuccess) ce = (cudaError_t)launch_surface_domains(L->f, d, scratch, out, bad, L->last);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, L->last);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, L->last);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(L->last);
+    cudaFree(d);
+    if (ce != cudaSuccess) return cuda_fail(ce, "surface domains");
+    if (hbad) return fail(ISF_ERR_TIMEOUT, "domain labelling: a bounded union retry ran out");
+    for (int i = 0; i < 4; ++i) out4[i] = (int64_t)h[i];
+    return ISF_OK;
+}
+
 int isf_lattice_stats(isf_lattice* L, double* p, double* zbar, double* p_c) {
     if (!L) return fail(ISF_ERR_ARG, "lattice is NULL");
     const double sites = (double)L->lay.R * L->lay.C * L->lay.L;

@@ -150,6 +150,11 @@ int launch_sweeps(const SweepArgs& a, int ctas, int threads, void* stream);
 int launch_unpack(const DevFilm& f, int8_t* dev_out, void* stream);
 int launch_pack(const DevFilm& f, const int8_t* dev_in, void* stream);
 int launch_surface(const DevFilm& f, uint8_t* dev_out, unsigned long long* dev_up, void* stream);
+// Domains of a surface image already on the device (R*C bytes): dev_scratch holds 2*R*C ints;
+// dev_out4 = {white domains, black domains, largest white, largest black}; *dev_bad = 1 if a
+// bounded union retry ran out.
+int launch_surface_domains(const DevFilm& f, const uint8_t* dev_img, int* dev_scratch, unsigned long long* dev_out4,
+                           int* dev_bad, void* stream);
 int launch_philox_blocks(uint64_t seed, uint32_t stream_id, uint64_t sweep, uint32_t q0,
                          int64_t nblocks, uint32_t* dev_out, void* stream);
 int sweep_max_ctas_for(const DevFilm& f, int threads, int* max_ctas);  // co-resident CTAs

@@ -176,6 +176,75 @@ __global__ void k_surface(DevFilm f, uint8_t* out, unsigned long long* up) {
     if ((threadIdx.x & 31) == 0 && n) atomicAdd(up, n);
 }
 
+// ---- domains of the PMOKE image (Sec. 6, Fig. 5) -------------------------------------------
+// Pixels are neighbours when their columns are in-plane neighbours of the film: (x +- 1, y),
+// (x, y +- 1), (x + 1, y - 1), (x - 1, y + 1), wrapping on periodic axes.  A domain is a
+// connected set of white (up) or of black (down) pixels; pixels with no atom belong to none.
+// Union-find: every pixel starts as its own root; each pixel links with its three "forward"
+// neighbours of the same colour (roots linked smaller-index-wins by compare-and-swap, retried
+// a bounded number of times); then every pixel takes its root as label.
+
+constexpr int kUnionTries = 1 << 20;
+
+__device__ __forceinline__ int dom_find(const int* parent, int x) {
+    int guard = 0;
+    while (parent[x] != x && ++guard < kUnionTries) x = parent[x];
+    return x;
+}
+
+__device__ __forceinline__ bool dom_union(int* parent, int a, int b) {
+    for (int tries = 0; tries < kUnionTries; ++tries) {
+        a = dom_find(parent, a);
+        b = dom_find(parent, b);
+        if (a == b) return true;
+        if (a < b) { const int t = a; a = b; b = t; }       // link the larger root under the smaller
+        const int old = atomicCAS(&parent[a], a, b);
+        if (old == a) return true;
+        a = old;
+    }
+    return false;
+}
+
+__global__ void k_dom_init(int64_t n, const uint8_t* img, int* parent) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        parent[p] = (int)p;
+}
+
+__global__ void k_dom_merge(int R, int C, uint32_t flags, const uint8_t* img, int* parent, int* bad) {
+    const int64_t n = (int64_t)R * C;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t v = img[p];
+        if (v == 128) continue;
+        const int x = (int)(p % C), y = (int)(p / C);
+        const int dx[3] = {1, 0, -1}, dy[3] = {0, 1, 1};
+        for (int k = 0; k < 3; ++k) {
+            int xx = x + dx[k], yy = y + dy[k];
+            if (xx < 0 || xx >= C) {
+                if (!(flags & 1u)) continue;
+                xx = (xx + C) % C;
+            }
+            if (yy >= R) {
+                if (!(flags & 2u)) continue;
+                yy -= R;
+            }
+            const int q = yy * C + xx;
+            if (img[q] == v && !dom_union(parent, (int)p, q)) atomicExch(bad, 1);
+        }
+    }
+}
+
+// out: [0] white domains, [1] black domains, [2] largest white, [3] largest black
+__global__ void k_dom_count(int64_t n, const uint8_t* img, int* parent, int* size, unsigned long long* out) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        if (img[p] == 128) continue;
+        const int r = dom_find(parent, (int)p);
+        const int s = atomicAdd(&size[r], 1) + 1;
+        const int w = img[p] == 255 ? 0 : 1;
+        atomicMax(&out[2 + w], (unsigned long long)s);
+        if (r == (int)p) atomicAdd(&out[w], 1ull);
+    }
+}
+
 __global__ void k_philox_blocks(uint64_t seed, uint32_t stream_id, uint64_t sweep, uint32_t q0,
                                 int64_t n, uint4* out) {
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n;
@@ -229,6 +298,22 @@ int launch_unpack(const DevFilm& f, int8_t* dev_out, void* stream) {
 int launch_surface(const DevFilm& f, uint8_t* dev_out, unsigned long long* dev_up, void* stream) {
     const int64_t total = (int64_t)f.R * f.C;
     k_surface<<<grid_for(total), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(f, dev_out, dev_up);
+    return (int)cudaGetLastError();
+}
+
+int launch_surface_domains(const DevFilm& f, const uint8_t* dev_img, int* dev_scratch, unsigned long long* dev_out4,
+                           int* dev_bad, void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t n = (int64_t)f.R * f.C;
+    int* parent = dev_scratch;
+    int* size = dev_scratch + n;
+    cudaError_t e = cudaMemsetAsync(size, 0, (size_t)n * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dev_out4, 0, 4 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dev_bad, 0, sizeof(int), s);
+    if (e != cudaSuccess) return (int)e;
+    k_dom_init<<<grid_for(n), kThreads, 0, s>>>(n, dev_img, parent);
+    k_dom_merge<<<grid_for(n), kThreads, 0, s>>>(f.R, f.C, f.flags, dev_img, parent, dev_bad);
+    k_dom_count<<<grid_for(n), kThreads, 0, s>>>(n, dev_img, parent, size, dev_out4);
     return (int)cudaGetLastError();
 }
 

@@ -70,6 +70,7 @@ def _declare(lib):
         "isf_set_path": (C.c_int, [vp, C.c_int32]),
         "isf_read_surface_image": (C.c_int, [vp, u8p, i64p]),
         "isf_lattice_stats": (C.c_int, [vp, dp, dp, dp]),
+        "isf_surface_domains": (C.c_int, [vp, i64p]),
         "isf_launch_info": (C.c_int, [vp, i32p, i32p, i32p]),
         "isf_set_item_sites": (C.c_int, [vp, C.c_int32]),
         "isf_lattice_create_slab": (C.c_int, [u8p, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, C.c_uint64,
@@ -302,6 +303,12 @@ class Lattice:
         out = np.zeros((self.layers, self.rows, self.cols), dtype=np.int8)
         _check(lib.isf_read_spins(self._h, _ptr(out, C.c_int8)), "read_spins")
         return out
+
+    def surface_domains(self) -> dict:
+        """Domains of the PMOKE image: counts and largest sizes, white (up) and black (down)."""
+        v = (C.c_int64 * 4)()
+        _check(lib.isf_surface_domains(self._h, v), "surface_domains")
+        return {"white": v[0], "black": v[1], "largest_white": v[2], "largest_black": v[3]}
 
     def surface_image(self) -> np.ndarray:
         """Simulated PMOKE image (255 up, 0 down, 128 no atom), rows x cols uint8."""

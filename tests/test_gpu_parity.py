@@ -332,7 +332,9 @@ def test_surface_image_and_stats_match_oracle(I, packed):
         lat.run(3)
         of.run([2.5], [h[k]], [0], [3])
         img = lat.surface_image()
-        assert np.array_equal(img, of.surface_image()), k
+        oimg = of.surface_image()
+        assert np.array_equal(img, oimg), k
+        assert lat.surface_domains() == oracle.domain_stats(oimg), k
     st = lat.stats()
     info = of.info()
     assert st["zbar"] == 2 * info["n_bonds"] / info["n_occ"]
@@ -351,4 +353,27 @@ def test_curie_estimate_of_a_scan(I):
     lat.run(-1)
     tc = I.estimate_tc(lat.observables())
     assert 7.0 <= tc <= 10.0
+    lat.close()
+
+
+@pytest.mark.parametrize("shape,periodic", [((64, 96), False), ((48, 48), True), ((300, 257), False)])
+def test_surface_domains_match_oracle(I, shape, periodic):
+    """Domain counts and largest domains of the PMOKE image (Sec. 6, Fig. 5) on films with many
+    domains: a high-temperature state on open and periodic films, and a large open film."""
+    from oracle import oracle
+    R, C = shape
+    if periodic:
+        spec = film(np.full((R, C), 2), 2, seed=5, periodic_x=True, periodic_y=True)
+    else:
+        spec = film(W.fractal_heights(R, C, 0.6, 0, 3, seed=R + C), 3, seed=9)
+    lat = I.Lattice(spec["heights"], spec["layers"], seed=spec["seed"], periodic_x=periodic, periodic_y=periodic)
+    of = oracle.Film(spec["heights"], spec["layers"], flags=3 if periodic else 0, seed=spec["seed"])
+    lat.set_schedule([6.0, 3.0], [0.0, 0.2], [0, 0], [2, 2])
+    lat.run(-1)
+    of.run([6.0, 3.0], [0.0, 0.2], [0, 0], [2, 2])
+    oimg = of.surface_image()
+    assert np.array_equal(lat.surface_image(), oimg)
+    want = oracle.domain_stats(oimg, periodic_x=periodic, periodic_y=periodic)
+    assert want["white"] > 3 and want["black"] > 3
+    assert lat.surface_domains() == want
     lat.close()

@@ -179,3 +179,47 @@ def test_surface_image(olib):
     f.set_spins(s)
     img = f.surface_image()
     assert img.tolist() == [[128, 255, 0], [255, 128, 0]]
+
+
+# Pixels touch when their columns are in-plane neighbours: (x +- 1, y), (x, y +- 1),
+# (x + 1, y - 1), (x - 1, y + 1); as a 3x3 structure over [dy + 1][dx + 1]:
+TRIANGULAR = np.array([[0, 1, 1], [1, 1, 1], [1, 1, 0]])
+
+
+@pytest.mark.parametrize("seed,shape", [(1, (9, 13)), (2, (20, 20)), (3, (1, 17)), (4, (31, 7)), (5, (12, 40))])
+def test_domain_stats_equal_scipy_labelling(seed, shape):
+    """The oracle's breadth-first domains equal scipy.ndimage.label with the triangular
+    connectivity, colour by colour, on random open images (with no-atom pixels)."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    img = rng.choice(np.array([0, 128, 255], dtype=np.uint8), size=shape, p=[0.45, 0.1, 0.45])
+    got = oracle.domain_stats(img)
+    for v, key in ((255, "white"), (0, "black")):
+        lab, n = ndimage.label(img == v, structure=TRIANGULAR)
+        sizes = np.bincount(lab.ravel())[1:]
+        assert got[key] == n
+        assert got["largest_" + key] == (int(sizes.max()) if n else 0)
+
+
+def test_domain_stats_special_cases():
+    """Hand-checked images: one diagonal chain touches along (1, -1) but not along (1, 1); a
+    stripe across the periodic edge is one domain; a checkerboard is all separate pixels in
+    the open case but joined along the triangular diagonal."""
+    img = np.full((3, 3), 128, dtype=np.uint8)
+    img[2, 0] = img[1, 1] = img[0, 2] = 255                 # (x, y) = (0,2), (1,1), (2,0): dx=+1, dy=-1
+    assert oracle.domain_stats(img)["white"] == 1
+    img = np.full((3, 3), 128, dtype=np.uint8)
+    img[0, 0] = img[1, 1] = img[2, 2] = 255                 # dx=+1, dy=+1: not bonded
+    assert oracle.domain_stats(img) == {"white": 3, "black": 0, "largest_white": 1, "largest_black": 0}
+    img = np.zeros((4, 6), dtype=np.uint8)
+    img[:, 0] = img[:, 5] = 255                             # two edge columns
+    assert oracle.domain_stats(img)["white"] == 2
+    assert oracle.domain_stats(img, periodic_x=True)["white"] == 1
+    assert oracle.domain_stats(img, periodic_x=True)["largest_white"] == 8
+    img = np.zeros((4, 4), dtype=np.uint8)
+    img[0, :] = img[3, :] = 255
+    assert oracle.domain_stats(img, periodic_y=True) == {"white": 1, "black": 1, "largest_white": 8,
+                                                          "largest_black": 8}
+    chk = (np.add.outer(np.arange(4), np.arange(4)) % 2 * 255).astype(np.uint8)
+    # (x, y) and (x + 1, y - 1) share the parity of x + y: the diagonals x + y = const join up
+    assert oracle.domain_stats(chk)["white"] + oracle.domain_stats(chk)["black"] == 7
