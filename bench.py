@@ -389,8 +389,8 @@ def measure_served(I, rate=200.0, duration=5.0, seed=5, pool=24, budget_gb=40.0,
 # recorded value (None: not captured for the current sources).
 NCU_TRAFFIC = {
     "fractal256": {"sources": ["kernels_resident.cu", "sweep_core.cuh", "device_common.cuh"],
-                   "sources_sha256": "21077db8540f0335bd4373d921db0f3709f994af5e31f3c9a003368d3030e189",
-                   "bytes_per_launch": 1185280.0},
+                   "sources_sha256": "7aff57690487776b19bfa62819ebbcf7d07783ccb473797bee5e5a15f6d8fec0",
+                   "bytes_per_launch": 1148672.0},
     "fractal2048": {"sources": ["kernels_sweep.cu", "sweep_core.cuh", "device_common.cuh"],
                     "sources_sha256": "691a712bae0ccbce75dc3fa1a3187d900b9d1bd8ca424a4695ce6087f833b22f",
                     "bytes_per_launch": 10961408.0 + 3328512.0},
