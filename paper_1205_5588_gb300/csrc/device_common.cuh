@@ -12,13 +12,20 @@ namespace isf {
 // 0 and 2 by the round constants, swaps the halves, XORs in the key, and the key advances by
 // the Weyl increments.  The key is uniform across the grid, so its schedule stays in uniform
 // registers.
+// One 32x32 -> 64-bit product as a single wide multiply (its low and high words).
+__device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t& lo, uint32_t& hi) {
+    unsigned long long p;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+    lo = (uint32_t)p;
+    hi = (uint32_t)(p >> 32);
+}
+
 __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        uint32_t lo0, hi0, lo1, hi1;
+        mul_wide(0xD2511F53u, c.x, lo0, hi0);
+        mul_wide(0xCD9E8D57u, c.z, lo1, hi1);
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;

@@ -212,8 +212,9 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
     full_add(U1, V2, k1, X[2], k2);
     full_add(U2, V3, k2, X[3], k3);
     X[4] = U3 ^ k3;
-    // transpose the 8 planes {X0..X4, S, O, 0}: byte k of P[r] = table index of lane 8k + r
-    uint32_t P[8] = {X[0], X[1], X[2], X[3], X[4], S, O, 0u};
+    // transpose the 8 planes {0, 0, X0..X4, S}: byte k of P[r] = 4 x the table index
+    // (up << 5) | X of lane 8k + r, i.e. its byte offset in the table
+    uint32_t P[8] = {0u, 0u, X[0], X[1], X[2], X[3], X[4], S};
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const uint32_t t = ((P[p] >> 4) ^ P[p + 4]) & 0x0F0F0F0Fu;
@@ -244,7 +245,8 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
             const int v = 4 * g + vv;
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const uint32_t t = tab[(P[4 * (v & 1) + b] >> (8 * (v >> 1))) & 0x7Fu];
+                const uint32_t t = *reinterpret_cast<const uint32_t*>(
+                    reinterpret_cast<const uint8_t*>(tab) + ((P[4 * (v & 1) + b] >> (8 * (v >> 1))) & 0xFFu));
                 thr[4 * vv + b] = t;
                 if (g) need |= needs_word(t);
             }
@@ -268,6 +270,7 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
             F |= lanes << (4 * (4 * g + vv));
         }
     }
+    F &= O;                     // vacant sites never flip
     if (F) {
         f.sp[base] = S ^ F;
         const uint32_t Fu = F & S, Fd = F & ~S;        // flipped up -> down, down -> up

@@ -10,9 +10,9 @@
 namespace isf {
 
 // Table of the current step in shared memory, indexed by the per-site byte a pass forms:
-//   int8   : (stored byte << 5) | (n + 12), stored byte 0 = down, 1 = vacancy, 2 = up
-//   packed : (occupied << 6) | (up << 5) | (n + 12)
-// Vacancies map to 0 ("never"), so they never flip and never draw a random word.
+//   int8   : (stored byte << 5) | (n + 12), stored byte 0 = down, 1 = vacancy, 2 = up;
+//            vacancies map to 0 ("never"), so they never flip and never draw a random word
+//   packed : (up << 5) | (n + 12); the packed kernel masks vacant sites out of the flips itself
 template <bool PACKED>
 __device__ __forceinline__ void stage_table(const uint32_t* tables, int k, uint32_t* tab, uint32_t* gate) {
     const uint32_t* src = tables + (size_t)k * kTableStride;
@@ -21,7 +21,7 @@ __device__ __forceinline__ void stage_table(const uint32_t* tables, int k, uint3
         const int X = t & 31;
         if (X <= 24) {
             if (PACKED) {
-                if (t >> 6) v = src[X * 2 + ((t >> 5) & 1)];
+                if (t < 64) v = src[X * 2 + (t >> 5)];
             } else {
                 const int sb = t >> 5;
                 if (sb == 0) v = src[X * 2 + 0];
@@ -70,10 +70,9 @@ __device__ __forceinline__ void philox10_xn(uint32_t q0, uint32_t s_lo, uint32_t
     for (int r = 0; r < 10; ++r) {
 #pragma unroll
         for (int v = 0; v < NW; ++v) {
-            const uint32_t lo0 = 0xD2511F53u * c0[v];
-            const uint32_t hi0 = __umulhi(0xD2511F53u, c0[v]);
-            const uint32_t lo1 = 0xCD9E8D57u * c2[v];
-            const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2[v]);
+            uint32_t lo0, hi0, lo1, hi1;
+            mul_wide(0xD2511F53u, c0[v], lo0, hi0);
+            mul_wide(0xCD9E8D57u, c2[v], lo1, hi1);
             c0[v] = hi1 ^ c1[v] ^ k0;
             c1[v] = lo1;
             c2[v] = hi0 ^ c3[v] ^ k1;
