@@ -66,6 +66,39 @@ __device__ __forceinline__ bool grid_barrier(FilmState* st, unsigned G, unsigned
     return true;
 }
 
+// The barrier in two halves, so that work needing no other CTA's writes of the pass (the next
+// pass's first random words) can run while thread 0 waits.
+__device__ __forceinline__ void grid_arrive(FilmState* st, unsigned G, unsigned& target) {
+    __syncthreads();
+    if (G > 1 && threadIdx.x == 0) {
+        target += G;
+        red_release_add_u32(&st->bar_count, 1u);
+    }
+}
+__device__ __forceinline__ bool grid_wait(FilmState* st, unsigned G, unsigned target, int* ok_s) {
+    if (G > 1) {
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            unsigned spins = 0;
+            while ((int)(ld_acquire_u32(&st->bar_count) - target) < 0) {
+                ++spins;
+                if ((spins & 15u) == 0 && ld_volatile_i32(&st->error)) { ok = 0; break; }
+                if (spins > kSpinLimit) {
+                    atomicCAS(&st->error, 0, (int)ISF_ERR_TIMEOUT);
+                    st->error_where = 1;
+                    ok = 0;
+                    break;
+                }
+                if (spins > 64) __nanosleep(32);
+            }
+            *ok_s = ok;
+        }
+        __syncthreads();
+        return *ok_s != 0;
+    }
+    return true;
+}
+
 // ---- int8 layout, open boundaries: one thread per 16-site chunk of a colour row ------------
 template <bool GATE>
 __device__ __forceinline__ void chunk_int8(const DevFilm& f, int c, int z, int j, int ck,
@@ -190,7 +223,7 @@ __device__ __forceinline__ void packed_loads(const DevFilm& f, const NbrClass& n
 template <bool GATE, bool NARROW>
 __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int j, int w,
                                             unsigned long long sweep, const uint32_t* tab,
-                                            uint32_t gthr, int& dM, int& dB) {
+                                            uint32_t gthr, int& dM, int& dB, const uint4 (&pre)[4], bool use_pre) {
     const NbrClass& nc = f.nb[c][z & 1];
     const int64_t base = addrw(f, c, z, j, w);
     uint32_t S, O, up[12], V[4];
@@ -199,7 +232,12 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
     // flight (every pass starts all warps together, so nothing else would fill that wait)
     const uint32_t q0 = block_counter(f, c, z, j, 32 * w);
     uint4 u_first[4];
-    philox10_xn<4>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u_first);
+    if (use_pre) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) u_first[v] = pre[v];
+    } else {
+        philox10_xn<4>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u_first);
+    }
     if (!O) return;             // no occupied site in the word (tested after the loads are issued)
     // X = n + 12 = 2 * (#up) + (#vacant) over the 12 neighbours, 5 bit-planes
     uint32_t U0, U1, U2, U3;
@@ -297,22 +335,26 @@ __device__ __forceinline__ int first_item(unsigned G, unsigned cta) {
 template <int MODE, bool GATE>
 __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned long long sweep,
                                             const uint32_t* tab, uint32_t gthr, int items,
-                                            ItemWalk w, unsigned G, unsigned cta, int& dM, int& dB) {
+                                            ItemWalk w, unsigned G, unsigned cta, int& dM, int& dB,
+                                            const uint4 (&pre)[4], bool have_pre) {
     const int stride = (int)G * blockDim.x;
     if (MODE == MODE_PACKED && f.items) {
-        // the colour's occupied words only, thread t taking entries t, t + stride, ...
+        // the colour's occupied words only, thread t taking entries t, t + stride, ...; the first
+        // one's first four Philox blocks may have been drawn before the pass (pre)
         const uint32_t* list = f.items + (int64_t)c * f.item_cap;
         const int n = f.nitems[c];
         const int wb = f.item_wbits, jb = f.item_jbits;
         const uint32_t wmask = (1u << wb) - 1u, jmask = (1u << jb) - 1u;
-        for (int it = first_item(G, cta); it < n; it += stride) {
+        const int it0 = first_item(G, cta);
+        for (int it = it0; it < n; it += stride) {
             const uint32_t e = list[it];
+            const bool use = have_pre && it == it0;
             if (f.narrow)
                 word_packed<GATE, true>(f, c, (int)(e >> (jb + wb)), (int)((e >> wb) & jmask), (int)(e & wmask), sweep,
-                                        tab, gthr, dM, dB);
+                                        tab, gthr, dM, dB, pre, use);
             else
                 word_packed<GATE, false>(f, c, (int)(e >> (jb + wb)), (int)((e >> wb) & jmask), (int)(e & wmask), sweep,
-                                         tab, gthr, dM, dB);
+                                         tab, gthr, dM, dB, pre, use);
         }
         return;
     }
@@ -320,7 +362,7 @@ __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned lo
     for (int it = first_item(G, cta); it < items; it += stride, w.next()) {
         if (MODE == MODE_INT8) chunk_int8<GATE>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB);
         else if (MODE == MODE_GENERIC) block_generic<GATE>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB);
-        else word_packed<GATE, false>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB);
+        else word_packed<GATE, false>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB, pre, false);
     }
 }
 
@@ -346,6 +388,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
     walk0.init(first_item(G, cta), (int)G * blockDim.x, per_row, nrows > 0 ? nrows : 1);
     // colours of this launch: all four, or one colour pass of one sweep
     const int c_begin = a.pass_plus1 ? a.pass_plus1 - 1 : 0, c_end = a.pass_plus1 ? a.pass_plus1 : 4;
+    // packed films with word lists on the grid path: the barrier is split (see grid_arrive)
+    const bool PREFETCH = MODE == MODE_PACKED && BAR == BAR_GRID && G > 1 && f.items != nullptr && !a.pass_plus1;
+    uint4 pf[4];
+    bool have_pf = false;
     int k = a.k0, pos = a.pos0;
     const bool folder = cta == 0 && threadIdx.x == 0;
     __shared__ RunState rs;     // touched by the folding thread only
@@ -367,8 +413,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
         const uint32_t gthr = gate_s;
         int dM = 0, dB = 0;
         for (int c = c_begin; c < c_end; ++c) {
-            if (a.use_gate) colour_pass<MODE, true>(f, c, sweep, tab, gthr, items, walk0, G, cta, dM, dB);
-            else colour_pass<MODE, false>(f, c, sweep, tab, gthr, items, walk0, G, cta, dM, dB);
+            if (a.use_gate) colour_pass<MODE, true>(f, c, sweep, tab, gthr, items, walk0, G, cta, dM, dB, pf, have_pf);
+            else colour_pass<MODE, false>(f, c, sweep, tab, gthr, items, walk0, G, cta, dM, dB, pf, have_pf);
             if (c == c_end - 1) {
                 long long sM = dM, sB = dB;
                 block_sum2(sM, sB, red);
@@ -381,6 +427,24 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
             if (BAR == BAR_CLUSTER) {
                 if (G > 1) cluster_barrier();
                 else __syncthreads();
+            } else if (PREFETCH) {
+                grid_arrive(st, G, target);
+                // the first word of the next pass (the lists do not change): its first four
+                // Philox blocks while thread 0 waits for the other CTAs
+                have_pf = false;
+                const int cn = (c + 1) & 3;
+                const long long tn = c == 3 ? t + 1 : t;
+                const int it0 = first_item(G, cta);
+                if (tn < a.nsweeps && it0 < f.nitems[cn]) {
+                    const uint32_t e = f.items[(int64_t)cn * f.item_cap + it0];
+                    const int wb = f.item_wbits, jbits = f.item_jbits;
+                    const uint32_t qn = block_counter(f, cn, (int)(e >> (jbits + wb)), (int)((e >> wb) & ((1u << jbits) - 1u)),
+                                                      32 * (int)(e & ((1u << wb) - 1u)));
+                    const unsigned long long sn = (unsigned long long)(a.sweep0 + tn + 1);
+                    philox10_xn<4>(qn, (uint32_t)sn, (uint32_t)(sn >> 32), 0u, f.key0, f.key1, pf);
+                    have_pf = true;
+                }
+                if (!grid_wait(st, G, target, &ok_s)) return;
             } else if (!grid_barrier(st, G, target, &ok_s)) {
                 return;
             }
