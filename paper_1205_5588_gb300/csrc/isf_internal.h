@@ -30,8 +30,14 @@
 namespace isf {
 
 constexpr uint32_t kAlways = 0xFFFFFFFFu;
-constexpr int kTableStride = 52;    // per step: thr[n+12][s'] (50 words), gate threshold, pad
+constexpr int kTableStride = 52;    // per step: thr[n+12][s'] (50 words), gate threshold, flags
 constexpr int kGateSlot = 50;
+constexpr int kFlagSlot = 51;
+// Step flag: a site whose 12 neighbours all share its spin still needs a random word (its
+// threshold is neither 0 nor "always"), so nearly every group of sites draws words and the
+// kernels skip the test of whether a group needs them.  A scheduling hint only: the words
+// drawn and the decisions are the same either way.
+constexpr uint32_t kFlagAlwaysDraw = 1u;
 constexpr int kMaxThreads = 1024;
 
 // Neighbour offsets of one (colour, layer parity) class: 9 unshifted, then 3 shifted by `sgn`

@@ -325,7 +325,7 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
             if (folder) { k_eq = s.step_eq[k]; k_tot = s.step_total[k]; }
         }
         const unsigned long long sweep = (unsigned long long)(s.sweep0 + t + 1);
-        const uint32_t gthr = *gate;
+        const uint32_t gthr = gate[0];
         int dM = 0, dB = 0;
         for (int c = 0; c < 4; ++c) {
             if (SPLIT && pending) {

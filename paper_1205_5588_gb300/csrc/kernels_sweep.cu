@@ -223,7 +223,8 @@ __device__ __forceinline__ void packed_loads(const DevFilm& f, const NbrClass& n
 template <bool GATE, bool NARROW>
 __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int j, int w,
                                             unsigned long long sweep, const uint32_t* tab,
-                                            uint32_t gthr, int& dM, int& dB, const uint4 (&pre)[4], bool use_pre) {
+                                            uint32_t gthr, bool always_draw, int& dM, int& dB, const uint4 (&pre)[4],
+                                            bool use_pre) {
     const NbrClass& nc = f.nb[c][z & 1];
     const int64_t base = addrw(f, c, z, j, w);
     uint32_t S, O, up[12], V[4];
@@ -286,7 +287,16 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
                 const uint32_t t = *reinterpret_cast<const uint32_t*>(
                     reinterpret_cast<const uint8_t*>(tab) + ((P[4 * (v & 1) + b] >> (8 * (v >> 1))) & 0xFFu));
                 thr[4 * vv + b] = t;
-                if (g) need |= needs_word(t);
+            }
+        }
+        // the second half draws its words only if a lane needs one (unless the step's table
+        // says nearly every group does)
+        if (g) {
+            if (always_draw) {
+                need = true;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) need |= needs_word(thr[i]);
             }
         }
         uint4 u[4];
@@ -335,7 +345,7 @@ __device__ __forceinline__ int first_item(unsigned G, unsigned cta) {
 template <int MODE, bool GATE>
 __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned long long sweep,
                                             const uint32_t* tab, uint32_t gthr, int items,
-                                            ItemWalk w, unsigned G, unsigned cta, int& dM, int& dB,
+                                            ItemWalk w, unsigned G, unsigned cta, bool always_draw, int& dM, int& dB,
                                             const uint4 (&pre)[4], bool have_pre) {
     const int stride = (int)G * blockDim.x;
     if (MODE == MODE_PACKED && f.items) {
@@ -351,10 +361,10 @@ __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned lo
             const bool use = have_pre && it == it0;
             if (f.narrow)
                 word_packed<GATE, true>(f, c, (int)(e >> (jb + wb)), (int)((e >> wb) & jmask), (int)(e & wmask), sweep,
-                                        tab, gthr, dM, dB, pre, use);
+                                        tab, gthr, always_draw, dM, dB, pre, use);
             else
                 word_packed<GATE, false>(f, c, (int)(e >> (jb + wb)), (int)((e >> wb) & jmask), (int)(e & wmask), sweep,
-                                         tab, gthr, dM, dB, pre, use);
+                                         tab, gthr, always_draw, dM, dB, pre, use);
         }
         return;
     }
@@ -362,7 +372,7 @@ __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned lo
     for (int it = first_item(G, cta); it < items; it += stride, w.next()) {
         if (MODE == MODE_INT8) chunk_int8<GATE>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB);
         else if (MODE == MODE_GENERIC) block_generic<GATE>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB);
-        else word_packed<GATE, false>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB, pre, false);
+        else word_packed<GATE, false>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, always_draw, dM, dB, pre, false);
     }
 }
 
@@ -375,7 +385,7 @@ enum { BAR_GRID = 0, BAR_CLUSTER = 1 };
 template <int MODE, int BAR = BAR_GRID>
 __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsigned cta) {
     __shared__ uint32_t tab[128];
-    __shared__ uint32_t gate_s;
+    __shared__ uint32_t gate_s[2];      // gate threshold, step flags
     __shared__ long long red[64];
     __shared__ int ok_s;
     const DevFilm& f = a.f;
@@ -401,20 +411,21 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
         k_eq = a.step_eq[k];
         k_tot = a.step_total[k];
     }
-    stage_table<MODE == MODE_PACKED>(a.tables, k, tab, &gate_s);
+    stage_table<MODE == MODE_PACKED>(a.tables, k, tab, gate_s);
     for (long long t = 0; t < a.nsweeps; ++t) {
         if (pos == a.step_total[k]) {
             ++k;
             pos = 0;
-            stage_table<MODE == MODE_PACKED>(a.tables, k, tab, &gate_s);
+            stage_table<MODE == MODE_PACKED>(a.tables, k, tab, gate_s);
             if (folder) { k_eq = a.step_eq[k]; k_tot = a.step_total[k]; }
         }
         const unsigned long long sweep = (unsigned long long)(a.sweep0 + t + 1);
-        const uint32_t gthr = gate_s;
+        const uint32_t gthr = gate_s[0];
+        const bool always_draw = (gate_s[1] & kFlagAlwaysDraw) != 0;
         int dM = 0, dB = 0;
         for (int c = c_begin; c < c_end; ++c) {
-            if (a.use_gate) colour_pass<MODE, true>(f, c, sweep, tab, gthr, items, walk0, G, cta, dM, dB, pf, have_pf);
-            else colour_pass<MODE, false>(f, c, sweep, tab, gthr, items, walk0, G, cta, dM, dB, pf, have_pf);
+            if (a.use_gate) colour_pass<MODE, true>(f, c, sweep, tab, gthr, items, walk0, G, cta, always_draw, dM, dB, pf, have_pf);
+            else colour_pass<MODE, false>(f, c, sweep, tab, gthr, items, walk0, G, cta, always_draw, dM, dB, pf, have_pf);
             if (c == c_end - 1) {
                 long long sM = dM, sB = dB;
                 block_sum2(sM, sB, red);

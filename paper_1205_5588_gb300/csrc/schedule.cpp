@@ -39,7 +39,10 @@ void build_step_table(double T, double h, double J, double h_s, uint32_t* out52)
     }
     const double a = std::fabs(h_s);
     out52[kGateSlot] = (a == 0.0) ? kAlways : count_below(std::exp(-a / T));
-    out52[kGateSlot + 1] = 0u;
+    // aligned sites: n = +12 with s = +1, n = -12 with s = -1
+    auto needs_word = [](uint32_t t) { return t != 0u && t != kAlways; };
+    const bool always = needs_word(out52[(12 + 12) * 2 + 1]) || needs_word(out52[(-12 + 12) * 2 + 0]);
+    out52[kFlagSlot] = always ? kFlagAlwaysDraw : 0u;
 }
 
 namespace {

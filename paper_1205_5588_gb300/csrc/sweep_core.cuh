@@ -30,7 +30,10 @@ __device__ __forceinline__ void stage_table(const uint32_t* tables, int k, uint3
         }
         tab[t] = v;
     }
-    if (threadIdx.x == 0) *gate = src[kGateSlot];
+    if (threadIdx.x == 0) {
+        gate[0] = src[kGateSlot];
+        gate[1] = src[kFlagSlot];
+    }
     __syncthreads();
 }
 
