@@ -389,11 +389,11 @@ def measure_served(I, rate=200.0, duration=5.0, seed=5, pool=24, budget_gb=40.0,
 # recorded value (None: not captured for the current sources).
 NCU_TRAFFIC = {
     "fractal256": {"sources": ["kernels_resident.cu", "sweep_core.cuh", "device_common.cuh"],
-                   "sources_sha256": "7aff57690487776b19bfa62819ebbcf7d07783ccb473797bee5e5a15f6d8fec0",
-                   "bytes_per_launch": 1148672.0},
+                   "sources_sha256": "431af0d2e9ceaffe84ef07562c19b522bdaaa546806c9de0aaf5796d5dbd83cd",
+                   "bytes_per_launch": 1255680.0},
     "fractal2048": {"sources": ["kernels_sweep.cu", "sweep_core.cuh", "device_common.cuh"],
-                    "sources_sha256": "691a712bae0ccbce75dc3fa1a3187d900b9d1bd8ca424a4695ce6087f833b22f",
-                    "bytes_per_launch": 10961408.0 + 3328512.0},
+                    "sources_sha256": "77b38e941175838cf991b7ed29a098322ca61dee801a15e40a839e662592a46b",
+                    "bytes_per_launch": 11376128.0 + 2352128.0},
 }
 
 
