@@ -174,9 +174,17 @@ int isf_read_trace(isf_lattice* lat, int64_t* host_out, int64_t max_pairs, int64
  *     barrier between colour passes) — the paper's row decomposition with CTAs as processes
  *     (Sec. 3, list items 1-2); int8 films that fit only;
  *   ISF_PATH_GLOBAL: spins in device memory, all SMs, a grid barrier between colour passes;
- *   ISF_PATH_AUTO (default): resident when the film fits, else global.
- * Errors: ISF_ERR_ARG (unknown path; resident for a packed film). */
-enum { ISF_PATH_AUTO = 0, ISF_PATH_GLOBAL = 1, ISF_PATH_RESIDENT = 2 };
+ *   ISF_PATH_SLABS: packed films only; the film split by rows over up to one CTA per SM, each
+ *     CTA's band of rows (plus one halo row on each side) in its shared memory, the boundary
+ *     rows exchanged through device memory after each colour pass, and each CTA waiting for
+ *     its two neighbours only (the same row decomposition, over the whole GPU); launches of at
+ *     most 4096 sweeps, each followed by a one-thread fold of the per-sweep M, B series;
+ *   ISF_PATH_AUTO (default): int8 films resident when the film fits, else global; packed films
+ *     slabs when a colour pass has more than 512 and at most (SMs x 512) / 3 occupied words
+ *     (films of roughly 100^2 to 900^2 sites per layer), else global.
+ * Errors: ISF_ERR_ARG (unknown path; resident for a packed film; slabs for an int8 film, a slab
+ * film or a packed film whose word lists could not be built). */
+enum { ISF_PATH_AUTO = 0, ISF_PATH_GLOBAL = 1, ISF_PATH_RESIDENT = 2, ISF_PATH_SLABS = 3 };
 int isf_set_path(isf_lattice* lat, int32_t path);
 
 /* Launch shape override: ctas = CTAs of the global kernel or cluster size (1..16) of the
@@ -198,7 +206,7 @@ int isf_set_item_sites(isf_lattice* lat, int32_t sites);
  * also report it as ISF_ERR_STATE. */
 int isf_debug_checks(uint64_t* out4);
 
-/* Shape of the last isf_run_sweeps launch: path (ISF_PATH_GLOBAL / ISF_PATH_RESIDENT, 0 before
+/* Shape of the last isf_run_sweeps launch: path (ISF_PATH_GLOBAL / ISF_PATH_RESIDENT / ISF_PATH_SLABS, 0 before
  * any launch), CTAs (global) or cluster size (resident), threads per CTA.  No device work. */
 int isf_launch_info(isf_lattice* lat, int32_t* path, int32_t* ctas, int32_t* threads);
 /* Sites per work item of the last isf_run_sweeps launch (16 or 8 resident, 16 int8 global, 32

@@ -21,7 +21,7 @@ LIB_NAME = "libisingfilm.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels_sweep.cu", "kernels_resident.cu", "kernels_aux.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels_sweep.cu", "kernels_slabs.cu", "kernels_resident.cu", "kernels_aux.cu", "noalloc.cu"]
 CPP_SOURCES = ["capi.cpp", "batch.cpp", "serve.cpp", "lattice.cpp", "schedule.cpp"]
 HEADERS = ["isf_internal.h", "device_common.cuh", "sweep_core.cuh", "capi_internal.h"]
 

@@ -130,9 +130,11 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
     }
     std::vector<uint32_t> items;
     if (lay.packed && build_word_items(lay, heights, items, f.nitems, &f.item_wbits, &f.item_jbits,
-                                       sw ? sw->jlo : 0, sw ? sw->jhi : lay.Rh)) {
+                                       sw ? sw->jlo : 0, sw ? sw->jhi : lay.Rh, sw ? nullptr : &L->roff_h)) {
         f.items = reinterpret_cast<const uint32_t*>(L->dev + lay.items_off);
         f.item_cap = lay.items_cap;
+    } else {
+        L->roff_h.clear();
     }
     if (lay.packed) f.narrow = (4 * lay.csw + 2 * lay.lsw) < ((int64_t)1 << 31) ? 1 : 0;
 
@@ -145,6 +147,11 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
         e = cudaMemcpyAsync(L->dev + lay.items_off, items.data(), items.size() * sizeof(uint32_t),
                             cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return bail(cuda_fail(e, "copy word lists"));
+    }
+    if (!L->roff_h.empty()) {
+        e = cudaMemcpyAsync(L->dev + lay.roff_off, L->roff_h.data(), L->roff_h.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "copy word-list row offsets"));
     }
     e = cudaMemcpyAsync(L->dev + lay.heights_off, heights, n_px, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return bail(cuda_fail(e, "copy heights"));
@@ -468,6 +475,106 @@ int isf_set_schedule(isf_lattice* L, int32_t nsteps, const double* T, const doub
     return ISF_OK;
 }
 
+// Rows [part[g], part[g+1]) of each of the G CTAs of the row-slab kernel: contiguous, 1..cap
+// rows each, cut where the running count of occupied words (all colours) is closest to an even
+// share.  Returns the most rows of any CTA.
+static int slab_partition(const isf_lattice* L, int G, int cap, std::vector<int32_t>& part) {
+    const int Rh = L->lay.Rh;
+    std::vector<int64_t> pre((size_t)Rh + 1, 0);
+    for (int j = 0; j < Rh; ++j) {
+        int64_t w = 0;
+        for (int cz = 0; cz < 4 * L->lay.L; ++cz) {
+            const int32_t* ro = L->roff_h.data() + (size_t)cz * (Rh + 1);
+            w += ro[j + 1] - ro[j];
+        }
+        pre[j + 1] = pre[j] + w;
+    }
+    part.assign((size_t)G + 1, 0);
+    int nrm = 0;
+    for (int g = 0; g < G; ++g) {
+        const int left = G - g - 1;                     // CTAs after this one
+        const int lo = std::max(part[g] + 1, Rh - left * cap);
+        const int hi = std::min(part[g] + cap, Rh - left);
+        const double target = (double)pre[Rh] * (g + 1) / G;
+        int best = lo;
+        for (int e = lo; e <= hi; ++e)
+            if (std::fabs((double)pre[e] - target) < std::fabs((double)pre[best] - target)) best = e;
+        part[g + 1] = best;
+        nrm = std::max(nrm, best - part[g]);
+    }
+    return nrm;
+}
+
+// Sweeps of a packed whole film by the row-slab kernel, in launches of at most kSeriesChunk
+// sweeps, each followed by the fold of its per-sweep series.  *fits = false (and nothing
+// launched) when the film or the requested shape does not fit the kernel.
+static int run_slabs(isf_lattice* L, int64_t nsweeps, cudaStream_t s, bool* fits) {
+    *fits = false;
+    const Layout& lay = L->lay;
+    if (!lay.packed || L->f.slab || !L->f.items || L->roff_h.empty() || lay.L > kSlabMaxLayers) return ISF_OK;
+    const int threads = L->threads ? L->threads : 512;
+    if (threads % 32 || threads < 64 || threads > 512) return ISF_OK;
+    int dev = 0, sms = 1, optin = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+    CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "device attribute");
+    const int G = L->ctas > 0 ? L->ctas : std::min(sms, lay.slab_gmax);
+    if (G < 1 || G > lay.slab_gmax) return ISF_OK;
+    const uint32_t per_row = slab_smem_bytes(L->f, 1) - slab_smem_bytes(L->f, 0);
+    const int64_t cap = ((int64_t)optin - kSlabStaticSmem - (int64_t)slab_smem_bytes(L->f, 0)) / per_row;
+    if (cap < 1 || cap * G < lay.Rh) return ISF_OK;
+    if (G != L->part_G) {
+        L->part_nrm = slab_partition(L, G, (int)std::min<int64_t>(cap, lay.Rh), L->part_h);
+        // pageable source: the copy is staged before cudaMemcpyAsync returns
+        CUDA_TRY(cudaMemcpyAsync(L->dev + lay.part_off, L->part_h.data(), L->part_h.size() * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, s), "copy row partition");
+        L->part_G = G;
+    }
+    const uint32_t smem = slab_smem_bytes(L->f, L->part_nrm);
+    int units = 0;
+    int e = slab_units(threads, smem, &units);
+    if (e) return cuda_fail((cudaError_t)e, "row-slab occupancy query");
+    if (units < G) return ISF_OK;
+    *fits = true;
+    SlabArgs A{};
+    A.part = reinterpret_cast<const int32_t*>(L->dev + lay.part_off);
+    A.roff = reinterpret_cast<const int32_t*>(L->dev + lay.roff_off);
+    A.xbuf = reinterpret_cast<uint32_t*>(L->dev + lay.xbuf_off);
+    A.done = reinterpret_cast<unsigned*>(L->dev + lay.done_off);
+    A.series = reinterpret_cast<unsigned long long*>(L->dev + lay.series_off);
+    A.nrm = L->part_nrm;
+    for (int64_t done = 0; done < nsweeps;) {
+        const int64_t n = std::min<int64_t>(nsweeps - done, kSeriesChunk);
+        A.s = sweep_args(L, n);
+        e = launch_slabs(A, G, threads, smem, s);
+        if (e) return cuda_fail((cudaError_t)e, "row-slab sweep kernel launch");
+        e = launch_fold_series(A.s, A.series, s);
+        if (e) return cuda_fail((cudaError_t)e, "series fold launch");
+        advance_cursor(L, n);
+        done += n;
+    }
+    L->last_path = ISF_PATH_SLABS; L->last_ctas = G; L->last_threads = threads; L->last_sites = 32;
+    L->last = s;
+    return ISF_OK;
+}
+
+// Automatic choice for packed whole films: the row-slab kernel when a colour pass has more words
+// than one CTA of the global kernel takes (512) but at most a third of a word per thread of a
+// full-GPU launch of it; else the global kernel.  Measured on 64^2 to 4096^2 fractal films of
+// 6 layers: in that range the global kernel's sweep is its four grid barriers plus one round of
+// words (about 18.5 us) and the slab kernel's 13 to 18 us; from about 0.45 words per thread on
+// the global kernel is the faster one.
+static bool slabs_preferred(const isf_lattice* L) {
+    if (!L->lay.packed || L->f.slab || !L->f.items || L->roff_h.empty() || L->lay.L > kSlabMaxLayers) return false;
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int64_t words = sweep_items_per_pass(L->f);
+    return words > 512 && words * 3 <= (int64_t)sms * 512;
+}
+
 int isf_run_sweeps(isf_lattice* L, int64_t nsweeps, void* cuda_stream) {
     if (!L) return fail(ISF_ERR_ARG, "lattice is NULL");
     if (!L->nsteps) return fail(ISF_ERR_STATE, "no schedule set");
@@ -480,6 +587,14 @@ int isf_run_sweeps(isf_lattice* L, int64_t nsweeps, void* cuda_stream) {
     CUDA_TRY(cudaSetDevice(L->device), "cudaSetDevice");
     const SweepArgs a = sweep_args(L, nsweeps);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (L->path == ISF_PATH_SLABS || (L->path == ISF_PATH_AUTO && slabs_preferred(L))) {
+        bool fits = false;
+        int rc = run_slabs(L, nsweeps, s, &fits);
+        if (rc) return rc;
+        if (fits) return ISF_OK;
+        if (L->path == ISF_PATH_SLABS)
+            return fail(ISF_ERR_ARG, "the row-slab path needs a packed whole film with word lists whose rows fit the CTAs' shared memory with this launch shape");
+    }
     bool launched = false;
     if (L->path != ISF_PATH_GLOBAL && !L->lay.packed) {
         ResPlan plan;
@@ -755,8 +870,10 @@ int isf_launch_info(isf_lattice* L, int32_t* path, int32_t* ctas, int32_t* threa
 }
 
 int isf_set_path(isf_lattice* L, int32_t path) {
-    if (!L || path < ISF_PATH_AUTO || path > ISF_PATH_RESIDENT) return fail(ISF_ERR_ARG, "bad arguments");
+    if (!L || path < ISF_PATH_AUTO || path > ISF_PATH_SLABS) return fail(ISF_ERR_ARG, "bad arguments");
     if (path == ISF_PATH_RESIDENT && L->lay.packed) return fail(ISF_ERR_ARG, "the resident path holds int8 films only");
+    if (path == ISF_PATH_SLABS && (!L->lay.packed || L->f.slab || !L->f.items || L->lay.L > kSlabMaxLayers))
+        return fail(ISF_ERR_ARG, "the row-slab path holds packed whole films of at most 16 layers with word lists only");
     L->path = path;
     return ISF_OK;
 }

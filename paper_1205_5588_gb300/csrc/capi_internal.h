@@ -47,6 +47,11 @@ struct isf_lattice {
     int32_t path = ISF_PATH_AUTO;
     int32_t last_path = 0, last_ctas = 0, last_threads = 0;   // shape of the last sweep launch
     int32_t last_sites = 0;
+    // row-slab kernel (packed whole films with word lists): host copy of the row offsets of the
+    // row-major lists, and the row partition last uploaded (part_G CTAs, at most part_nrm rows each)
+    std::vector<int32_t> roff_h;
+    std::vector<int32_t> part_h;
+    int32_t part_G = 0, part_nrm = 0;
     // row slab of a larger film (f.slab): whole-film rows [y0, y1) are this film's own rows,
     // local row 0 is whole-film row ya; the next colour pass isf_run_pass expects
     int32_t slab_y0 = 0, slab_y1 = 0, slab_ya = 0, slab_rows = 0;

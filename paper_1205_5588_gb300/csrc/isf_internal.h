@@ -39,6 +39,10 @@ constexpr int kFlagSlot = 51;
 // drawn and the decisions are the same either way.
 constexpr uint32_t kFlagAlwaysDraw = 1u;
 constexpr int kMaxThreads = 1024;
+constexpr int kMaxSlabCTAs = 192;     // row-slab kernel: most CTAs (one per SM)
+constexpr int kSeriesChunk = 4096;    // row-slab kernel: most sweeps per launch
+constexpr int kSlabMaxLayers = 16;    // row-slab kernel: most layers
+constexpr uint32_t kSlabStaticSmem = 3072;   // row-slab kernel: its static shared arrays, rounded up
 
 // Neighbour offsets of one (colour, layer parity) class: 9 unshifted, then 3 shifted by `sgn`
 // columns (-1 or +1).  Units: bytes (int8) or words (packed).
@@ -131,16 +135,25 @@ struct Layout {
     size_t heights_off, state_off, total_bytes;
     size_t items_off;             // packed: occupied-word lists, 4 x items_cap uint32
     int64_t items_cap;            // packed: L * Rh * nw (0 for int8)
+    // packed: row-slab kernel scratch (kernels_slabs.cu)
+    size_t roff_off;              // 4 x L x (Rh + 1) int32: first list entry of each (colour, z, row)
+    size_t part_off;              // (kMaxSlabCTAs + 1) int32: first row of each CTA
+    size_t done_off;              // kMaxSlabCTAs x 32 uint32: boundary words published, one line per CTA
+    size_t xbuf_off;              // slab_gmax x 4 x 2 rows of L x nw uint32 (stride rounded up to 4): boundary rows
+    size_t series_off;            // kSeriesChunk x 2 uint64: dM, dB per sweep
+    int32_t slab_gmax;            // most CTAs the slab kernel may use (min(kMaxSlabCTAs, Rh))
 };
 
 int make_layout(int32_t rows, int32_t cols, int32_t layers, uint32_t flags, Layout* out,
                 const char** why);
 int check_colouring(const Layout& lay, const char** why);
 // Occupied-word lists of a packed film (host, from the height map): out gets 4 * items_cap
-// entries (colour c's list at c * items_cap, n[c] of them); false when an entry's fields do not
-// fit 32 bits (the kernels then walk every word).
+// entries (colour c's list at c * items_cap, n[c] of them, in (z, row, word) order); false when
+// an entry's fields do not fit 32 bits (the kernels then walk every word).  Rows [jlo, jhi)
+// only.  roff (optional): 4 x L x (Rh + 1) offsets, the words of colour c, layer z, row j being
+// entries [roff[(c L + z)(Rh + 1) + j], roff[(c L + z)(Rh + 1) + j + 1]).
 bool build_word_items(const Layout& lay, const uint8_t* heights, std::vector<uint32_t>& out, int32_t n[4],
-                      int32_t* wbits, int32_t* jbits, int32_t jlo, int32_t jhi);   // rows [jlo, jhi) only
+                      int32_t* wbits, int32_t* jbits, int32_t jlo, int32_t jhi, std::vector<int32_t>* roff = nullptr);
 void fill_neighbour_classes(const Layout& lay, DevFilm* f);
 
 // Host threshold table (schedule.cpp): thr[n+12][s'] for one step, plus the gate slot.
@@ -164,6 +177,31 @@ int launch_surface_domains(const DevFilm& f, const uint8_t* dev_img, int* dev_sc
 int launch_philox_blocks(uint64_t seed, uint32_t stream_id, uint64_t sweep, uint32_t q0,
                          int64_t nblocks, uint32_t* dev_out, void* stream);
 int sweep_max_ctas_for(const DevFilm& f, int threads, int* max_ctas);  // co-resident CTAs
+
+// Row slabs in shared memory (kernels_slabs.cu): a packed film split by rows over G co-resident
+// CTAs, each holding its rows and one halo row on each side in shared memory.  A CTA updates its
+// two boundary rows first in every colour pass and publishes them (xbuf, done); at the end of
+// the pass it imports its neighbours' boundary rows of that colour into its halo.  No grid
+// barrier: a CTA waits only for its two neighbours.
+struct alignas(16) SlabArgs {
+    SweepArgs s;
+    const int32_t* part;          // [G + 1] first colour row of each CTA (part[G] = Rh)
+    const int32_t* roff;          // [4][L][Rh + 1] first list entry of each (colour, z, row)
+    uint32_t* xbuf;               // [G][4][2] rows of L x nw words, stride rounded up to 4: boundary rows
+                                  // (side 0: the first own row, 1: the last)
+    unsigned* done;               // [G][32] 1 + boundary words each CTA has published this launch
+    unsigned long long* series;   // [nsweeps][2] per-sweep dM, dB (two's complement sums)
+    int32_t nrm;                  // most rows of any CTA
+    int32_t pad_;
+};
+// Shared memory of a CTA of the row-slab kernel whose largest slab has nrm rows.
+uint32_t slab_smem_bytes(const DevFilm& f, int nrm);
+// Co-resident CTAs of the row-slab kernel with this block size and shared memory (0 when the
+// shared memory does not fit).
+int slab_units(int threads, uint32_t smem, int* units);
+int launch_slabs(const SlabArgs& a, int G, int threads, uint32_t smem, void* stream);
+// Folds a launch's per-sweep series into M, B, the step sums and records (one thread).
+int launch_fold_series(const SweepArgs& a, const unsigned long long* series, void* stream);
 
 // Cluster-resident sweeps (kernels_resident.cu): the film sits in the shared memory of one
 // thread-block cluster of K CTAs (row slabs), int8 layout, any boundary flags.

@@ -163,29 +163,6 @@ __device__ __forceinline__ void block_generic(const DevFilm& f, int c, int z, in
 }
 
 // ---- packed layout: one thread per 32-site word --------------------------------------------
-__device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t& s, uint32_t& cy) {
-    s = a ^ b ^ c;
-    cy = (a & b) | (c & (a ^ b));
-}
-// bit-sliced population count of 12 one-bit inputs per lane -> 4 bit-planes
-__device__ __forceinline__ void popcount12(const uint32_t* x, uint32_t& b0, uint32_t& b1, uint32_t& b2, uint32_t& b3) {
-    uint32_t s0, c0, s1, c1, s2, c2, s3, c3;
-    full_add(x[0], x[1], x[2], s0, c0);
-    full_add(x[3], x[4], x[5], s1, c1);
-    full_add(x[6], x[7], x[8], s2, c2);
-    full_add(x[9], x[10], x[11], s3, c3);
-    uint32_t t0, d0;
-    full_add(s0, s1, s2, t0, d0);
-    b0 = t0 ^ s3;
-    const uint32_t d1 = t0 & s3;
-    uint32_t e0, f0, e1, f1;
-    full_add(c0, c1, c2, e0, f0);
-    full_add(c3, d0, d1, e1, f1);
-    b1 = e0 ^ e1;
-    const uint32_t f2 = e0 & e1;
-    full_add(f0, f1, f2, b2, b3);
-}
-
 // Loads of one packed word position: the own spin and occupancy words and the 12 neighbour
 // spin and occupancy words (three of them shifted by one column, completed from the word before
 // or after), reduced to the neighbours' up bits and their bit-sliced vacancy count V.  NARROW:
@@ -240,98 +217,8 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
         philox10_xn<4>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u_first);
     }
     if (!O) return;             // no occupied site in the word (tested after the loads are issued)
-    // X = n + 12 = 2 * (#up) + (#vacant) over the 12 neighbours, 5 bit-planes
-    uint32_t U0, U1, U2, U3;
-    popcount12(up, U0, U1, U2, U3);
-    const uint32_t V0 = V[0], V1 = V[1], V2 = V[2], V3 = V[3];
-    uint32_t X[5], k2, k3;
-    X[0] = V0;
-    X[1] = U0 ^ V1;
-    const uint32_t k1 = U0 & V1;
-    full_add(U1, V2, k1, X[2], k2);
-    full_add(U2, V3, k2, X[3], k3);
-    X[4] = U3 ^ k3;
-    // transpose the 8 planes {0, 0, X0..X4, S}: byte k of P[r] = 4 x the table index
-    // (up << 5) | X of lane 8k + r, i.e. its byte offset in the table
-    uint32_t P[8] = {0u, 0u, X[0], X[1], X[2], X[3], X[4], S};
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const uint32_t t = ((P[p] >> 4) ^ P[p + 4]) & 0x0F0F0F0Fu;
-        P[p + 4] ^= t;
-        P[p] ^= t << 4;
-    }
-#pragma unroll
-    for (int p = 0; p < 8; p += (p & 1) ? 3 : 1) {   // p = 0, 1, 4, 5
-        const uint32_t t = ((P[p] >> 2) ^ P[p + 2]) & 0x33333333u;
-        P[p + 2] ^= t;
-        P[p] ^= t << 2;
-    }
-#pragma unroll
-    for (int p = 0; p < 8; p += 2) {
-        const uint32_t t = ((P[p] >> 1) ^ P[p + 1]) & 0x55555555u;
-        P[p + 1] ^= t;
-        P[p] ^= t << 1;
-    }
-    uint32_t F = 0;
-    // two halves of 16 lanes (4 Philox blocks each): all 16 lookups first, then the half's four
-    // blocks interleaved when any of its lanes needs a word
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-        uint32_t thr[16];
-        bool need = false;
-#pragma unroll
-        for (int vv = 0; vv < 4; ++vv) {
-            const int v = 4 * g + vv;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const uint32_t t = *reinterpret_cast<const uint32_t*>(
-                    reinterpret_cast<const uint8_t*>(tab) + ((P[4 * (v & 1) + b] >> (8 * (v >> 1))) & 0xFFu));
-                thr[4 * vv + b] = t;
-            }
-        }
-        // the second half draws its words only if a lane needs one (unless the step's table
-        // says nearly every group does)
-        if (g) {
-            if (always_draw) {
-                need = true;
-            } else {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) need |= needs_word(thr[i]);
-            }
-        }
-        uint4 u[4];
-        if (g == 0) {
-#pragma unroll
-            for (int vv = 0; vv < 4; ++vv) u[vv] = u_first[vv];
-        } else {
-#pragma unroll
-            for (int vv = 0; vv < 4; ++vv) u[vv] = make_uint4(0, 0, 0, 0);
-            if (need) philox10_xn<4>(q0 + 4, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u);
-        }
-#pragma unroll
-        for (int vv = 0; vv < 4; ++vv) {
-            uint32_t lanes = 0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if (metropolis_accept(word_of(u[vv], b), thr[4 * vv + b])) lanes |= 1u << b;
-            if (GATE) lanes = gate_block(lanes, gthr, q0 + 4 * g + vv, sweep, f.key0, f.key1);
-            F |= lanes << (4 * (4 * g + vv));
-        }
-    }
-    F &= O;                     // vacant sites never flip
-    if (F) {
-        f.sp[base] = S ^ F;
-        const uint32_t Fu = F & S, Fd = F & ~S;        // flipped up -> down, down -> up
-        const int nu = __popc(Fu), nd = __popc(Fd);
-        int xu = 0, xd = 0;
-#pragma unroll
-        for (int p = 0; p < 5; ++p) {
-            xu += __popc(X[p] & Fu) << p;
-            xd += __popc(X[p] & Fd) << p;
-        }
-        dM += -2 * (nu - nd);
-        dB += -2 * ((xu - 12 * nu) - (xd - 12 * nd));
-    }
+    const uint32_t F = packed_decide<GATE>(S, O, up, V, q0, sweep, tab, gthr, always_draw, f.key0, f.key1, u_first, dM, dB);
+    if (F) f.sp[base] = S ^ F;
 }
 
 // First work item of this thread in a pass.  Warps are numbered across CTAs first (warp w of

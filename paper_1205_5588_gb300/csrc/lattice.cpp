@@ -71,7 +71,17 @@ int make_layout(int32_t rows, int32_t cols, int32_t layers, uint32_t flags, Layo
     L.state_off = align256(L.heights_off + (size_t)rows * (size_t)cols);
     L.items_cap = packed ? (int64_t)layers * L.Rh * L.nw : 0;
     L.items_off = align256(L.state_off + sizeof(FilmState));
-    L.total_bytes = align256(L.items_off + (size_t)4 * (size_t)L.items_cap * sizeof(uint32_t));
+    size_t end = L.items_off + (size_t)4 * (size_t)L.items_cap * sizeof(uint32_t);
+    if (packed) {
+        L.slab_gmax = std::min(kMaxSlabCTAs, L.Rh);
+        L.roff_off = align256(end);
+        L.part_off = align256(L.roff_off + (size_t)4 * (size_t)layers * (size_t)(L.Rh + 1) * sizeof(int32_t));
+        L.done_off = align256(L.part_off + (size_t)(kMaxSlabCTAs + 1) * sizeof(int32_t));
+        L.xbuf_off = align256(L.done_off + (size_t)kMaxSlabCTAs * 32 * sizeof(uint32_t));
+        L.series_off = align256(L.xbuf_off + (size_t)L.slab_gmax * 8 * (((size_t)layers * (size_t)L.nw + 3) & ~(size_t)3) * sizeof(uint32_t));
+        end = L.series_off + (size_t)kSeriesChunk * 2 * sizeof(unsigned long long);
+    }
+    L.total_bytes = align256(end);
     *out = L;
     return ISF_OK;
 }
@@ -83,7 +93,7 @@ static int bits_for(int64_t n) {
 }
 
 bool build_word_items(const Layout& lay, const uint8_t* heights, std::vector<uint32_t>& out, int32_t n[4],
-                      int32_t* wbits, int32_t* jbits, int32_t jlo, int32_t jhi) {
+                      int32_t* wbits, int32_t* jbits, int32_t jlo, int32_t jhi, std::vector<int32_t>* roff) {
     const int wb = bits_for(lay.nw), jb = bits_for(lay.Rh), zb = bits_for(lay.L);
     if (wb + jb + zb > 32) return false;
     out.assign((size_t)4 * (size_t)lay.items_cap, 0u);
@@ -95,18 +105,22 @@ bool build_word_items(const Layout& lay, const uint8_t* heights, std::vector<uin
             uint8_t& t = top[((size_t)y * 2 + (x & 1)) * lay.nw + ((x >> 1) >> 5)];
             t = std::max(t, heights[(size_t)y * lay.C + x]);
         }
+    if (roff) roff->assign((size_t)4 * (size_t)lay.L * (size_t)(lay.Rh + 1), 0);
     for (int c = 0; c < 4; ++c) {
         uint32_t* dst = out.data() + (size_t)c * lay.items_cap;
         int64_t k = 0;
         for (int z = 0; z < lay.L; ++z) {
             const int zp = z & 1, px = (c & 1) ^ zp, py = ((c >> 1) & 1) ^ zp;
-            for (int j = std::max(jlo, 0); j < std::min(jhi, lay.Rh); ++j) {
+            int32_t* ro = roff ? roff->data() + ((size_t)c * lay.L + z) * (lay.Rh + 1) : nullptr;
+            for (int j = 0; j < lay.Rh; ++j) {
+                if (ro) ro[j] = (int32_t)k;
                 const int y = 2 * j + py;
-                if (y >= lay.R) continue;
+                if (j < jlo || j >= jhi || y >= lay.R) continue;
                 for (int w = 0; w < lay.nw; ++w)
                     if (z < top[((size_t)y * 2 + px) * lay.nw + w])
                         dst[k++] = ((uint32_t)z << (jb + wb)) | ((uint32_t)j << wb) | (uint32_t)w;
             }
+            if (ro) ro[lay.Rh] = (int32_t)k;
         }
         n[c] = (int32_t)k;
     }

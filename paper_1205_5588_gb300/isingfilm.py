@@ -14,7 +14,7 @@ import numpy as np
 from . import build as _build
 
 PERIODIC_X, PERIODIC_Y, PERIODIC_Z, PACKED = 1, 2, 4, 8
-PATHS = {"auto": 0, "global": 1, "resident": 2}
+PATHS = {"auto": 0, "global": 1, "resident": 2, "slabs": 3}
 INIT = {"random": 0, "up": 1, "down": 2}
 STATUS = {0: "ISF_OK", -1: "ISF_ERR_ARG", -2: "ISF_ERR_OOM", -3: "ISF_ERR_CUDA", -4: "ISF_ERR_COLOURING",
           -5: "ISF_ERR_SCHEDULE", -6: "ISF_ERR_TIMEOUT", -7: "ISF_ERR_STATE"}
@@ -365,7 +365,7 @@ class Lattice:
         p, c, t, w = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         _check(lib.isf_launch_info(self._h, C.byref(p), C.byref(c), C.byref(t)), "launch_info")
         _check(lib.isf_launch_item_sites(self._h, C.byref(w)), "launch_item_sites")
-        return {"path": {0: None, 1: "global", 2: "resident"}[p.value], "ctas": c.value, "threads": t.value,
+        return {"path": {0: None, 1: "global", 2: "resident", 3: "slabs"}[p.value], "ctas": c.value, "threads": t.value,
                 "item_sites": w.value}
 
     def set_path(self, path="auto"):
