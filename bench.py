@@ -488,11 +488,13 @@ def profile_case(args):
     s = spec["schedule"]
     lat = I.Lattice(spec["heights"], spec["layers"], periodic_x=spec["periodic_x"], periodic_y=spec["periodic_y"],
                     packed=spec["packed"], seed=spec["seed"], init=spec["init"])
+    if args.path != "auto":
+        lat.set_path(args.path)
     if args.ctas or args.threads:
         lat.set_launch(args.ctas, args.threads)
     lat.set_schedule(s["T"][:1], s["h"][:1], [0], [args.profile_sweeps], J=spec["J"])
     lat.run(-1)
-    print("profile case done, M_last =", lat.observables()[0]["M_last"])
+    print("profile case done, M_last =", lat.observables()[0]["M_last"], "launch", lat.launch_info())
     lat.close()
 
 
@@ -516,6 +518,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--ref-sweeps", type=int, default=0)
+    ap.add_argument("--path", default="auto", choices=["auto", "global", "resident", "slabs"],
+                    help="sweep kernel of the profiling case")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling case: one launch of this many sweeps at the first schedule step, no JSON")
     args = ap.parse_args()
