@@ -389,11 +389,11 @@ def measure_served(I, rate=200.0, duration=5.0, seed=5, pool=24, budget_gb=40.0,
 # recorded value (None: not captured for the current sources).
 NCU_TRAFFIC = {
     "fractal256": {"sources": ["kernels_resident.cu", "sweep_core.cuh", "device_common.cuh"],
-                   "sources_sha256": "431af0d2e9ceaffe84ef07562c19b522bdaaa546806c9de0aaf5796d5dbd83cd",
-                   "bytes_per_launch": 1255680.0},
+                   "sources_sha256": "f36ebbab1af1299b3c47ee70d982d7ff64c27ea00cc75d4b1f52033a3fddf4b6",
+                   "bytes_per_launch": 1309952.0},
     "fractal2048": {"sources": ["kernels_sweep.cu", "sweep_core.cuh", "device_common.cuh"],
-                    "sources_sha256": "77b38e941175838cf991b7ed29a098322ca61dee801a15e40a839e662592a46b",
-                    "bytes_per_launch": 11376128.0 + 2352128.0},
+                    "sources_sha256": "e725b0d9e6ea9c7cd3bbee4ce7dc34d56594a97627305addba604eda973c0ad8",
+                    "bytes_per_launch": 11446528.0 + 2158336.0},
 }
 
 

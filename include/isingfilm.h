@@ -178,7 +178,7 @@ int isf_read_trace(isf_lattice* lat, int64_t* host_out, int64_t max_pairs, int64
  *     CTA's band of rows (plus one halo row on each side) in its shared memory, the boundary
  *     rows exchanged through device memory after each colour pass, and each CTA waiting for
  *     its two neighbours only (the same row decomposition, over the whole GPU); launches of at
- *     most 4096 sweeps, each followed by a one-thread fold of the per-sweep M, B series;
+ *     most 2048 sweeps, each followed by a one-thread fold of the per-sweep M, B series;
  *   ISF_PATH_AUTO (default): int8 films resident when the film fits, else global; packed films
  *     slabs when a colour pass has more than 512 and at most (SMs x 512) / 3 occupied words
  *     (films of roughly 100^2 to 900^2 sites per layer), else global.

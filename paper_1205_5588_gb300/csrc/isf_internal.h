@@ -40,7 +40,7 @@ constexpr int kFlagSlot = 51;
 constexpr uint32_t kFlagAlwaysDraw = 1u;
 constexpr int kMaxThreads = 1024;
 constexpr int kMaxSlabCTAs = 192;     // row-slab kernel: most CTAs (one per SM)
-constexpr int kSeriesChunk = 4096;    // row-slab kernel: most sweeps per launch
+constexpr int kSeriesChunk = 2048;    // row-slab kernel: most sweeps per launch
 constexpr int kSlabMaxLayers = 16;    // row-slab kernel: most layers
 constexpr uint32_t kSlabStaticSmem = 3072;   // row-slab kernel: its static shared arrays, rounded up
 
@@ -138,7 +138,7 @@ struct Layout {
     // packed: row-slab kernel scratch (kernels_slabs.cu)
     size_t roff_off;              // 4 x L x (Rh + 1) int32: first list entry of each (colour, z, row)
     size_t part_off;              // (kMaxSlabCTAs + 1) int32: first row of each CTA
-    size_t done_off;              // kMaxSlabCTAs x 32 uint32: boundary words published, one line per CTA
+    size_t done_off;              // slab_gmax x 32 uint32: boundary words published, one line per CTA
     size_t xbuf_off;              // slab_gmax x 4 x 2 rows of L x nw uint32 (stride rounded up to 4): boundary rows
     size_t series_off;            // kSeriesChunk x 2 uint64: dM, dB per sweep
     int32_t slab_gmax;            // most CTAs the slab kernel may use (min(kMaxSlabCTAs, Rh))

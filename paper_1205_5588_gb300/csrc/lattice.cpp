@@ -77,7 +77,7 @@ int make_layout(int32_t rows, int32_t cols, int32_t layers, uint32_t flags, Layo
         L.roff_off = align256(end);
         L.part_off = align256(L.roff_off + (size_t)4 * (size_t)layers * (size_t)(L.Rh + 1) * sizeof(int32_t));
         L.done_off = align256(L.part_off + (size_t)(kMaxSlabCTAs + 1) * sizeof(int32_t));
-        L.xbuf_off = align256(L.done_off + (size_t)kMaxSlabCTAs * 32 * sizeof(uint32_t));
+        L.xbuf_off = align256(L.done_off + (size_t)L.slab_gmax * 32 * sizeof(uint32_t));
         L.series_off = align256(L.xbuf_off + (size_t)L.slab_gmax * 8 * (((size_t)layers * (size_t)L.nw + 3) & ~(size_t)3) * sizeof(uint32_t));
         end = L.series_off + (size_t)kSeriesChunk * 2 * sizeof(unsigned long long);
     }

@@ -55,12 +55,13 @@ def test_slab_gate_parity(I):
 
 
 def test_slab_runs_longer_than_one_launch(I):
-    """4100 sweeps: two launches (4096 + 4), each folded after it; and a run cut in odd chunks."""
+    """4100 sweeps: three launches (2048 + 2048 + 4), each folded after it; and a run cut in odd
+    chunks."""
     spec = film(W.fractal_heights(16, 40, 0.7, 1, 2, seed=2), 2, seed=6)
     sched = W.schedule([2.5, 3.5, 1.0], [0.4, -0.4, 0.0], [50, 0, 10], [2000, 2030, 10])
     o = run_oracle(spec, sched)
     assert_same_run(run_gpu(I, spec, sched, path="slabs"), o)
-    assert_same_run(run_gpu(I, spec, sched, path="slabs", chunks=[1, 4095, 3, 1]), o)
+    assert_same_run(run_gpu(I, spec, sched, path="slabs", chunks=[1, 2047, 2049, 3]), o)
 
 
 def test_slabs_and_global_interleave(I):
