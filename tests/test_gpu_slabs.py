@@ -125,6 +125,23 @@ def test_automatic_path_choice(I, R, L, want):
     lat.close()
 
 
+def test_slab_layer_limit(I):
+    """16 layers run on the row-slab kernel; 17 are refused there, and the automatic choice then
+    takes the global kernel."""
+    sched = W.schedule([3.0, 5.0], [0.5, -0.5], [1, 1], [3, 3])
+    spec = film(W.fractal_heights(40, 64, 0.7, 4, 16, seed=12), 16, seed=3)
+    assert_same_run(run_gpu(I, spec, sched, path="slabs"), run_oracle(spec, sched))
+    H = W.fractal_heights(300, 300, 0.7, 4, 17, seed=13)
+    lat = I.Lattice(H, 17, packed=True)
+    with pytest.raises(I.IsfError) as e:
+        lat.set_path("slabs")
+    assert e.value.code == -1
+    lat.set_schedule([3.0], [0.0], [0], [1])
+    lat.run(-1)
+    assert lat.launch_info()["path"] == "global"
+    lat.close()
+
+
 def test_slab_path_errors(I):
     H = W.fractal_heights(12, 10, 0.7, 1, 3, seed=2)
     lat = I.Lattice(H, 3)                                    # int8
