@@ -187,11 +187,13 @@ int isf_read_trace(isf_lattice* lat, int64_t* host_out, int64_t max_pairs, int64
 enum { ISF_PATH_AUTO = 0, ISF_PATH_GLOBAL = 1, ISF_PATH_RESIDENT = 2, ISF_PATH_SLABS = 3 };
 int isf_set_path(isf_lattice* lat, int32_t path);
 
-/* Launch shape override: ctas = CTAs of the global kernel or cluster size (1..16) of the
- * resident kernel (0 = automatic); threads per CTA (0 = automatic; else a multiple of 32 up to
- * 1024; the global kernel uses at most 256; the resident kernel 64..512 with 16-site items and
- * 64..768 with 8-site items, one warp of which folds the observables and takes no sites).
- * Trajectories do not depend on it. */
+/* Launch shape override: ctas = CTAs of the global kernel, cluster size (1..16) of the resident
+ * kernel, or row bands of the row-slab kernel (one CTA each, at most min(192, colour rows), all
+ * co-resident) (0 = automatic); threads per CTA (0 = automatic; else a multiple of 32 up to 1024;
+ * the global kernel uses at most 512; the row-slab kernel 64..512; the resident kernel 64..512
+ * with 16-site items and 64..768 with 8-site items, one warp of which folds the observables and
+ * takes no sites).  A shape the row-slab kernel cannot run makes isf_run_sweeps fail with
+ * ISF_ERR_ARG when that path is forced.  Trajectories do not depend on it. */
 int isf_set_launch(isf_lattice* lat, int32_t ctas, int32_t threads);
 
 /* Sites per work item of the resident kernel: 16, 8, or 0 = automatic (8 when a quarter or more
@@ -206,8 +208,9 @@ int isf_set_item_sites(isf_lattice* lat, int32_t sites);
  * also report it as ISF_ERR_STATE. */
 int isf_debug_checks(uint64_t* out4);
 
-/* Shape of the last isf_run_sweeps launch: path (ISF_PATH_GLOBAL / ISF_PATH_RESIDENT / ISF_PATH_SLABS, 0 before
- * any launch), CTAs (global) or cluster size (resident), threads per CTA.  No device work. */
+/* Shape of the last isf_run_sweeps launch: path (ISF_PATH_GLOBAL / ISF_PATH_RESIDENT /
+ * ISF_PATH_SLABS, 0 before any launch), CTAs (global), cluster size (resident) or row bands
+ * (slabs), threads per CTA.  No device work. */
 int isf_launch_info(isf_lattice* lat, int32_t* path, int32_t* ctas, int32_t* threads);
 /* Sites per work item of the last isf_run_sweeps launch (16 or 8 resident, 16 int8 global, 32
  * packed global; 0 before any launch).  No device work. */
