@@ -524,10 +524,12 @@ static int run_slabs(isf_lattice* L, int64_t nsweeps, cudaStream_t s, bool* fits
     const int64_t cap = ((int64_t)optin - kSlabStaticSmem - (int64_t)slab_smem_bytes(L->f, 0)) / per_row;
     if (cap < 1 || cap * G < lay.Rh) return ISF_OK;
     if (G != L->part_G) {
+        // a new partition: the film's earlier launches (which read the old one) must be done
+        int rc = sync_film(L);
+        if (rc) return rc;
         L->part_nrm = slab_partition(L, G, (int)std::min<int64_t>(cap, lay.Rh), L->part_h);
-        // pageable source: the copy is staged before cudaMemcpyAsync returns
-        CUDA_TRY(cudaMemcpyAsync(L->dev + lay.part_off, L->part_h.data(), L->part_h.size() * sizeof(int32_t),
-                                 cudaMemcpyHostToDevice, s), "copy row partition");
+        CUDA_TRY(cudaMemcpy(L->dev + lay.part_off, L->part_h.data(), L->part_h.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice), "copy row partition");
         L->part_G = G;
     }
     const uint32_t smem = slab_smem_bytes(L->f, L->part_nrm);
