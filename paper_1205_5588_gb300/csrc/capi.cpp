@@ -118,6 +118,7 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
     if (lay.packed) {
         f.sp = reinterpret_cast<uint32_t*>(L->dev);
         f.op = f.sp + 4 * lay.csw;
+        f.vq = reinterpret_cast<const uint32_t*>(L->dev + lay.vq_off);
     } else {
         f.s8 = L->dev;
     }

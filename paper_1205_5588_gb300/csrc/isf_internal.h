@@ -68,6 +68,9 @@ struct DevFilm {
     // packed layout
     uint32_t* sp;                 // spin bit-planes
     uint32_t* op;                 // occupancy bit-planes
+    const uint32_t* vq;           // per word position (same indexing as sp / op) 4 words, 16-byte
+                                  // aligned: the bit-sliced count of vacant neighbours (1s, 2s,
+                                  // 4s, 8s) of each of its 32 sites; fixed by the occupancy
     int64_t Wp, lsw, csw;         // row pitch, layer stride, colour stride (words)
     int32_t nw;                   // words per row
     int32_t pad_;
@@ -135,6 +138,7 @@ struct Layout {
     size_t heights_off, state_off, total_bytes;
     size_t items_off;             // packed: occupied-word lists, 4 x items_cap uint32
     int64_t items_cap;            // packed: L * Rh * nw (0 for int8)
+    size_t vq_off;                // packed: 4 x csw x 16 B, the vacant-neighbour counts (DevFilm.vq)
     // packed: row-slab kernel scratch (kernels_slabs.cu)
     size_t roff_off;              // 4 x L x (Rh + 1) int32: first list entry of each (colour, z, row)
     size_t part_off;              // (kMaxSlabCTAs + 1) int32: first row of each CTA

@@ -6,6 +6,7 @@
 
 #include "../../include/isingfilm.h"
 #include "device_common.cuh"
+#include "sweep_core.cuh"
 
 namespace isf {
 
@@ -103,6 +104,38 @@ __global__ void k_init_packed(DevFilm f, int init, const int8_t* src) {
         }
         f.sp[t] = sbits;
         f.op[t] = obits;
+    }
+}
+
+// Bit-sliced count of vacant neighbours of every site of every packed word position (a word's
+// 32 sites, 4 planes: 1s, 2s, 4s, 8s), from the occupancy planes: the same 12 neighbour words
+// as a colour pass reads (three shifted by one column), each vacancy one count.  Occupancy never
+// changes, so the sweep kernels read these 16 bytes instead of 12 neighbour occupancy words and
+// their 12-input count.  Halo and padding positions get zeros (never read as a site).
+__global__ void k_init_vq(DevFilm f) {
+    const int64_t total = (int64_t)4 * (f.L + 2) * (f.Rh + 2) * f.Wp;
+    uint32_t* vq = const_cast<uint32_t*>(f.vq);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = t / f.Wp;
+        const int wd = (int)(t - row * f.Wp);
+        const int jj = (int)(row % (f.Rh + 2));
+        const int64_t r2 = row / (f.Rh + 2);
+        const int zz = (int)(r2 % (f.L + 2));
+        const int c = (int)(r2 / (f.L + 2));
+        const int z = zz - 1, j = jj - 1, w = wd - 1;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (z >= 0 && z < f.L && j >= 0 && j < f.Rh && w >= 0 && w < f.nw) {
+            const NbrClass& nc = f.nb[c][z & 1];
+            const uint32_t* o = f.op + t;
+            uint32_t vac[12];
+            for (int k = 0; k < 9; ++k) vac[k] = ~o[nc.off[k]];
+            for (int k = 9; k < 12; ++k)
+                vac[k] = nc.sgn < 0 ? ~__funnelshift_l(o[nc.off[k] - 1], o[nc.off[k]], 1)
+                                    : ~__funnelshift_r(o[nc.off[k]], o[nc.off[k] + 1], 1);
+            popcount12(vac, v.x, v.y, v.z, v.w);
+        }
+        *reinterpret_cast<uint4*>(vq + 4 * t) = v;
     }
 }
 
@@ -259,8 +292,10 @@ __global__ void k_philox_blocks(uint64_t seed, uint32_t stream_id, uint64_t swee
 int launch_init(const DevFilm& f, int init, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (f.packed) {
+        if (!f.vq) return (int)cudaErrorInvalidValue;
         const int64_t total = (int64_t)4 * (f.L + 2) * (f.Rh + 2) * f.Wp;
         k_init_packed<<<grid_for(total), kThreads, 0, s>>>(f, init, nullptr);
+        k_init_vq<<<grid_for(total), kThreads, 0, s>>>(f);
     } else {
         const int64_t total = (int64_t)4 * (f.L + 2) * (f.Rh + 2) * (f.P / 4);
         k_init_int8<<<grid_for(total), kThreads, 0, s>>>(f, init, nullptr);

@@ -163,10 +163,11 @@ __device__ __forceinline__ void block_generic(const DevFilm& f, int c, int z, in
 }
 
 // ---- packed layout: one thread per 32-site word --------------------------------------------
-// Loads of one packed word position: the own spin and occupancy words and the 12 neighbour
-// spin and occupancy words (three of them shifted by one column, completed from the word before
-// or after), reduced to the neighbours' up bits and their bit-sliced vacancy count V.  NARROW:
-// every offset fits 32 bits, so each address is one 32-bit offset from the own word's pointer.
+// Loads of one packed word position: the own spin and occupancy words, the 12 neighbour spin
+// words (three of them shifted by one column, completed from the word before or after) as the
+// neighbours' up bits, and the position's precomputed bit-sliced count V of vacant neighbours.
+// NARROW: every offset fits 32 bits, so each address is one 32-bit offset from the own word's
+// pointer.
 template <bool NARROW>
 __device__ __forceinline__ void packed_loads(const DevFilm& f, const NbrClass& nc, int64_t base, uint32_t& S,
                                              uint32_t& O, uint32_t up[12], uint32_t V[4]) {
@@ -184,17 +185,11 @@ __device__ __forceinline__ void packed_loads(const DevFilm& f, const NbrClass& n
 #pragma unroll
         for (int k = 9; k < 12; ++k) up[k] = __funnelshift_r(spb[off(k)], spb[off(k) + 1], 1);
     }
-    uint32_t vac[12];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) vac[k] = ~opb[off(k)];
-    if (nc.sgn < 0) {
-#pragma unroll
-        for (int k = 9; k < 12; ++k) vac[k] = ~__funnelshift_l(opb[off(k) - 1], opb[off(k)], 1);
-    } else {
-#pragma unroll
-        for (int k = 9; k < 12; ++k) vac[k] = ~__funnelshift_r(opb[off(k)], opb[off(k) + 1], 1);
-    }
-    popcount12(vac, V[0], V[1], V[2], V[3]);
+    const uint4 v = *reinterpret_cast<const uint4*>(f.vq + 4 * base);
+    V[0] = v.x;
+    V[1] = v.y;
+    V[2] = v.z;
+    V[3] = v.w;
 }
 
 template <bool GATE, bool NARROW>
