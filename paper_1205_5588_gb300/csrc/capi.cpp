@@ -118,7 +118,6 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
     if (lay.packed) {
         f.sp = reinterpret_cast<uint32_t*>(L->dev);
         f.op = f.sp + 4 * lay.csw;
-        f.vq = reinterpret_cast<const uint32_t*>(L->dev + lay.vq_off);
     } else {
         f.s8 = L->dev;
     }
@@ -138,6 +137,10 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
         L->roff_h.clear();
     }
     if (lay.packed) f.narrow = (4 * lay.csw + 2 * lay.lsw) < ((int64_t)1 << 31) ? 1 : 0;
+    if (f.items && f.narrow) {
+        f.ient = reinterpret_cast<const uint32_t*>(L->dev + lay.ient_off);
+        f.ivq = reinterpret_cast<const uint32_t*>(L->dev + lay.ivq_off);
+    }
 
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     auto bail = [&](int code) { isf_lattice_destroy(L); return code; };
@@ -158,6 +161,10 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
     if (e != cudaSuccess) return bail(cuda_fail(e, "copy heights"));
     int ke = launch_init(f, init, s);
     if (ke) return bail(cuda_fail((cudaError_t)ke, "init kernel"));
+    if (f.ient) {
+        ke = launch_init_entries(f, s);
+        if (ke) return bail(cuda_fail((cudaError_t)ke, "word-list entries kernel"));
+    }
 
     long long red[4];
     rc = recompute(L, s, red);
@@ -562,11 +569,11 @@ static int run_slabs(isf_lattice* L, int64_t nsweeps, cudaStream_t s, bool* fits
 }
 
 // Automatic choice for packed whole films: the row-slab kernel when a colour pass has more words
-// than one CTA of the global kernel takes (512) but at most a third of a word per thread of a
+// than one CTA of the global kernel takes (512) but at most a fifth of a word per thread of a
 // full-GPU launch of it; else the global kernel.  Measured on 64^2 to 4096^2 fractal films of
 // 6 layers: in that range the global kernel's sweep is its four grid barriers plus one round of
-// words (about 18.5 us) and the slab kernel's 13 to 18 us; from about 0.45 words per thread on
-// the global kernel is the faster one.
+// words (about 17 us) and the slab kernel's 13 to 16 us; from about a quarter of a word per
+// thread on the global kernel is the faster one.
 static bool slabs_preferred(const isf_lattice* L) {
     if (!L->lay.packed || L->f.slab || !L->f.items || L->roff_h.empty() || L->lay.L > kSlabMaxLayers) return false;
     int dev = 0, sms = 1;
@@ -575,7 +582,7 @@ static bool slabs_preferred(const isf_lattice* L) {
         return false;
     }
     const int64_t words = sweep_items_per_pass(L->f);
-    return words > 512 && words * 3 <= (int64_t)sms * 512;
+    return words > 512 && words * 5 <= (int64_t)sms * 512;
 }
 
 int isf_run_sweeps(isf_lattice* L, int64_t nsweeps, void* cuda_stream) {

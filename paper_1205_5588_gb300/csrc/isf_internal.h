@@ -68,9 +68,7 @@ struct DevFilm {
     // packed layout
     uint32_t* sp;                 // spin bit-planes
     uint32_t* op;                 // occupancy bit-planes
-    const uint32_t* vq;           // per word position (same indexing as sp / op) 4 words, 16-byte
-                                  // aligned: the bit-sliced count of vacant neighbours (1s, 2s,
-                                  // 4s, 8s) of each of its 32 sites; fixed by the occupancy
+
     int64_t Wp, lsw, csw;         // row pitch, layer stride, colour stride (words)
     int32_t nw;                   // words per row
     int32_t pad_;
@@ -81,6 +79,12 @@ struct DevFilm {
     int32_t nitems[4];
     int32_t item_wbits, item_jbits;
     int32_t narrow;               // packed: 1 if every neighbour offset and index fits 32 bits
+    // packed, narrow, with lists: per list entry (same indexing as items) the word index with the
+    // layer parity in bit 31 and the Philox counter (ient, 2 words), and the bit-sliced count of
+    // vacant neighbours (1s, 2s, 4s, 8s) of its 32 sites (ivq, 4 words, 16-byte aligned), both
+    // fixed by the occupancy; nullptr when not built
+    const uint32_t* ient;
+    const uint32_t* ivq;
     // row slab of a larger film (0: a whole film).  Local colour-row j is row (j + cj0) mod cRh
     // of the whole film (its Philox counters are the whole film's); the sweep kernels update
     // rows [jlo, jhi) only, the others are halo copies of the neighbouring slabs' rows.
@@ -138,7 +142,7 @@ struct Layout {
     size_t heights_off, state_off, total_bytes;
     size_t items_off;             // packed: occupied-word lists, 4 x items_cap uint32
     int64_t items_cap;            // packed: L * Rh * nw (0 for int8)
-    size_t vq_off;                // packed: 4 x csw x 16 B, the vacant-neighbour counts (DevFilm.vq)
+    size_t ient_off, ivq_off;     // packed: 4 x items_cap x 8 B and x 16 B (DevFilm.ient, ivq)
     // packed: row-slab kernel scratch (kernels_slabs.cu)
     size_t roff_off;              // 4 x L x (Rh + 1) int32: first list entry of each (colour, z, row)
     size_t part_off;              // (kMaxSlabCTAs + 1) int32: first row of each CTA
@@ -168,6 +172,8 @@ void derive_record(const StepRec& r, double T, double h, double J, long long n_o
 
 // Device launchers (kernels.cu); all return a cudaError_t as int.
 int launch_init(const DevFilm& f, int init, void* stream);
+// Fills f.ient and f.ivq from the word lists and the occupancy planes (packed, after launch_init).
+int launch_init_entries(const DevFilm& f, void* stream);
 int launch_recompute(const DevFilm& f, FilmState* st, void* stream);  // M, B, n_occ, bonds -> st->red
 int launch_sweeps(const SweepArgs& a, int ctas, int threads, void* stream);
 int launch_unpack(const DevFilm& f, int8_t* dev_out, void* stream);

@@ -107,35 +107,37 @@ __global__ void k_init_packed(DevFilm f, int init, const int8_t* src) {
     }
 }
 
-// Bit-sliced count of vacant neighbours of every site of every packed word position (a word's
-// 32 sites, 4 planes: 1s, 2s, 4s, 8s), from the occupancy planes: the same 12 neighbour words
-// as a colour pass reads (three shifted by one column), each vacancy one count.  Occupancy never
-// changes, so the sweep kernels read these 16 bytes instead of 12 neighbour occupancy words and
-// their 12-input count.  Halo and padding positions get zeros (never read as a site).
-__global__ void k_init_vq(DevFilm f) {
-    const int64_t total = (int64_t)4 * (f.L + 2) * (f.Rh + 2) * f.Wp;
-    uint32_t* vq = const_cast<uint32_t*>(f.vq);
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = t / f.Wp;
-        const int wd = (int)(t - row * f.Wp);
-        const int jj = (int)(row % (f.Rh + 2));
-        const int64_t r2 = row / (f.Rh + 2);
-        const int zz = (int)(r2 % (f.L + 2));
-        const int c = (int)(r2 / (f.L + 2));
-        const int z = zz - 1, j = jj - 1, w = wd - 1;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (z >= 0 && z < f.L && j >= 0 && j < f.Rh && w >= 0 && w < f.nw) {
+// Per entry of the packed word lists: the word index (layer parity in bit 31) and Philox counter
+// the sweep kernels would derive from (z, row, word), and the bit-sliced count of vacant
+// neighbours of its 32 sites (1s, 2s, 4s, 8s) from the occupancy planes, i.e. the same 12
+// neighbour words a colour pass reads, three shifted by one column.  Occupancy never changes, so
+// the sweep kernels read these 24 bytes instead of decoding the entry and loading and counting
+// 12 neighbour occupancy words.
+__global__ void k_init_entries(DevFilm f) {
+    const int wb = f.item_wbits, jb = f.item_jbits;
+    const uint32_t wmask = (1u << wb) - 1u, jmask = (1u << jb) - 1u;
+    uint32_t* ent = const_cast<uint32_t*>(f.ient);
+    uint4* vq = reinterpret_cast<uint4*>(const_cast<uint32_t*>(f.ivq));
+    for (int c = 0; c < 4; ++c) {
+        const uint32_t* list = f.items + (int64_t)c * f.item_cap;
+        for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < f.nitems[c]; it += gridDim.x * blockDim.x) {
+            const uint32_t e = list[it];
+            const int z = (int)(e >> (jb + wb)), j = (int)((e >> wb) & jmask), w = (int)(e & wmask);
+            const int64_t base = addrw(f, c, z, j, w);
             const NbrClass& nc = f.nb[c][z & 1];
-            const uint32_t* o = f.op + t;
+            const uint32_t* o = f.op + base;
             uint32_t vac[12];
             for (int k = 0; k < 9; ++k) vac[k] = ~o[nc.off[k]];
             for (int k = 9; k < 12; ++k)
                 vac[k] = nc.sgn < 0 ? ~__funnelshift_l(o[nc.off[k] - 1], o[nc.off[k]], 1)
                                     : ~__funnelshift_r(o[nc.off[k]], o[nc.off[k] + 1], 1);
+            uint4 v;
             popcount12(vac, v.x, v.y, v.z, v.w);
+            const int64_t at = (int64_t)c * f.item_cap + it;
+            vq[at] = v;
+            ent[2 * at] = (uint32_t)base | ((uint32_t)(z & 1) << 31);
+            ent[2 * at + 1] = block_counter(f, c, z, j, 32 * w);
         }
-        *reinterpret_cast<uint4*>(vq + 4 * t) = v;
     }
 }
 
@@ -292,14 +294,21 @@ __global__ void k_philox_blocks(uint64_t seed, uint32_t stream_id, uint64_t swee
 int launch_init(const DevFilm& f, int init, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (f.packed) {
-        if (!f.vq) return (int)cudaErrorInvalidValue;
         const int64_t total = (int64_t)4 * (f.L + 2) * (f.Rh + 2) * f.Wp;
         k_init_packed<<<grid_for(total), kThreads, 0, s>>>(f, init, nullptr);
-        k_init_vq<<<grid_for(total), kThreads, 0, s>>>(f);
     } else {
         const int64_t total = (int64_t)4 * (f.L + 2) * (f.Rh + 2) * (f.P / 4);
         k_init_int8<<<grid_for(total), kThreads, 0, s>>>(f, init, nullptr);
     }
+    return (int)cudaGetLastError();
+}
+
+int launch_init_entries(const DevFilm& f, void* stream) {
+    if (!f.packed || !f.items || !f.narrow || !f.ient || !f.ivq) return (int)cudaErrorInvalidValue;
+    int64_t n = 0;
+    for (int c = 0; c < 4; ++c) n = n > f.nitems[c] ? n : f.nitems[c];
+    if (n == 0) return (int)cudaSuccess;
+    k_init_entries<<<grid_for(n), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(f);
     return (int)cudaGetLastError();
 }
 

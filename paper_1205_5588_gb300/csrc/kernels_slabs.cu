@@ -54,7 +54,9 @@ struct SlabGeom {
     int xs;                     // xbuf row stride: per rounded up to 4 words (16-byte rows)
 };
 
-// The 12 neighbours' up bits and the bit-sliced count of vacant neighbours of the word at `base`.
+// The 12 neighbours' up bits of the word at `base`; COUNT: also the bit-sliced count of vacant
+// neighbours V from their occupancy bits (else V is the word's precomputed count).
+template <bool COUNT>
 __device__ __forceinline__ void slab_loads(const uint2* film, int base, const int* off, int sgn, uint32_t& S,
                                            uint32_t& O, uint32_t up[12], uint32_t V[4]) {
     const uint2 own = film[base];
@@ -79,7 +81,7 @@ __device__ __forceinline__ void slab_loads(const uint2* film, int base, const in
             vac[k] = ~__funnelshift_r(a0.y, a1.y, 1);
         }
     }
-    popcount12(vac, V[0], V[1], V[2], V[3]);
+    if (COUNT) popcount12(vac, V[0], V[1], V[2], V[3]);
 }
 
 // Segment tables of one colour pass of this CTA's rows, in the (z, row, word) word lists:
@@ -313,7 +315,16 @@ __global__ void __launch_bounds__(kSlabBlock, 1) k_slabs(const __grid_constant__
                     const int jj = j - g.jr0 + 1;
                     const int at = c * g.cs + (z + 1) * g.ls + jj * g.Wp + w + 1;
                     uint32_t S, O, up[12], V[4];
-                    slab_loads(film, at, off_s[c][z & 1], sgn_s[c][z & 1], S, O, up, V);
+                    if (f.ivq) {
+                        const uint4 v = reinterpret_cast<const uint4*>(f.ivq)[(int64_t)c * f.item_cap + idx];
+                        V[0] = v.x;
+                        V[1] = v.y;
+                        V[2] = v.z;
+                        V[3] = v.w;
+                        slab_loads<false>(film, at, off_s[c][z & 1], sgn_s[c][z & 1], S, O, up, V);
+                    } else {
+                        slab_loads<true>(film, at, off_s[c][z & 1], sgn_s[c][z & 1], S, O, up, V);
+                    }
                     const uint32_t q0 = block_counter(f, c, z, j, 32 * w);
                     uint4 u_first[4];
                     philox10_xn<4>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u_first);

@@ -170,12 +170,11 @@ __device__ __forceinline__ void block_generic(const DevFilm& f, int c, int z, in
 // pointer.
 template <bool NARROW>
 __device__ __forceinline__ void packed_loads(const DevFilm& f, const NbrClass& nc, int64_t base, uint32_t& S,
-                                             uint32_t& O, uint32_t up[12], uint32_t V[4]) {
+                                             uint32_t& O, uint32_t up[12]) {
     const uint32_t* spb = f.sp + base;
-    const uint32_t* opb = f.op + base;
     auto off = [&](int k) -> int64_t { return NARROW ? (int64_t)(int32_t)nc.off[k] : nc.off[k]; };
     S = spb[0];
-    O = opb[0];
+    O = f.op[base];
 #pragma unroll
     for (int k = 0; k < 9; ++k) up[k] = spb[off(k)];
     if (nc.sgn < 0) {
@@ -185,25 +184,48 @@ __device__ __forceinline__ void packed_loads(const DevFilm& f, const NbrClass& n
 #pragma unroll
         for (int k = 9; k < 12; ++k) up[k] = __funnelshift_r(spb[off(k)], spb[off(k) + 1], 1);
     }
-    const uint4 v = *reinterpret_cast<const uint4*>(f.vq + 4 * base);
-    V[0] = v.x;
-    V[1] = v.y;
-    V[2] = v.z;
-    V[3] = v.w;
 }
 
-template <bool GATE, bool NARROW>
-__device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int j, int w,
-                                            unsigned long long sweep, const uint32_t* tab,
-                                            uint32_t gthr, bool always_draw, int& dM, int& dB, const uint4 (&pre)[4],
-                                            bool use_pre) {
-    const NbrClass& nc = f.nb[c][z & 1];
-    const int64_t base = addrw(f, c, z, j, w);
+// The bit-sliced count of vacant neighbours from the 12 neighbour occupancy words (for words
+// that have no precomputed entry).
+template <bool NARROW>
+__device__ __forceinline__ void packed_vacancies(const DevFilm& f, const NbrClass& nc, int64_t base, uint32_t V[4]) {
+    const uint32_t* opb = f.op + base;
+    auto off = [&](int k) -> int64_t { return NARROW ? (int64_t)(int32_t)nc.off[k] : nc.off[k]; };
+    uint32_t vac[12];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) vac[k] = ~opb[off(k)];
+    if (nc.sgn < 0) {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) vac[k] = ~__funnelshift_l(opb[off(k) - 1], opb[off(k)], 1);
+    } else {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) vac[k] = ~__funnelshift_r(opb[off(k)], opb[off(k) + 1], 1);
+    }
+    popcount12(vac, V[0], V[1], V[2], V[3]);
+}
+
+// One packed word at word index `base` of colour c (layer parity zp), Philox counter q0.  vq: its
+// precomputed vacant-neighbour count (VQ), else counted from the occupancy words.
+template <bool GATE, bool NARROW, bool VQ>
+__device__ __forceinline__ void word_packed_at(const DevFilm& f, int c, int zp, int64_t base, uint32_t q0,
+                                               const uint4* vq, unsigned long long sweep, const uint32_t* tab,
+                                               uint32_t gthr, bool always_draw, int& dM, int& dB,
+                                               const uint4 (&pre)[4], bool use_pre) {
+    const NbrClass& nc = f.nb[c][zp];
     uint32_t S, O, up[12], V[4];
-    packed_loads<NARROW>(f, nc, base, S, O, up, V);
+    packed_loads<NARROW>(f, nc, base, S, O, up);
+    if (VQ) {
+        const uint4 v = *vq;
+        V[0] = v.x;
+        V[1] = v.y;
+        V[2] = v.z;
+        V[3] = v.w;
+    } else {
+        packed_vacancies<NARROW>(f, nc, base, V);
+    }
     // the first half's four Philox blocks do not depend on the loads: drawn while they are in
     // flight (every pass starts all warps together, so nothing else would fill that wait)
-    const uint32_t q0 = block_counter(f, c, z, j, 32 * w);
     uint4 u_first[4];
     if (use_pre) {
 #pragma unroll
@@ -214,6 +236,15 @@ __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int 
     if (!O) return;             // no occupied site in the word (tested after the loads are issued)
     const uint32_t F = packed_decide<GATE>(S, O, up, V, q0, sweep, tab, gthr, always_draw, f.key0, f.key1, u_first, dM, dB);
     if (F) f.sp[base] = S ^ F;
+}
+
+template <bool GATE, bool NARROW>
+__device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int j, int w,
+                                            unsigned long long sweep, const uint32_t* tab,
+                                            uint32_t gthr, bool always_draw, int& dM, int& dB, const uint4 (&pre)[4],
+                                            bool use_pre) {
+    word_packed_at<GATE, NARROW, false>(f, c, z & 1, addrw(f, c, z, j, w), block_counter(f, c, z, j, 32 * w), nullptr,
+                                        sweep, tab, gthr, always_draw, dM, dB, pre, use_pre);
 }
 
 // First work item of this thread in a pass.  Warps are numbered across CTAs first (warp w of
@@ -238,6 +269,18 @@ __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned lo
         const int wb = f.item_wbits, jb = f.item_jbits;
         const uint32_t wmask = (1u << wb) - 1u, jmask = (1u << jb) - 1u;
         const int it0 = first_item(G, cta);
+        if (f.ient) {
+            // each entry's word index (layer parity in bit 31), Philox counter and vacant-neighbour
+            // count, precomputed
+            const uint2* ent = reinterpret_cast<const uint2*>(f.ient) + (int64_t)c * f.item_cap;
+            const uint4* vq = reinterpret_cast<const uint4*>(f.ivq) + (int64_t)c * f.item_cap;
+            for (int it = it0; it < n; it += stride) {
+                const uint2 pq = ent[it];
+                word_packed_at<GATE, true, true>(f, c, (int)(pq.x >> 31), (int64_t)(pq.x & 0x7FFFFFFFu), pq.y, vq + it,
+                                                 sweep, tab, gthr, always_draw, dM, dB, pre, have_pre && it == it0);
+            }
+            return;
+        }
         for (int it = it0; it < n; it += stride) {
             const uint32_t e = list[it];
             const bool use = have_pre && it == it0;
@@ -329,10 +372,15 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
                 const long long tn = c == 3 ? t + 1 : t;
                 const int it0 = first_item(G, cta);
                 if (tn < a.nsweeps && it0 < f.nitems[cn]) {
-                    const uint32_t e = f.items[(int64_t)cn * f.item_cap + it0];
-                    const int wb = f.item_wbits, jbits = f.item_jbits;
-                    const uint32_t qn = block_counter(f, cn, (int)(e >> (jbits + wb)), (int)((e >> wb) & ((1u << jbits) - 1u)),
-                                                      32 * (int)(e & ((1u << wb) - 1u)));
+                    uint32_t qn;
+                    if (f.ient) {
+                        qn = f.ient[2 * ((int64_t)cn * f.item_cap + it0) + 1];
+                    } else {
+                        const uint32_t e = f.items[(int64_t)cn * f.item_cap + it0];
+                        const int wb = f.item_wbits, jbits = f.item_jbits;
+                        qn = block_counter(f, cn, (int)(e >> (jbits + wb)), (int)((e >> wb) & ((1u << jbits) - 1u)),
+                                           32 * (int)(e & ((1u << wb) - 1u)));
+                    }
                     const unsigned long long sn = (unsigned long long)(a.sweep0 + tn + 1);
                     philox10_xn<4>(qn, (uint32_t)sn, (uint32_t)(sn >> 32), 0u, f.key0, f.key1, pf);
                     have_pf = true;

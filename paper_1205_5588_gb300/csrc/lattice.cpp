@@ -73,8 +73,9 @@ int make_layout(int32_t rows, int32_t cols, int32_t layers, uint32_t flags, Layo
     L.items_off = align256(L.state_off + sizeof(FilmState));
     size_t end = L.items_off + (size_t)4 * (size_t)L.items_cap * sizeof(uint32_t);
     if (packed) {
-        L.vq_off = align256(end);
-        end = L.vq_off + (size_t)4 * (size_t)L.csw * 16;
+        L.ient_off = align256(end);
+        L.ivq_off = align256(L.ient_off + (size_t)4 * (size_t)L.items_cap * 8);
+        end = L.ivq_off + (size_t)4 * (size_t)L.items_cap * 16;
         L.slab_gmax = std::min(kMaxSlabCTAs, L.Rh);
         L.roff_off = align256(end);
         L.part_off = align256(L.roff_off + (size_t)4 * (size_t)layers * (size_t)(L.Rh + 1) * sizeof(int32_t));

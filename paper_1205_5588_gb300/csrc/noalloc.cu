@@ -119,7 +119,6 @@ extern "C" int isf_run_noalloc(const uint8_t* heights, int32_t rows, int32_t col
     if (lay.packed) {
         f.sp = reinterpret_cast<uint32_t*>(base);
         f.op = f.sp + 4 * lay.csw;
-        f.vq = reinterpret_cast<const uint32_t*>(base + lay.vq_off);
     } else {
         f.s8 = base;
     }
