@@ -392,8 +392,8 @@ NCU_TRAFFIC = {
                    "sources_sha256": "f36ebbab1af1299b3c47ee70d982d7ff64c27ea00cc75d4b1f52033a3fddf4b6",
                    "bytes_per_launch": 1309952.0},
     "fractal2048": {"sources": ["kernels_sweep.cu", "sweep_core.cuh", "device_common.cuh"],
-                    "sources_sha256": "e725b0d9e6ea9c7cd3bbee4ce7dc34d56594a97627305addba604eda973c0ad8",
-                    "bytes_per_launch": 11446528.0 + 2158336.0},
+                    "sources_sha256": "b1c39ff4877599158e4994f6b00728b0aafd8eae77c7eea3cddb8a75e10749fa",
+                    "bytes_per_launch": 20983552.0 + 2446592.0},
 }
 
 
