@@ -86,7 +86,9 @@ typedef struct {
     double m, abs_m, e, chi, chi_abs, C;
 } isf_step_obs;
 
-/* Device bytes a lattice of this shape needs (spins, heights, state).  0 if invalid. */
+/* Device bytes a lattice of this shape needs (spins, heights, state; packed films also their
+ * occupied-word lists with a 24-byte record per entry and the row-slab kernel's scratch).  0 if
+ * invalid. */
 size_t isf_lattice_bytes(int32_t rows, int32_t cols, int32_t layers, uint32_t flags);
 
 /* Build a film on the current CUDA device from a host height map.
