@@ -79,10 +79,10 @@ struct DevFilm {
     int32_t nitems[4];
     int32_t item_wbits, item_jbits;
     int32_t narrow;               // packed: 1 if every neighbour offset and index fits 32 bits
-    // packed, narrow, with lists: per list entry (same indexing as items) the word index with the
-    // layer parity in bit 31 and the Philox counter (ient, 2 words), and the bit-sliced count of
-    // vacant neighbours (1s, 2s, 4s, 8s) of its 32 sites (ivq, 4 words, 16-byte aligned), both
-    // fixed by the occupancy; nullptr when not built
+    // packed with lists (only narrow films have them): per list entry (same indexing as items)
+    // the word index with the layer parity in bit 31 and the Philox counter (ient, 2 words), and
+    // the bit-sliced count of vacant neighbours (1s, 2s, 4s, 8s) of its 32 sites (ivq, 4 words,
+    // 16-byte aligned), both fixed by the occupancy; nullptr when there are no lists
     const uint32_t* ient;
     const uint32_t* ivq;
     // row slab of a larger film (0: a whole film).  Local colour-row j is row (j + cj0) mod cRh

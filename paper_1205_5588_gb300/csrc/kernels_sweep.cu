@@ -261,35 +261,19 @@ __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned lo
                                             ItemWalk w, unsigned G, unsigned cta, bool always_draw, int& dM, int& dB,
                                             const uint4 (&pre)[4], bool have_pre) {
     const int stride = (int)G * blockDim.x;
-    if (MODE == MODE_PACKED && f.items) {
-        // the colour's occupied words only, thread t taking entries t, t + stride, ...; the first
-        // one's first four Philox blocks may have been drawn before the pass (pre)
-        const uint32_t* list = f.items + (int64_t)c * f.item_cap;
+    if (MODE == MODE_PACKED && f.ient) {
+        // the colour's occupied words only, thread t taking entries t, t + stride, ...: each
+        // entry's word index (layer parity in bit 31), Philox counter and vacant-neighbour count
+        // are precomputed; the first one's first four Philox blocks may have been drawn before
+        // the pass (pre)
+        const uint2* ent = reinterpret_cast<const uint2*>(f.ient) + (int64_t)c * f.item_cap;
+        const uint4* vq = reinterpret_cast<const uint4*>(f.ivq) + (int64_t)c * f.item_cap;
         const int n = f.nitems[c];
-        const int wb = f.item_wbits, jb = f.item_jbits;
-        const uint32_t wmask = (1u << wb) - 1u, jmask = (1u << jb) - 1u;
         const int it0 = first_item(G, cta);
-        if (f.ient) {
-            // each entry's word index (layer parity in bit 31), Philox counter and vacant-neighbour
-            // count, precomputed
-            const uint2* ent = reinterpret_cast<const uint2*>(f.ient) + (int64_t)c * f.item_cap;
-            const uint4* vq = reinterpret_cast<const uint4*>(f.ivq) + (int64_t)c * f.item_cap;
-            for (int it = it0; it < n; it += stride) {
-                const uint2 pq = ent[it];
-                word_packed_at<GATE, true, true>(f, c, (int)(pq.x >> 31), (int64_t)(pq.x & 0x7FFFFFFFu), pq.y, vq + it,
-                                                 sweep, tab, gthr, always_draw, dM, dB, pre, have_pre && it == it0);
-            }
-            return;
-        }
         for (int it = it0; it < n; it += stride) {
-            const uint32_t e = list[it];
-            const bool use = have_pre && it == it0;
-            if (f.narrow)
-                word_packed<GATE, true>(f, c, (int)(e >> (jb + wb)), (int)((e >> wb) & jmask), (int)(e & wmask), sweep,
-                                        tab, gthr, always_draw, dM, dB, pre, use);
-            else
-                word_packed<GATE, false>(f, c, (int)(e >> (jb + wb)), (int)((e >> wb) & jmask), (int)(e & wmask), sweep,
-                                         tab, gthr, always_draw, dM, dB, pre, use);
+            const uint2 pq = ent[it];
+            word_packed_at<GATE, true, true>(f, c, (int)(pq.x >> 31), (int64_t)(pq.x & 0x7FFFFFFFu), pq.y, vq + it, sweep,
+                                             tab, gthr, always_draw, dM, dB, pre, have_pre && it == it0);
         }
         return;
     }
@@ -324,7 +308,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
     // colours of this launch: all four, or one colour pass of one sweep
     const int c_begin = a.pass_plus1 ? a.pass_plus1 - 1 : 0, c_end = a.pass_plus1 ? a.pass_plus1 : 4;
     // packed films with word lists on the grid path: the barrier is split (see grid_arrive)
-    const bool PREFETCH = MODE == MODE_PACKED && BAR == BAR_GRID && G > 1 && f.items != nullptr && !a.pass_plus1;
+    const bool PREFETCH = MODE == MODE_PACKED && BAR == BAR_GRID && G > 1 && f.ient != nullptr && !a.pass_plus1;
     uint4 pf[4];
     bool have_pf = false;
     int k = a.k0, pos = a.pos0;
@@ -372,15 +356,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
                 const long long tn = c == 3 ? t + 1 : t;
                 const int it0 = first_item(G, cta);
                 if (tn < a.nsweeps && it0 < f.nitems[cn]) {
-                    uint32_t qn;
-                    if (f.ient) {
-                        qn = f.ient[2 * ((int64_t)cn * f.item_cap + it0) + 1];
-                    } else {
-                        const uint32_t e = f.items[(int64_t)cn * f.item_cap + it0];
-                        const int wb = f.item_wbits, jbits = f.item_jbits;
-                        qn = block_counter(f, cn, (int)(e >> (jbits + wb)), (int)((e >> wb) & ((1u << jbits) - 1u)),
-                                           32 * (int)(e & ((1u << wb) - 1u)));
-                    }
+                    const uint32_t qn = f.ient[2 * ((int64_t)cn * f.item_cap + it0) + 1];
                     const unsigned long long sn = (unsigned long long)(a.sweep0 + tn + 1);
                     philox10_xn<4>(qn, (uint32_t)sn, (uint32_t)(sn >> 32), 0u, f.key0, f.key1, pf);
                     have_pf = true;
