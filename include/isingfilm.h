@@ -279,9 +279,10 @@ int isf_fold_series(int32_t nsteps, const double* T, const double* h, const int3
  * fit one CTA's shared memory are taken from a device queue by a persistent single-CTA kernel,
  * films that need a cluster by a persistent cluster kernel (cluster size K), and the other films
  * (bit-packed, periodic-column, or too large for a cluster) by persistent kernels that run each
- * with its state in device memory on one CTA (up to 2^20 lattice sites) or one cluster of 8 CTAs
- * (up to 2^24), all concurrently on forked streams; larger films run after them on the
- * multi-CTA global path.  Each film's
+ * with its state in device memory on one CTA (up to 2^20 lattice sites, and at most an even share
+ * of the whole batch's work per such CTA, so that no film finishes last on its own CTA) or one
+ * cluster of 8 CTAs (up to 2^24), all concurrently on forked streams; larger films run after
+ * them on the multi-CTA global path.  Each film's
  * trajectory is the one it has alone.  Asynchronous on cuda_stream; read each film with
  * isf_read_observables / isf_read_spins afterwards. */
 typedef struct isf_batch isf_batch;
@@ -305,7 +306,7 @@ int isf_batch_run_sweeps(isf_batch* batch, int64_t max_sweeps, void* cuda_stream
 /* Last run (12 int32): films in the single-CTA / cluster / multi-CTA global classes, CTAs and
  * clusters launched, cluster size, threads of the two resident kernels; then films in the
  * one-CTA global-memory class (bit-packed, periodic-column or over-sized int8 films of at most
- * 2^20 lattice sites) and CTAs launched for it; then films in the one-cluster (8 CTAs)
+ * 2^20 lattice sites and an even share of the work) and CTAs launched for it; then films in the one-cluster (8 CTAs)
  * global-memory class (the same kinds, up to 2^24 sites) and clusters launched for it. */
 int isf_batch_info(isf_batch* batch, int32_t* out12);
 void isf_batch_destroy(isf_batch* batch);

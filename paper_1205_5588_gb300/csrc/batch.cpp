@@ -331,6 +331,21 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
     const int tb = b->threads_b ? b->threads_b : kDefaultThreadsB;
     std::vector<Item> A, B, D, E;
     std::vector<isf_lattice*> C;
+    // a film in global memory takes one CTA (class D) only if its work is at most an even share
+    // of the whole batch's work per such CTA; a larger one would finish last on its own CTA, so it
+    // takes a cluster (class E)
+    double total_work = 0.0;
+    for (isf_lattice* L : b->films) {
+        int64_t n = sweeps_remaining(L);
+        if (max_sweeps > 0 && n > max_sweeps) n = max_sweeps;
+        if (n > 0) total_work += (double)n * L->lay.L * L->lay.Rh * L->lay.Ch;
+    }
+    int d_units = 0;
+    if (batch_global_units(kThreadsD, &d_units) || d_units < 1) {
+        cudaGetLastError();
+        d_units = 1;
+    }
+    const double d_limit = total_work / d_units;
     for (isf_lattice* L : b->films) {
         if (L->device != b->device) return fail(ISF_ERR_ARG, "all films of a batch must be on one device");
         int64_t n = sweeps_remaining(L);
@@ -342,7 +357,7 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
         const int64_t sites = (int64_t)L->lay.L * L->lay.R * L->lay.C;
         if (queueable && resident_plan(L->f, 1, ta, 16, &it.plan) == 0) A.push_back(it);
         else if (queueable && resident_plan(L->f, K, tb, 16, &it.plan) == 0) B.push_back(it);
-        else if (sites <= kMaxSitesD) D.push_back(it);
+        else if (sites <= kMaxSitesD && it.work <= d_limit) D.push_back(it);
         else if (sites <= kMaxSitesE) E.push_back(it);
         else C.push_back(L);
         cudaGetLastError();

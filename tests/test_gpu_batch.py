@@ -22,10 +22,10 @@ def mixed_films():
     shapes = [(40, 52, 3, {}), (64, 64, 2, {}), (17, 23, 5, {}), (96, 130, 4, {}),
               (200, 256, 4, {}),                     # needs a cluster
               (150, 310, 5, {}),                     # needs a cluster
-              (48, 64, 3, {"packed": True}),         # one CTA, global memory
-              (16, 16, 3, {"periodic_x": True, "periodic_y": True}),   # one CTA, global memory
+              (48, 64, 3, {"packed": True}),         # global memory: one CTA or a cluster by its share of the work
+              (16, 16, 3, {"periodic_x": True, "periodic_y": True}),   # one CTA, global memory (a tiny share)
               (8, 12, 2, {}), (33, 65, 6, {}),
-              (96, 200, 5, {"packed": True}),        # one CTA, global memory
+              (96, 200, 5, {"packed": True}),        # global memory: one CTA or a cluster by its share of the work
               (512, 1024, 3, {"packed": True, "short": True}),   # over 2^20 sites: a cluster, global memory
               (2000, 2000, 1, {"short": True})]      # int8, too large for a cluster's shared memory
     for i, (R, Cc, L, extra) in enumerate(shapes):
@@ -64,7 +64,9 @@ def test_batch_matches_oracle_and_solo(I, graph, tune):
     b.run()
     info = b.info()
     assert info["single_cta_films"] >= 5 and info["cluster_films"] >= 2, info
-    assert info["global_cta_films"] >= 3 and info["global_cluster_films"] >= 2, info
+    # a global-memory film takes one CTA only if its work is at most an even share of the batch's
+    # per CTA (here the two largest films hold most of the work): one CTA or a cluster each
+    assert info["global_cta_films"] >= 1 and info["global_cta_films"] + info["global_cluster_films"] == 5, info
     for f, lat in zip(films, lats):
         o = run_oracle(f, f["schedule"])
         assert_records_equal(lat.observables(), o["recs"])
