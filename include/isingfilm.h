@@ -296,9 +296,12 @@ int isf_batch_set_launch(isf_batch* batch, int32_t threads_single, int32_t clust
 /* on != 0: capture the queue upload and the two persistent launches in a CUDA graph once and
  * replay it on later runs with the same shape (the per-film arguments are refreshed each run). */
 int isf_batch_set_graph(isf_batch* batch, int32_t on);
-/* Autotuner: times short probe runs of the largest film of each class (copies, not the members)
- * over cluster sizes {8, 16} and threads {128, 256, 384, 512}; keeps the fastest per class,
- * cached per (device, class, layers, row and column size class) for the process. */
+/* Autotuner: times short probe runs (copies, not the members) over threads {128, 256, 384, 512}:
+ * of the largest single-CTA film, keeping the fastest threads; and, for cluster sizes {8, 16},
+ * of the largest cluster film that fits that size, keeping the (size, threads) with the least
+ * probe time x rounds of the queue (the films that fit, over the co-resident clusters; films
+ * that fit only 16 CTAs then run on the global-memory cluster kernel).  Probe times are cached
+ * per (device, class, size, threads, layers, row and column size class) for the process. */
 int isf_batch_tune(isf_batch* batch, void* cuda_stream);
 int isf_batch_run(isf_batch* batch, void* cuda_stream);
 /* As isf_batch_run, but every member advances at most max_sweeps sweeps (>= 1; -1 = to the end). */

@@ -178,6 +178,7 @@ struct TuneKey {
 };
 struct TuneVal {
     int K, threads;
+    double t;       // probe time, ms (negative: the shape does not run)
 };
 std::mutex g_tune_mu;
 std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
@@ -267,48 +268,79 @@ int isf_batch_set_graph(isf_batch* b, int32_t on) {
     return ISF_OK;
 }
 
+namespace {
+// Probe time of a film shape at (K, threads), cached per process (cls: 0 single CTA, 1 cluster).
+double cached_probe(const isf_lattice* L, int cls, int K, int threads, const std::string& dev, cudaStream_t s) {
+    const TuneKey key{dev, cls * 100 + K * 1000 + threads, L->lay.L, bucket(L->lay.Rh), bucket(L->lay.Ch)};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (auto& kv : g_tune_cache)
+            if (kv.first == key) return kv.second.t;
+    }
+    const double t = probe(L, K, threads, 20, s);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache.push_back({key, TuneVal{K, threads, t}});
+    return t;
+}
+}  // namespace
+
 int isf_batch_tune(isf_batch* b, void* cuda_stream) {
     if (!b) return fail(ISF_ERR_ARG, "batch is NULL");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const std::string dev = device_name();
-    // representative films: the largest of each class
-    const isf_lattice* rep[2] = {nullptr, nullptr};
-    double rep_work[2] = {0, 0};
+    const int ths[4] = {128, 256, 384, 512};
+    // single-CTA class: the threads that run its largest film fastest
+    const isf_lattice* rep0 = nullptr;
+    double rep0_work = 0;
+    std::vector<const isf_lattice*> cluster_films;
     for (isf_lattice* L : b->films) {
-        if (L->lay.packed) continue;
+        if (L->lay.packed || (L->lay.flags & ISF_PERIODIC_X)) continue;
         ResPlan p;
-        const int cls = resident_plan(L->f, 1, 0, 16, &p) == 0 ? 0 : (resident_plan(L->f, 16, 0, 16, &p) == 0 ? 1 : -1);
-        cudaGetLastError();
-        if (cls < 0) continue;
         const double w = (double)L->lay.L * L->lay.Rh * L->lay.Ch;
-        if (w > rep_work[cls]) { rep_work[cls] = w; rep[cls] = L; }
+        if (resident_plan(L->f, 1, 0, 16, &p) == 0) {
+            if (w > rep0_work) { rep0_work = w; rep0 = L; }
+        } else if (resident_plan(L->f, 16, 0, 16, &p) == 0) {
+            cluster_films.push_back(L);
+        }
+        cudaGetLastError();
     }
-    for (int cls = 0; cls < 2; ++cls) {
-        const isf_lattice* L = rep[cls];
-        if (!L) continue;
-        TuneKey key{dev, cls, L->lay.L, bucket(L->lay.Rh), bucket(L->lay.Ch)};
-        TuneVal best{cls ? kDefaultK : 1, cls ? kDefaultThreadsB : kDefaultThreadsA};
-        bool cached = false;
-        {
-            std::lock_guard<std::mutex> lock(g_tune_mu);
-            for (auto& kv : g_tune_cache)
-                if (kv.first == key) { best = kv.second; cached = true; }
+    if (rep0) {
+        double best_t = 1e300;
+        int best_th = kDefaultThreadsA;
+        for (int th : ths) {
+            const double t = cached_probe(rep0, 0, 1, th, dev, s);
+            if (t > 0 && t < best_t) { best_t = t; best_th = th; }
         }
-        if (!cached) {
-            double best_t = 1e300;
-            const int Ks[2] = {8, 16};
-            const int ths[4] = {128, 256, 384, 512};
-            for (int ki = 0; ki < (cls ? 2 : 1); ++ki)
-                for (int ti = 0; ti < 4; ++ti) {
-                    const int K = cls ? Ks[ki] : 1;
-                    const double t = probe(L, K, ths[ti], 20, s);
-                    if (t > 0 && t < best_t) { best_t = t; best = TuneVal{K, ths[ti]}; }
-                }
-            std::lock_guard<std::mutex> lock(g_tune_mu);
-            g_tune_cache.push_back({key, best});
+        b->threads_a = best_th;
+    }
+    // cluster class: for each cluster size, the films that fit it queue over the co-resident
+    // clusters, so the size is chosen by (probe time of the largest film that fits) x (rounds of
+    // the queue); films that fit only the larger size run on the global-memory cluster kernel
+    double best_score = 1e300;
+    for (int K : {8, 16}) {
+        const isf_lattice* rep = nullptr;
+        double rep_work = 0;
+        int n_fit = 0;
+        for (const isf_lattice* L : cluster_films) {
+            ResPlan p;
+            if (resident_plan(L->f, K, 0, 16, &p) != 0) { cudaGetLastError(); continue; }
+            ++n_fit;
+            const double w = (double)L->lay.L * L->lay.Rh * L->lay.Ch;
+            if (w > rep_work) { rep_work = w; rep = L; }
         }
-        if (cls == 0) b->threads_a = best.threads;
-        else { b->K_b = best.K; b->threads_b = best.threads; }
+        if (!rep) continue;
+        for (int th : ths) {
+            const double t = cached_probe(rep, 1, K, th, dev, s);
+            ResPlan p;
+            int units = 0;
+            if (t <= 0 || resident_plan(rep->f, K, th, 16, &p) != 0 || batch_units_possible(K, th, p.smem, &units) ||
+                units < 1) {
+                cudaGetLastError();
+                continue;
+            }
+            const double score = t * (double)((n_fit + units - 1) / units);
+            if (score < best_score) { best_score = score; b->K_b = K; b->threads_b = th; }
+        }
     }
     return set_last_error(ISF_OK, "");
 }
