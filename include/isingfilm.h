@@ -301,7 +301,7 @@ int isf_batch_set_graph(isf_batch* batch, int32_t on);
  * of the largest cluster film that fits that size, keeping the (size, threads) with the least
  * probe time x rounds of the queue (the films that fit, over the co-resident clusters; films
  * that fit only 16 CTAs then run on the global-memory cluster kernel).  Probe times are cached
- * per (device, class, size, threads, layers, row and column size class) for the process. */
+ * per (device, cluster size, threads, layers, row and column size class) for the process. */
 int isf_batch_tune(isf_batch* batch, void* cuda_stream);
 int isf_batch_run(isf_batch* batch, void* cuda_stream);
 /* As isf_batch_run, but every member advances at most max_sweeps sweeps (>= 1; -1 = to the end). */

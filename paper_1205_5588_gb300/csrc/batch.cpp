@@ -169,19 +169,18 @@ struct Item {
 };
 
 // ---- autotuner --------------------------------------------------------------------------------
+// A probe: a film shape (layers, row and column size classes) on a device at a launch shape
+// (cluster size K, threads); its time in ms, negative when the shape does not run.
 struct TuneKey {
     std::string dev;
-    int cls, L, rh_bucket, ch_bucket;
+    int K, threads, L, rh_bucket, ch_bucket;
     bool operator==(const TuneKey& o) const {
-        return dev == o.dev && cls == o.cls && L == o.L && rh_bucket == o.rh_bucket && ch_bucket == o.ch_bucket;
+        return dev == o.dev && K == o.K && threads == o.threads && L == o.L && rh_bucket == o.rh_bucket &&
+               ch_bucket == o.ch_bucket;
     }
 };
-struct TuneVal {
-    int K, threads;
-    double t;       // probe time, ms (negative: the shape does not run)
-};
 std::mutex g_tune_mu;
-std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
+std::vector<std::pair<TuneKey, double>> g_tune_cache;
 
 int bucket(int v) {
     int b = 1;
@@ -269,17 +268,17 @@ int isf_batch_set_graph(isf_batch* b, int32_t on) {
 }
 
 namespace {
-// Probe time of a film shape at (K, threads), cached per process (cls: 0 single CTA, 1 cluster).
-double cached_probe(const isf_lattice* L, int cls, int K, int threads, const std::string& dev, cudaStream_t s) {
-    const TuneKey key{dev, cls * 100 + K * 1000 + threads, L->lay.L, bucket(L->lay.Rh), bucket(L->lay.Ch)};
+// Probe time of a film's shape at (K, threads), cached for the process.
+double cached_probe(const isf_lattice* L, int K, int threads, const std::string& dev, cudaStream_t s) {
+    const TuneKey key{dev, K, threads, L->lay.L, bucket(L->lay.Rh), bucket(L->lay.Ch)};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         for (auto& kv : g_tune_cache)
-            if (kv.first == key) return kv.second.t;
+            if (kv.first == key) return kv.second;
     }
     const double t = probe(L, K, threads, 20, s);
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache.push_back({key, TuneVal{K, threads, t}});
+    g_tune_cache.push_back({key, t});
     return t;
 }
 }  // namespace
@@ -308,7 +307,7 @@ int isf_batch_tune(isf_batch* b, void* cuda_stream) {
         double best_t = 1e300;
         int best_th = kDefaultThreadsA;
         for (int th : ths) {
-            const double t = cached_probe(rep0, 0, 1, th, dev, s);
+            const double t = cached_probe(rep0, 1, th, dev, s);
             if (t > 0 && t < best_t) { best_t = t; best_th = th; }
         }
         b->threads_a = best_th;
@@ -330,7 +329,7 @@ int isf_batch_tune(isf_batch* b, void* cuda_stream) {
         }
         if (!rep) continue;
         for (int th : ths) {
-            const double t = cached_probe(rep, 1, K, th, dev, s);
+            const double t = cached_probe(rep, K, th, dev, s);
             ResPlan p;
             int units = 0;
             if (t <= 0 || resident_plan(rep->f, K, th, 16, &p) != 0 || batch_units_possible(K, th, p.smem, &units) ||
