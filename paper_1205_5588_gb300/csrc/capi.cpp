@@ -521,7 +521,8 @@ static int slab_partition(const isf_lattice* L, int G, int cap, std::vector<int3
 static int run_slabs(isf_lattice* L, int64_t nsweeps, cudaStream_t s, bool* fits) {
     *fits = false;
     const Layout& lay = L->lay;
-    if (!lay.packed || L->f.slab || !L->f.items || L->roff_h.empty() || lay.L > kSlabMaxLayers) return ISF_OK;
+    if (!lay.packed || L->f.slab || !L->f.items || !L->f.ivq || L->roff_h.empty() || lay.L > kSlabMaxLayers)
+        return ISF_OK;
     const int threads = L->threads ? L->threads : 512;
     if (threads % 32 || threads < 64 || threads > 512) return ISF_OK;
     int dev = 0, sms = 1, optin = 0;

@@ -9,7 +9,8 @@
 // (0: the row below the band, 1..nr: own rows, nr + 1: the row above) and word index ww
 // (0 and nw + 1: vacant padding), one uint2 {spin bits, occupancy bits} per 32-site word.  The
 // 12 neighbour offsets of each (colour, layer parity) class are the device-memory layout's with
-// these strides, so the word update is the global kernel's, reading shared memory.
+// these strides, so the word update is the global kernel's, reading shared memory; a word's
+// vacant-neighbour count comes from its list entry's precomputed record.
 //
 // Colour pass P (colour c = P mod 4) on CTA r:
 //   - the warps take r's occupied words of colour c 32 at a time from a shared counter, the two
@@ -54,34 +55,20 @@ struct SlabGeom {
     int xs;                     // xbuf row stride: per rounded up to 4 words (16-byte rows)
 };
 
-// The 12 neighbours' up bits of the word at `base`; COUNT: also the bit-sliced count of vacant
-// neighbours V from their occupancy bits (else V is the word's precomputed count).
-template <bool COUNT>
+// The word's own spin and occupancy words and the 12 neighbours' up bits (three of them shifted
+// by one column, completed from the word before or after).
 __device__ __forceinline__ void slab_loads(const uint2* film, int base, const int* off, int sgn, uint32_t& S,
-                                           uint32_t& O, uint32_t up[12], uint32_t V[4]) {
+                                           uint32_t& O, uint32_t up[12]) {
     const uint2 own = film[base];
     S = own.x;
     O = own.y;
-    uint32_t vac[12];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const uint2 v = film[base + off[k]];
-        up[k] = v.x;
-        vac[k] = ~v.y;
-    }
+    for (int k = 0; k < 9; ++k) up[k] = film[base + off[k]].x;
 #pragma unroll
     for (int k = 9; k < 12; ++k) {
-        const uint2 a0 = film[base + off[k]];
-        const uint2 a1 = film[base + off[k] + sgn];
-        if (sgn < 0) {
-            up[k] = __funnelshift_l(a1.x, a0.x, 1);
-            vac[k] = ~__funnelshift_l(a1.y, a0.y, 1);
-        } else {
-            up[k] = __funnelshift_r(a0.x, a1.x, 1);
-            vac[k] = ~__funnelshift_r(a0.y, a1.y, 1);
-        }
+        const uint32_t a0 = film[base + off[k]].x, a1 = film[base + off[k] + sgn].x;
+        up[k] = sgn < 0 ? __funnelshift_l(a1, a0, 1) : __funnelshift_r(a0, a1, 1);
     }
-    if (COUNT) popcount12(vac, V[0], V[1], V[2], V[3]);
 }
 
 // Segment tables of one colour pass of this CTA's rows, in the (z, row, word) word lists:
@@ -315,16 +302,12 @@ __global__ void __launch_bounds__(kSlabBlock, 1) k_slabs(const __grid_constant__
                     const int jj = j - g.jr0 + 1;
                     const int at = c * g.cs + (z + 1) * g.ls + jj * g.Wp + w + 1;
                     uint32_t S, O, up[12], V[4];
-                    if (f.ivq) {
-                        const uint4 v = reinterpret_cast<const uint4*>(f.ivq)[(int64_t)c * f.item_cap + idx];
-                        V[0] = v.x;
-                        V[1] = v.y;
-                        V[2] = v.z;
-                        V[3] = v.w;
-                        slab_loads<false>(film, at, off_s[c][z & 1], sgn_s[c][z & 1], S, O, up, V);
-                    } else {
-                        slab_loads<true>(film, at, off_s[c][z & 1], sgn_s[c][z & 1], S, O, up, V);
-                    }
+                    const uint4 v = reinterpret_cast<const uint4*>(f.ivq)[(int64_t)c * f.item_cap + idx];
+                    V[0] = v.x;
+                    V[1] = v.y;
+                    V[2] = v.z;
+                    V[3] = v.w;
+                    slab_loads(film, at, off_s[c][z & 1], sgn_s[c][z & 1], S, O, up);
                     const uint32_t q0 = block_counter(f, c, z, j, 32 * w);
                     uint4 u_first[4];
                     philox10_xn<4>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u_first);
