@@ -128,12 +128,14 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
         f.slab = 1;
         f.cRh = sw->cRh; f.cj0 = sw->cj0; f.jlo = sw->jlo; f.jhi = sw->jhi;
     }
-    // word lists (with their per-entry records) for packed films whose word indices and
-    // neighbour offsets fit 32 bits; the kernels walk every word of the others
-    if (lay.packed) f.narrow = (4 * lay.csw + 2 * lay.lsw) < ((int64_t)1 << 31) ? 1 : 0;
+    // item lists (with their per-entry records) for films whose indices and neighbour offsets
+    // fit 32 bits; the kernels walk every item of the others
+    f.narrow = lay.packed ? ((4 * lay.csw + 2 * lay.lsw) < ((int64_t)1 << 31) ? 1 : 0)
+                          : ((4 * lay.cs8 + 2 * lay.ls8) < ((int64_t)1 << 31) ? 1 : 0);
     std::vector<uint32_t> items;
-    if (lay.packed && f.narrow && build_word_items(lay, heights, items, f.nitems, &f.item_wbits, &f.item_jbits,
-                                                   sw ? sw->jlo : 0, sw ? sw->jhi : lay.Rh, sw ? nullptr : &L->roff_h)) {
+    if (f.narrow && build_word_items(lay, heights, items, f.nitems, &f.item_wbits, &f.item_jbits,
+                                     sw ? sw->jlo : 0, sw ? sw->jhi : lay.Rh,
+                                     (sw || !lay.packed) ? nullptr : &L->roff_h)) {
         f.items = reinterpret_cast<const uint32_t*>(L->dev + lay.items_off);
         f.item_cap = lay.items_cap;
     } else {
@@ -141,7 +143,7 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
     }
     if (f.items) {
         f.ient = reinterpret_cast<const uint32_t*>(L->dev + lay.ient_off);
-        f.ivq = reinterpret_cast<const uint32_t*>(L->dev + lay.ivq_off);
+        if (lay.packed) f.ivq = reinterpret_cast<const uint32_t*>(L->dev + lay.ivq_off);
     }
 
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);

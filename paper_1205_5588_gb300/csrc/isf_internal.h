@@ -72,17 +72,18 @@ struct DevFilm {
     int64_t Wp, lsw, csw;         // row pitch, layer stride, colour stride (words)
     int32_t nw;                   // words per row
     int32_t pad_;
-    // packed layout: per colour the words holding at least one occupied site, in (z, row,
-    // word) order, each (z << (jbits + wbits)) | (j << wbits) | w; nullptr when not built
+    // per colour the items (packed: 32-site words; int8: 16-site chunks) holding at least one
+    // occupied site, in (z, row, item) order, each (z << (jbits + wbits)) | (j << wbits) | w;
+    // nullptr when not built
     const uint32_t* items;        // [4][item_cap]
     int64_t item_cap;
     int32_t nitems[4];
     int32_t item_wbits, item_jbits;
-    int32_t narrow;               // packed: 1 if every neighbour offset and index fits 32 bits
-    // packed with lists (only narrow films have them): per list entry (same indexing as items)
-    // the word index with the layer parity in bit 31 and the Philox counter (ient, 2 words), and
-    // the bit-sliced count of vacant neighbours (1s, 2s, 4s, 8s) of its 32 sites (ivq, 4 words,
-    // 16-byte aligned), both fixed by the occupancy; nullptr when there are no lists
+    int32_t narrow;               // 1 if every neighbour offset and index (words / bytes) fits 32 bits
+    // with lists (only narrow films have them): per list entry (same indexing as items) the word
+    // index (packed) or byte offset (int8) with the layer parity in bit 31 and the Philox counter
+    // (ient, 2 words); packed: the bit-sliced count of vacant neighbours (1s, 2s, 4s, 8s) of its
+    // 32 sites (ivq, 4 words, 16-byte aligned); fixed by the occupancy; nullptr when absent
     const uint32_t* ient;
     const uint32_t* ivq;
     // row slab of a larger film (0: a whole film).  Local colour-row j is row (j + cj0) mod cRh
@@ -140,9 +141,10 @@ struct Layout {
     int64_t nw, Wp, lsw, csw;
     size_t spin_bytes;            // int8 array, or both bit-plane sets
     size_t heights_off, state_off, total_bytes;
-    size_t items_off;             // packed: occupied-word lists, 4 x items_cap uint32
-    int64_t items_cap;            // packed: L * Rh * nw (0 for int8)
-    size_t ient_off, ivq_off;     // packed: 4 x items_cap x 8 B and x 16 B (DevFilm.ient, ivq)
+    size_t items_off;             // occupied-item lists, 4 x items_cap uint32
+    int64_t items_cap;            // packed: L * Rh * nw; int8 with open boundaries: L * Rh * nck; else 0
+    size_t ient_off;              // 4 x items_cap x 8 B (DevFilm.ient)
+    size_t ivq_off;               // packed: 4 x items_cap x 16 B (DevFilm.ivq)
     // packed: row-slab kernel scratch (kernels_slabs.cu)
     size_t roff_off;              // 4 x L x (Rh + 1) int32: first list entry of each (colour, z, row)
     size_t part_off;              // (kMaxSlabCTAs + 1) int32: first row of each CTA

@@ -107,12 +107,12 @@ __global__ void k_init_packed(DevFilm f, int init, const int8_t* src) {
     }
 }
 
-// Per entry of the packed word lists: the word index (layer parity in bit 31) and Philox counter
-// the sweep kernels would derive from (z, row, word), and the bit-sliced count of vacant
-// neighbours of its 32 sites (1s, 2s, 4s, 8s) from the occupancy planes, i.e. the same 12
-// neighbour words a colour pass reads, three shifted by one column.  Occupancy never changes, so
-// the sweep kernels read these 24 bytes instead of decoding the entry and loading and counting
-// 12 neighbour occupancy words.
+// Per entry of the item lists: the word index (packed) or byte offset (int8) with the layer
+// parity in bit 31, and the Philox counter, which the sweep kernels would derive from (z, row,
+// item); packed films also the bit-sliced count of vacant neighbours of the word's 32 sites (1s,
+// 2s, 4s, 8s) from the occupancy planes, i.e. the same 12 neighbour words a colour pass reads,
+// three shifted by one column.  Occupancy never changes, so the sweep kernels read these records
+// instead of decoding the entry (and, packed, loading and counting 12 occupancy words).
 __global__ void k_init_entries(DevFilm f) {
     const int wb = f.item_wbits, jb = f.item_jbits;
     const uint32_t wmask = (1u << wb) - 1u, jmask = (1u << jb) - 1u;
@@ -123,6 +123,12 @@ __global__ void k_init_entries(DevFilm f) {
         for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < f.nitems[c]; it += gridDim.x * blockDim.x) {
             const uint32_t e = list[it];
             const int z = (int)(e >> (jb + wb)), j = (int)((e >> wb) & jmask), w = (int)(e & wmask);
+            const int64_t at = (int64_t)c * f.item_cap + it;
+            if (!f.packed) {    // int8: a 16-site chunk's byte offset and Philox counter
+                ent[2 * at] = (uint32_t)addr8(f, c, z, j, 16 * w) | ((uint32_t)(z & 1) << 31);
+                ent[2 * at + 1] = block_counter(f, c, z, j, 16 * w);
+                continue;
+            }
             const int64_t base = addrw(f, c, z, j, w);
             const NbrClass& nc = f.nb[c][z & 1];
             const uint32_t* o = f.op + base;
@@ -133,7 +139,6 @@ __global__ void k_init_entries(DevFilm f) {
                                     : ~__funnelshift_r(o[nc.off[k]], o[nc.off[k] + 1], 1);
             uint4 v;
             popcount12(vac, v.x, v.y, v.z, v.w);
-            const int64_t at = (int64_t)c * f.item_cap + it;
             vq[at] = v;
             ent[2 * at] = (uint32_t)base | ((uint32_t)(z & 1) << 31);
             ent[2 * at + 1] = block_counter(f, c, z, j, 32 * w);
@@ -304,7 +309,7 @@ int launch_init(const DevFilm& f, int init, void* stream) {
 }
 
 int launch_init_entries(const DevFilm& f, void* stream) {
-    if (!f.packed || !f.items || !f.narrow || !f.ient || !f.ivq) return (int)cudaErrorInvalidValue;
+    if (!f.items || !f.narrow || !f.ient || (f.packed && !f.ivq)) return (int)cudaErrorInvalidValue;
     int64_t n = 0;
     for (int c = 0; c < 4; ++c) n = n > f.nitems[c] ? n : f.nitems[c];
     if (n == 0) return (int)cudaSuccess;

@@ -100,17 +100,24 @@ __device__ __forceinline__ bool grid_wait(FilmState* st, unsigned G, unsigned ta
 }
 
 // ---- int8 layout, open boundaries: one thread per 16-site chunk of a colour row ------------
+// The chunk at byte offset `base` of colour c (layer parity zp), Philox counter q0.
+template <bool GATE>
+__device__ __forceinline__ void chunk_int8_at(const DevFilm& f, int c, int zp, int64_t base, uint32_t q0,
+                                              unsigned long long sweep, const uint32_t* tab, uint32_t gthr, int& dM,
+                                              int& dB) {
+    const NbrClass& nc = f.nb[c][zp];
+    uint8_t* own = f.s8 + base;
+    const uint8_t* nbp[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) nbp[k] = own + nc.off[k];
+    update_chunk16<GATE>(own, nbp, nc.sgn, q0, sweep, tab, gthr, f.key0, f.key1, 0, f.Ch, dM, dB);
+}
 template <bool GATE>
 __device__ __forceinline__ void chunk_int8(const DevFilm& f, int c, int z, int j, int ck,
                                            unsigned long long sweep, const uint32_t* tab,
                                            uint32_t gthr, int& dM, int& dB) {
-    const NbrClass& nc = f.nb[c][z & 1];
-    uint8_t* own = f.s8 + addr8(f, c, z, j, 16 * ck);
-    const uint8_t* nbp[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) nbp[k] = own + nc.off[k];
-    update_chunk16<GATE>(own, nbp, nc.sgn, block_counter(f, c, z, j, 16 * ck), sweep, tab, gthr,
-                         f.key0, f.key1, 16 * ck, f.Ch, dM, dB);
+    chunk_int8_at<GATE>(f, c, z & 1, addr8(f, c, z, j, 16 * ck), block_counter(f, c, z, j, 16 * ck), sweep, tab, gthr,
+                        dM, dB);
 }
 
 // ---- int8 layout, any boundary (periodic wraps): one thread per 4-site Philox block --------
@@ -274,6 +281,17 @@ __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned lo
             const uint2 pq = ent[it];
             word_packed_at<GATE, true, true>(f, c, (int)(pq.x >> 31), (int64_t)(pq.x & 0x7FFFFFFFu), pq.y, vq + it, sweep,
                                              tab, gthr, always_draw, dM, dB, pre, have_pre && it == it0);
+        }
+        return;
+    }
+    if (MODE == MODE_INT8 && f.ient) {
+        // the colour's chunks holding an occupied site, each with its precomputed byte offset
+        // (layer parity in bit 31) and Philox counter
+        const uint2* ent = reinterpret_cast<const uint2*>(f.ient) + (int64_t)c * f.item_cap;
+        const int n = f.nitems[c];
+        for (int it = first_item(G, cta); it < n; it += stride) {
+            const uint2 pq = ent[it];
+            chunk_int8_at<GATE>(f, c, (int)(pq.x >> 31), (int64_t)(pq.x & 0x7FFFFFFFu), pq.y, sweep, tab, gthr, dM, dB);
         }
         return;
     }
@@ -552,7 +570,7 @@ int launch_batch_cluster_global(const SweepArgs* films, int n, unsigned* next, i
 }
 
 int sweep_items_per_pass(const DevFilm& f) {
-    if (f.packed && f.items) return std::max(std::max(f.nitems[0], f.nitems[1]), std::max(f.nitems[2], f.nitems[3]));
+    if (f.items) return std::max(std::max(f.nitems[0], f.nitems[1]), std::max(f.nitems[2], f.nitems[3]));
     const int per_row = f.packed ? f.nw : ((f.flags & 7u) ? f.Qw : f.nck);
     return f.L * f.Rh * per_row;
 }

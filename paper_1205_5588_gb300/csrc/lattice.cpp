@@ -69,12 +69,15 @@ int make_layout(int32_t rows, int32_t cols, int32_t layers, uint32_t flags, Layo
     L.spin_bytes = packed ? (size_t)2 * 4 * (size_t)L.csw * 4 : (size_t)4 * (size_t)L.cs8;
     L.heights_off = align256(L.spin_bytes);
     L.state_off = align256(L.heights_off + (size_t)rows * (size_t)cols);
-    L.items_cap = packed ? (int64_t)layers * L.Rh * L.nw : 0;
+    // occupied-item lists: 32-site words of packed films, 16-site chunks of int8 films with open
+    // boundaries (periodic int8 films run the generic path, which walks every site)
+    L.items_cap = packed ? (int64_t)layers * L.Rh * L.nw : (per ? 0 : (int64_t)layers * L.Rh * L.nck);
     L.items_off = align256(L.state_off + sizeof(FilmState));
     size_t end = L.items_off + (size_t)4 * (size_t)L.items_cap * sizeof(uint32_t);
+    L.ient_off = align256(end);
+    end = L.ient_off + (size_t)4 * (size_t)L.items_cap * 8;
     if (packed) {
-        L.ient_off = align256(end);
-        L.ivq_off = align256(L.ient_off + (size_t)4 * (size_t)L.items_cap * 8);
+        L.ivq_off = align256(end);
         end = L.ivq_off + (size_t)4 * (size_t)L.items_cap * 16;
         L.slab_gmax = std::min(kMaxSlabCTAs, L.Rh);
         L.roff_off = align256(end);
@@ -97,15 +100,18 @@ static int bits_for(int64_t n) {
 
 bool build_word_items(const Layout& lay, const uint8_t* heights, std::vector<uint32_t>& out, int32_t n[4],
                       int32_t* wbits, int32_t* jbits, int32_t jlo, int32_t jhi, std::vector<int32_t>* roff) {
-    const int wb = bits_for(lay.nw), jb = bits_for(lay.Rh), zb = bits_for(lay.L);
+    // items of a colour row: 32-site words (packed) or 16-site chunks (int8)
+    const int per_row = lay.packed ? (int)lay.nw : (int)lay.nck, shift = lay.packed ? 5 : 4;
+    if (lay.items_cap == 0) return false;
+    const int wb = bits_for(per_row), jb = bits_for(lay.Rh), zb = bits_for(lay.L);
     if (wb + jb + zb > 32) return false;
     out.assign((size_t)4 * (size_t)lay.items_cap, 0u);
-    // tallest pixel among the 32 columns of each (row y, column parity, word w): a word of
-    // layer z holds an occupied site iff z < that height
-    std::vector<uint8_t> top((size_t)lay.R * 2 * lay.nw, 0);
+    // tallest pixel among the columns of each (row y, column parity, item w): an item of layer z
+    // holds an occupied site iff z < that height
+    std::vector<uint8_t> top((size_t)lay.R * 2 * per_row, 0);
     for (int y = 0; y < lay.R; ++y)
         for (int x = 0; x < lay.C; ++x) {
-            uint8_t& t = top[((size_t)y * 2 + (x & 1)) * lay.nw + ((x >> 1) >> 5)];
+            uint8_t& t = top[((size_t)y * 2 + (x & 1)) * per_row + ((x >> 1) >> shift)];
             t = std::max(t, heights[(size_t)y * lay.C + x]);
         }
     if (roff) roff->assign((size_t)4 * (size_t)lay.L * (size_t)(lay.Rh + 1), 0);
@@ -119,8 +125,8 @@ bool build_word_items(const Layout& lay, const uint8_t* heights, std::vector<uin
                 if (ro) ro[j] = (int32_t)k;
                 const int y = 2 * j + py;
                 if (j < jlo || j >= jhi || y >= lay.R) continue;
-                for (int w = 0; w < lay.nw; ++w)
-                    if (z < top[((size_t)y * 2 + px) * lay.nw + w])
+                for (int w = 0; w < per_row; ++w)
+                    if (z < top[((size_t)y * 2 + px) * per_row + w])
                         dst[k++] = ((uint32_t)z << (jb + wb)) | ((uint32_t)j << wb) | (uint32_t)w;
             }
             if (ro) ro[lay.Rh] = (int32_t)k;
