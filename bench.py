@@ -392,8 +392,8 @@ NCU_TRAFFIC = {
                    "sources_sha256": "f36ebbab1af1299b3c47ee70d982d7ff64c27ea00cc75d4b1f52033a3fddf4b6",
                    "bytes_per_launch": 1309952.0},
     "fractal2048": {"sources": ["kernels_sweep.cu", "sweep_core.cuh", "device_common.cuh"],
-                    "sources_sha256": "eef826b91c1d5a855d3d4d8622baf92ca9fbe4db9cd172210c23c1b1eb058937",
-                    "bytes_per_launch": 20988672.0 + 2140416.0},
+                    "sources_sha256": "1eaef32c6540c29532335150a443768566022045f45b69e381857ffcc1ad8d5d",
+                    "bytes_per_launch": 21053440.0 + 2549504.0},
 }
 
 
