@@ -369,7 +369,8 @@ class Lattice:
                 "item_sites": w.value}
 
     def set_path(self, path="auto"):
-        """'resident' (film in one cluster's shared memory), 'global', or 'auto'."""
+        """'resident' (int8 film in one cluster's shared memory), 'global' (film in device memory,
+        all SMs), 'slabs' (packed film in row bands, one per CTA, in shared memory) or 'auto'."""
         _check(lib.isf_set_path(self._h, PATHS[path]), "set_path")
 
     def save(self, path):
