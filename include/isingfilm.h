@@ -210,6 +210,18 @@ int isf_set_item_sites(isf_lattice* lat, int32_t sites);
  * also report it as ISF_ERR_STATE. */
 int isf_debug_checks(uint64_t* out4);
 
+/* The occupied-item lists the library keeps for a film of this shape (host only, no device
+ * work): per colour c the entries (z << (jbits + wbits)) | (j << wbits) | w, in (z, row, item)
+ * order, of the items holding an occupied site — 32-site words (ISF_PACKED) or 16-site chunks
+ * (int8 with open boundaries) of colour row j, layer z, where item w covers columns i (= x>>1)
+ * 32w..32w+31 or 16w..16w+15 (Sec. 3's rows of one colour; occupancy as in isf_lattice_create).
+ * heights: host, rows*cols; n_out[4]: entries per colour; out: 4 x cap uint32, colour c's list
+ * from out[c * cap]; cap >= layers * ceil(rows/2) * items per row; bits_out[2] = (wbits, jbits).
+ * Errors: ISF_ERR_ARG (bad shape or pointers, cap too small, a film without lists: periodic int8,
+ * or fields that do not fit 32 bits), ISF_ERR_COLOURING. */
+int isf_debug_item_lists(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, uint32_t flags,
+                         int32_t* n_out, uint32_t* out, int64_t cap, int32_t* bits_out);
+
 /* Shape of the last isf_run_sweeps launch: path (ISF_PATH_GLOBAL / ISF_PATH_RESIDENT /
  * ISF_PATH_SLABS, 0 before any launch), CTAs (global), cluster size (resident) or row bands
  * (slabs), threads per CTA.  No device work. */

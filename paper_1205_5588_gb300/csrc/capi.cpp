@@ -867,6 +867,29 @@ int isf_launch_item_sites(isf_lattice* L, int32_t* sites) {
     return ISF_OK;
 }
 
+int isf_debug_item_lists(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, uint32_t flags,
+                         int32_t* n_out, uint32_t* out, int64_t cap, int32_t* bits_out) {
+    if (!heights || !n_out || !out || !bits_out) return fail(ISF_ERR_ARG, "a pointer argument is NULL");
+    Layout lay;
+    const char* why = "";
+    int rc = make_layout(rows, cols, layers, flags, &lay, &why);
+    if (rc) return fail(rc, why);
+    if (lay.items_cap == 0) return fail(ISF_ERR_ARG, "this film has no item lists (periodic int8)");
+    if (cap < lay.items_cap) return fail(ISF_ERR_ARG, "cap is smaller than layers x colour rows x items per row");
+    std::vector<uint32_t> items;
+    int32_t n[4], wb = 0, jb = 0;
+    if (!build_word_items(lay, heights, items, n, &wb, &jb, 0, lay.Rh))
+        return fail(ISF_ERR_ARG, "the list entries' fields do not fit 32 bits");
+    for (int c = 0; c < 4; ++c) {
+        n_out[c] = n[c];
+        std::memcpy(out + (size_t)c * cap, items.data() + (size_t)c * lay.items_cap, (size_t)n[c] * sizeof(uint32_t));
+    }
+    bits_out[0] = wb;
+    bits_out[1] = jb;
+    g_err.clear();
+    return ISF_OK;
+}
+
 int isf_debug_checks(uint64_t* out4) {
     if (!out4) return fail(ISF_ERR_ARG, "out is NULL");
     unsigned long long v[4];

@@ -73,6 +73,8 @@ def _declare(lib):
         "isf_surface_domains": (C.c_int, [vp, i64p]),
         "isf_launch_info": (C.c_int, [vp, i32p, i32p, i32p]),
         "isf_set_item_sites": (C.c_int, [vp, C.c_int32]),
+        "isf_debug_item_lists": (C.c_int, [u8p, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, i32p,
+                                           C.POINTER(C.c_uint32), C.c_int64, i32p]),
         "isf_lattice_create_slab": (C.c_int, [u8p, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, C.c_uint64,
                                               C.c_int32, C.c_int32, C.c_int32, vp, C.POINTER(vp)]),
         "isf_slab_info": (C.c_int, [vp, i32p, C.POINTER(C.c_size_t), i64p]),
@@ -162,6 +164,21 @@ def flags_of(periodic_x=False, periodic_y=False, periodic_z=False, packed=False)
 
 def lattice_bytes(rows, cols, layers, flags) -> int:
     return int(lib.isf_lattice_bytes(rows, cols, layers, flags))
+
+
+def item_lists(heights, layers, flags=0) -> tuple[list[np.ndarray], int, int]:
+    """The occupied-item lists the library keeps for a film (host only): per colour an array of
+    entries (z << (jbits + wbits)) | (j << wbits) | w, and (wbits, jbits)."""
+    h = np.ascontiguousarray(heights, dtype=np.uint8)
+    rows, cols = h.shape
+    per_row = -(-(-(-cols // 2)) // (32 if flags & PACKED else 16))
+    cap = layers * ((rows + 1) // 2) * per_row
+    n = (C.c_int32 * 4)()
+    out = np.zeros(4 * max(cap, 1), dtype=np.uint32)
+    bits = (C.c_int32 * 2)()
+    _check(lib.isf_debug_item_lists(h.ctypes.data_as(C.POINTER(C.c_uint8)), rows, cols, layers, flags, n,
+                                    out.ctypes.data_as(C.POINTER(C.c_uint32)), cap, bits), "debug_item_lists")
+    return [out[c * cap:c * cap + n[c]].copy() for c in range(4)], bits[0], bits[1]
 
 
 def fold_series(T, h, sweeps_eq, sweeps_meas, n_occ, M, B, J=1.0) -> list[dict]:
