@@ -222,6 +222,15 @@ int isf_debug_checks(uint64_t* out4);
 int isf_debug_item_lists(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, uint32_t flags,
                          int32_t* n_out, uint32_t* out, int64_t cap, int32_t* bits_out);
 
+/* The row bands ISF_PATH_SLABS would give a packed film of this shape split over `bands` CTAs
+ * of at most max_rows colour rows each (host only, no device work): part_out[0..bands] (bands + 1
+ * int32), band g holding colour rows [part_out[g], part_out[g+1]); contiguous, 1..max_rows rows
+ * each, cut where the running count of occupied words (all colours and layers) is closest to an
+ * even share (Sec. 3's split of the image rows between processes).  Errors: ISF_ERR_ARG (bad
+ * shape or pointers, bands outside 1..colour rows, bands x max_rows below the colour rows). */
+int isf_debug_slab_partition(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, int32_t bands,
+                             int32_t max_rows, int32_t* part_out);
+
 /* Shape of the last isf_run_sweeps launch: path (ISF_PATH_GLOBAL / ISF_PATH_RESIDENT /
  * ISF_PATH_SLABS, 0 before any launch), CTAs (global), cluster size (resident) or row bands
  * (slabs), threads per CTA.  No device work. */

@@ -490,13 +490,14 @@ int isf_set_schedule(isf_lattice* L, int32_t nsteps, const double* T, const doub
 // Rows [part[g], part[g+1]) of each of the G CTAs of the row-slab kernel: contiguous, 1..cap
 // rows each, cut where the running count of occupied words (all colours) is closest to an even
 // share.  Returns the most rows of any CTA.
-static int slab_partition(const isf_lattice* L, int G, int cap, std::vector<int32_t>& part) {
-    const int Rh = L->lay.Rh;
+static int slab_partition(const Layout& lay, const std::vector<int32_t>& roff, int G, int cap,
+                          std::vector<int32_t>& part) {
+    const int Rh = lay.Rh;
     std::vector<int64_t> pre((size_t)Rh + 1, 0);
     for (int j = 0; j < Rh; ++j) {
         int64_t w = 0;
-        for (int cz = 0; cz < 4 * L->lay.L; ++cz) {
-            const int32_t* ro = L->roff_h.data() + (size_t)cz * (Rh + 1);
+        for (int cz = 0; cz < 4 * lay.L; ++cz) {
+            const int32_t* ro = roff.data() + (size_t)cz * (Rh + 1);
             w += ro[j + 1] - ro[j];
         }
         pre[j + 1] = pre[j] + w;
@@ -540,7 +541,7 @@ static int run_slabs(isf_lattice* L, int64_t nsweeps, cudaStream_t s, bool* fits
         // a new partition: the film's earlier launches (which read the old one) must be done
         int rc = sync_film(L);
         if (rc) return rc;
-        L->part_nrm = slab_partition(L, G, (int)std::min<int64_t>(cap, lay.Rh), L->part_h);
+        L->part_nrm = slab_partition(lay, L->roff_h, G, (int)std::min<int64_t>(cap, lay.Rh), L->part_h);
         CUDA_TRY(cudaMemcpy(L->dev + lay.part_off, L->part_h.data(), L->part_h.size() * sizeof(int32_t),
                             cudaMemcpyHostToDevice), "copy row partition");
         L->part_G = G;
@@ -886,6 +887,26 @@ int isf_debug_item_lists(const uint8_t* heights, int32_t rows, int32_t cols, int
     }
     bits_out[0] = wb;
     bits_out[1] = jb;
+    g_err.clear();
+    return ISF_OK;
+}
+
+int isf_debug_slab_partition(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, int32_t bands,
+                             int32_t max_rows, int32_t* part_out) {
+    if (!heights || !part_out) return fail(ISF_ERR_ARG, "a pointer argument is NULL");
+    Layout lay;
+    const char* why = "";
+    int rc = make_layout(rows, cols, layers, ISF_PACKED, &lay, &why);
+    if (rc) return fail(rc, why);
+    if (bands < 1 || bands > lay.Rh || max_rows < 1 || (int64_t)max_rows * bands < lay.Rh)
+        return fail(ISF_ERR_ARG, "need 1 <= bands <= colour rows and bands x max_rows >= colour rows");
+    std::vector<uint32_t> items;
+    std::vector<int32_t> roff, part;
+    int32_t n[4], wb = 0, jb = 0;
+    if (!build_word_items(lay, heights, items, n, &wb, &jb, 0, lay.Rh, &roff))
+        return fail(ISF_ERR_ARG, "the list entries' fields do not fit 32 bits");
+    slab_partition(lay, roff, bands, std::min(max_rows, lay.Rh), part);
+    std::memcpy(part_out, part.data(), part.size() * sizeof(int32_t));
     g_err.clear();
     return ISF_OK;
 }

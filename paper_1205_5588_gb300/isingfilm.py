@@ -75,6 +75,7 @@ def _declare(lib):
         "isf_set_item_sites": (C.c_int, [vp, C.c_int32]),
         "isf_debug_item_lists": (C.c_int, [u8p, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, i32p,
                                            C.POINTER(C.c_uint32), C.c_int64, i32p]),
+        "isf_debug_slab_partition": (C.c_int, [u8p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, i32p]),
         "isf_lattice_create_slab": (C.c_int, [u8p, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, C.c_uint64,
                                               C.c_int32, C.c_int32, C.c_int32, vp, C.POINTER(vp)]),
         "isf_slab_info": (C.c_int, [vp, i32p, C.POINTER(C.c_size_t), i64p]),
@@ -179,6 +180,16 @@ def item_lists(heights, layers, flags=0) -> tuple[list[np.ndarray], int, int]:
     _check(lib.isf_debug_item_lists(h.ctypes.data_as(C.POINTER(C.c_uint8)), rows, cols, layers, flags, n,
                                     out.ctypes.data_as(C.POINTER(C.c_uint32)), cap, bits), "debug_item_lists")
     return [out[c * cap:c * cap + n[c]].copy() for c in range(4)], bits[0], bits[1]
+
+
+def slab_partition(heights, layers, bands, max_rows) -> np.ndarray:
+    """The row bands the row-slab kernel would use for a packed film (host only): bands + 1
+    colour-row boundaries."""
+    h = np.ascontiguousarray(heights, dtype=np.uint8)
+    out = np.zeros(bands + 1, dtype=np.int32)
+    _check(lib.isf_debug_slab_partition(h.ctypes.data_as(C.POINTER(C.c_uint8)), h.shape[0], h.shape[1], layers, bands,
+                                        max_rows, out.ctypes.data_as(C.POINTER(C.c_int32))), "debug_slab_partition")
+    return out
 
 
 def fold_series(T, h, sweeps_eq, sweeps_meas, n_occ, M, B, J=1.0) -> list[dict]:

@@ -75,3 +75,41 @@ def test_item_lists_refused_for_periodic_int8(I):
     with pytest.raises(I.IsfError) as e:
         I.item_lists(H, 3, I.PERIODIC_X | I.PERIODIC_Y)
     assert e.value.code == -1
+
+
+def row_weights(I, H, L):
+    """Occupied words per colour row, all colours and layers (the partition's weights)."""
+    lists, wb, jb = I.item_lists(H, L, I.PACKED)
+    Rh = (H.shape[0] + 1) // 2
+    w = np.zeros(Rh, dtype=np.int64)
+    for lst in lists:
+        np.add.at(w, (lst >> wb) & ((1 << jb) - 1), 1)
+    return w
+
+
+@pytest.mark.parametrize("shape,bands,max_rows", [((2048, 2048, 6, 3), 152, 24), ((300, 200, 5, 7), 40, 10),
+                                                  ((90, 70, 4, 8), 45, 1), ((90, 70, 4, 8), 1, 45),
+                                                  ((160, 90, 5, 31), 13, 100), ((33, 65, 6, 9), 7, 3)])
+def test_slab_partition_properties(I, shape, bands, max_rows):
+    """The row bands of the row-slab kernel: contiguous, cover every colour row, 1..max_rows rows
+    each, and each cut within one row's weight of an even share of the occupied words."""
+    R, C, L, seed = shape
+    H = W.fractal_heights(R, C, 0.7, 1, L, seed=seed)
+    part = I.slab_partition(H, L, bands, max_rows)
+    Rh = (R + 1) // 2
+    assert part[0] == 0 and part[-1] == Rh and len(part) == bands + 1
+    sizes = np.diff(part)
+    assert sizes.min() >= 1 and sizes.max() <= max_rows
+    w = row_weights(I, H, L)
+    pre = np.concatenate([[0], np.cumsum(w)])
+    if bands * max_rows >= 2 * Rh:          # the row limit leaves room to balance
+        for g in range(1, bands):
+            assert abs(pre[part[g]] - pre[-1] * g / bands) <= w.max(), g
+
+
+def test_slab_partition_refusals(I):
+    H = W.fractal_heights(20, 30, 0.7, 1, 3, seed=5)
+    for bands, max_rows in ((11, 5), (0, 5), (4, 2)):       # 10 colour rows
+        with pytest.raises(I.IsfError) as e:
+            I.slab_partition(H, 3, bands, max_rows)
+        assert e.value.code == -1
