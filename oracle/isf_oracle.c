@@ -184,8 +184,9 @@ uint32_t or_threshold(double T, double h, double J, int n, int s)
     return threshold_of_probability(p);
 }
 
-/* Eq. 9: the switching-field gate passes with probability exp(-|S_i h_s| / T); |S_i| = 1. */
-static uint32_t gate_threshold(double T, double h_s)
+/* Eq. 9: the switching-field gate passes with probability exp(-|S_i h_s| / T); |S_i| = 1.
+ * Same encoding as the Eq. 8 threshold: the gate word g passes iff g < the count (or always). */
+uint32_t or_gate_threshold(double T, double h_s)
 {
     double a = fabs(h_s);
     if (a == 0.0) return OR_ALWAYS;
@@ -382,7 +383,7 @@ int or_run(or_film* f, int nsteps, const double* T, const double* h, const int* 
             thr[n + 12][0] = or_threshold(T[k], h[k], J, n, -1);
             thr[n + 12][1] = or_threshold(T[k], h[k], J, n, +1);
         }
-        uint32_t gate = gate_threshold(T[k], h_s);
+        uint32_t gate = or_gate_threshold(T[k], h_s);
 
         or_step_obs* r = &rec[k];
         memset(r, 0, sizeof(*r));

@@ -59,6 +59,10 @@ uint32_t or_site_word(const or_film* f, uint32_t stream, uint64_t sweep, int x, 
 /* Acceptance threshold for current spin s (+1/-1) with neighbour sum n at (T, h, J) (Eq. 8). */
 uint32_t or_threshold(double T, double h, double J, int n, int s);
 
+/* Threshold of the switching-field gate of Eq. 9 (pass probability exp(-|h_s| / T), |S_i| = 1),
+ * in the same encoding; h_s = 0 gives "always" (the gate is off). */
+uint32_t or_gate_threshold(double T, double h_s);
+
 int  or_film_create(const uint8_t* heights, int rows, int cols, int layers, unsigned flags,
                     uint64_t seed, int init, or_film** out);
 void or_film_destroy(or_film* f);

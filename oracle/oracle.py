@@ -87,6 +87,8 @@ def _declare(lib):
     lib.or_site_word.restype = C.c_uint32
     lib.or_threshold.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, C.c_int]
     lib.or_threshold.restype = C.c_uint32
+    lib.or_gate_threshold.argtypes = [C.c_double, C.c_double]
+    lib.or_gate_threshold.restype = C.c_uint32
     lib.or_film_create.argtypes = [u8p, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_uint64, C.c_int,
                                    C.POINTER(C.c_void_p)]
     lib.or_film_create.restype = C.c_int
@@ -139,6 +141,12 @@ def philox(ctr, key, lib=None) -> np.ndarray:
 def threshold(T, h, J, n, s, lib=None) -> int:
     lib = lib or load()
     return int(lib.or_threshold(T, h, J, n, s))
+
+
+def gate_threshold(T, h_s, lib=None) -> int:
+    """Eq. 9 gate threshold: the gate word g passes iff g < it (or it is ALWAYS)."""
+    lib = lib or load()
+    return int(lib.or_gate_threshold(T, h_s))
 
 
 def threshold_table(T, h, J=1.0, lib=None) -> np.ndarray:

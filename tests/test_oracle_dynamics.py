@@ -4,6 +4,9 @@
   standard errors, on periodic, open and masked films, with and without a field.
 - The Eq. 9 gate multiplies both directions of a flip by the same probability, so it must
   leave those equilibrium averages unchanged; with h_s = 0 it must change nothing at all.
+  Its own probability is pinned where Eq. 8 always accepts (J = 0, h = 0): a site flips
+  exactly when its gate word passes exp(-|h_s| / T), site by site; and at T = h_s = 1000 the
+  flip rate per attempt is e^-1 times an Eq. 8 acceptance in [exp(-0.024), 1].
 - T = inf: every attempt flips, so M alternates in sign and B never changes.
 - T = 0 from all up with h >= 0 (Sec. 5, the T = 0 argument): nothing flips; E = -J bonds - h N.
 - High T: <M^2>/N -> 1 and T^2 C / N -> J^2 bonds / N.
@@ -74,6 +77,58 @@ def test_gate_slows_flips(olib):
         _, ser = f.run([8.0], [0.0], [0], [400], h_s=h_s, series=True)
         flips.append(np.abs(np.diff(ser[:, 0])).sum())
     assert flips[1] < 0.5 * flips[0]
+
+
+def _gate_count(p):
+    """#{g in [0, 2^32): (g + 1/2) 2^-32 < p} in exact rationals (the Eq. 8/9 encoding)."""
+    from tests.test_oracle_rng_table import _count_exact
+    return _count_exact(p)
+
+
+@pytest.mark.parametrize("T,h_s", [(2.0, 1.0), (3.0, -4.5), (0.7, 0.35), (1e3, 1e3)])
+def test_gate_decides_every_flip_when_eq8_always_accepts(olib, T, h_s):
+    """With J = 0 and h = 0 every Eq. 8 step has dE = 0 and is accepted, so a site flips in a
+    sweep exactly when its Eq. 9 gate word (stream 1) passes: g < #{g : (g + 1/2) 2^-32 <
+    exp(-|h_s| / T)}.  Checked site by site over several sweeps, against that count formed here
+    in exact rationals."""
+    H = np.array([[3, 2, 0, 3, 1], [1, 3, 3, 2, 0], [2, 0, 1, 3, 3], [3, 3, 2, 1, 2]], dtype=np.uint8)
+    L = 3
+    f = oracle.Film(H, L, seed=0xFEED, lib=olib)
+    cnt = _gate_count(np.exp(-abs(h_s) / T))
+    occ = [(x, y, z) for z in range(L) for y in range(H.shape[0]) for x in range(H.shape[1]) if z < H[y, x]]
+    flips = 0
+    for sweep in range(1, 9):
+        before = f.spins()
+        f.run([T], [0.0], [0], [1], J=0.0, h_s=h_s)
+        after = f.spins()
+        for (x, y, z) in occ:
+            g = f.site_word(oracle.STREAM_GATE, sweep, x, y, z)
+            passed = g < cnt
+            assert (after[z, y, x] != before[z, y, x]) == passed, (sweep, x, y, z, g, cnt)
+            flips += passed
+    assert 0 < flips < 8 * len(occ)
+
+
+def test_gate_flip_rate(olib):
+    """At T = 1000 with h_s = 1000 the gate passes with probability e^-1, and Eq. 8 accepts with
+    probability between exp(-24/1000) and 1 (|dE| <= 2 (12 J + |h|) with h = 0): the flip fraction
+    per attempt lies in [0.976 e^-1, e^-1] up to 5 binomial standard deviations."""
+    H = np.full((12, 12), 3, dtype=np.uint8)
+    f = oracle.Film(H, 3, flags=3, seed=11, lib=olib)
+    N = f.info()["n_occ"]
+    nsw = 300
+    prev = f.spins()
+    flips = 0
+    for _ in range(nsw):
+        f.run([1e3], [0.0], [0], [1], h_s=1e3)
+        cur = f.spins()
+        flips += int((cur != prev).sum())
+        prev = cur
+    n = N * nsw
+    frac = flips / n
+    p = np.exp(-1.0)
+    sd = np.sqrt(p * (1 - p) / n)
+    assert np.exp(-24.0 / 1e3) * p - 5 * sd <= frac <= p + 5 * sd, (frac, p, sd)
 
 
 @pytest.mark.parametrize("flags,init", [(3, oracle.INIT_RANDOM), (0, oracle.INIT_UP)])

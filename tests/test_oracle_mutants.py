@@ -82,6 +82,25 @@ def _measurement_fails(lib):
     return recs[0]["n_meas"] != 10 or recs[0]["sumM"] != int(ser[4:, 0].sum())
 
 
+def _gate_fails(lib):
+    from tests.test_oracle_dynamics import _gate_count
+    H = np.full((3, 4), 2, dtype=np.uint8)
+    f = oracle.Film(H, 2, seed=3, lib=lib)
+    for T, h_s in ((2.0, 1.0), (0.7, -0.35)):
+        cnt = _gate_count(math.exp(-abs(h_s) / T))
+        before = f.spins()
+        f.run([T], [0.0], [0], [1], J=0.0, h_s=h_s)
+        after = f.spins()
+        sweep = f.info()["sweep"]
+        for z in range(2):
+            for y in range(3):
+                for x in range(4):
+                    passed = f.site_word(oracle.STREAM_GATE, sweep, x, y, z) < cnt
+                    if (after[z, y, x] != before[z, y, x]) != passed:
+                        return True
+    return False
+
+
 MUTANTS = [
     ("field sign in dE", "(J * (double)n + h)", "(J * (double)n - h)", _enum_fails),
     ("temperature dropped", "exp(-dE / T)", "exp(-dE)", _enum_fails),
@@ -93,6 +112,9 @@ MUTANTS = [
     ("bond update sign", "f->B += -2 * (int64_t)s * n;", "f->B += 2 * (int64_t)s * n;", _bookkeeping_fails),
     ("threshold rounding", "p * 4294967296.0 - 0.5", "p * 4294967296.0 + 0.5", _threshold_fails),
     ("measured window off by one", "if (t >= sweeps_eq[k])", "if (t > sweeps_eq[k])", _measurement_fails),
+    ("temperature dropped from the gate", "exp(-a / T)", "exp(-a)", _gate_fails),
+    ("gate exponent doubled", "exp(-a / T)", "exp(-2.0 * a / T)", _gate_fails),
+    ("gate word compared the wrong way", "if (!(g < gate)) continue;", "if (!(g > gate)) continue;", _gate_fails),
 ]
 
 

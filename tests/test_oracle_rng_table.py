@@ -4,6 +4,8 @@
   implementation of the SC'11 generator), on edge and random counters/keys.
 - The threshold is checked against its defining inequality with exact rational arithmetic,
   and against the limits Eq. 8 fixes (dE <= 0 always accepted, T = inf always, T = 0 never).
+- The Eq. 9 gate threshold is checked the same way against exp(-|h_s| / T), with its limits
+  (h_s = 0 and T = inf always pass, T = 0 never) and closed-form values e^-1, e^-1/2.
 """
 from fractions import Fraction
 import math
@@ -110,3 +112,38 @@ def test_threshold_table_matches_probability(olib):
             t = int(tab[n + 12, sp])
             approx = 1.0 if t == ALWAYS else t / 2.0**32
             assert abs(approx - p) <= 2.0**-32 + 1e-15
+
+
+@pytest.mark.parametrize("T", [0.3, 1.0, 2.0, 4.5, 8.0, 1e3])
+@pytest.mark.parametrize("h_s", [0.0, 0.25, -1.0, 2.0, 4.0, -8.0, 1e3])
+def test_gate_threshold_definition(olib, T, h_s):
+    """Eq. 9 gate (items 4-5 of Sec. 5): it passes with probability exp(-|S_i h_s| / T), |S_i| = 1,
+    encoded like Eq. 8: g passes iff g < thr, thr = #{g : (g + 1/2) 2^-32 < p}, counts of 2^32 - 1
+    or more stored as ALWAYS; h_s = 0 means no gate (p = 1)."""
+    thr = oracle.gate_threshold(T, h_s, lib=olib)
+    cnt = _count_exact(math.exp(-abs(h_s) / T))
+    if cnt >= (1 << 32) - 1:
+        assert thr == ALWAYS
+    else:
+        assert thr == cnt
+        p = Fraction(math.exp(-abs(h_s) / T))
+        if thr > 0:
+            assert (Fraction(thr - 1) + Fraction(1, 2)) / (1 << 32) < p
+        assert (Fraction(thr) + Fraction(1, 2)) / (1 << 32) >= p
+    # the sign of the switching field does not matter (|S_i h_s|)
+    assert oracle.gate_threshold(T, -h_s, lib=olib) == thr
+
+
+def test_gate_threshold_limits(olib):
+    inf = float("inf")
+    for h_s in (0.5, 3.0, -7.0):
+        assert oracle.gate_threshold(inf, h_s, lib=olib) == ALWAYS      # T = inf: p = 1
+        assert oracle.gate_threshold(0.0, h_s, lib=olib) == 0           # T = 0: p = exp(-inf) = 0
+    assert oracle.gate_threshold(0.0, 0.0, lib=olib) == ALWAYS          # h_s = 0: no gate at any T
+    assert oracle.gate_threshold(2.0, 0.0, lib=olib) == ALWAYS
+    # e^-1 and e^-1/2 as fractions of 2^32 (closed forms, independent of the oracle's rounding)
+    assert abs(oracle.gate_threshold(2.0, 2.0, lib=olib) / 2.0**32 - math.exp(-1.0)) <= 2.0**-32
+    assert abs(oracle.gate_threshold(4.0, -2.0, lib=olib) / 2.0**32 - math.exp(-0.5)) <= 2.0**-32
+    # a larger switching field never lets the gate pass more often
+    vals = [oracle.gate_threshold(3.0, a, lib=olib) for a in (0.1, 0.5, 1.0, 2.0, 5.0, 20.0)]
+    assert all(a >= b for a, b in zip(vals, vals[1:]))
