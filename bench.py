@@ -1,20 +1,27 @@
 """Benchmark: Metropolis spin-flip attempts/s of the CUDA path on one GB300 (or N replicas).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload fractal256|flat16|fractal2048]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload fractal2048|fractal256|flat16]
     python bench.py --impl reference ...      # the CPU oracle on a bounded sample, same metric
 
-One step = one pass of the whole hot path over one film: the full temperature scan (or
-hysteresis loop) of the workload, every sweep of every schedule step, with the spins resident
-in device memory.  Synthetic seeded inputs (fractal height maps) stand in for the paper's STM
-images.  Timing: CUDA events on the launching stream around each step; L2 is flushed between
-steps (outside the events); W untimed warm-up steps; max over ranks.  Under torchrun every rank
-runs its own replica of the film (the single-film path has no exchange step).
+Headline (`value`): the 2048 x 2048 x (2..6) fractal film with bit-packed spins (one bit per
+spin, 32 spins per uint32 word), hysteresis loop at T = 2 with h = +8 -> -8 -> +8 in steps of 0.05
+(641 field steps x 200 sweeps).  One step = one pass of the whole hot path over that film: every
+sweep of every field step, spins resident in device memory, one persistent launch.  Synthetic
+seeded inputs (fractal height maps) stand in for the paper's STM images.
+
+Timing: CUDA events on the launching stream around each step; L2 is flushed between steps
+(256 MiB write, outside the events); W >= 3 untimed warm-up steps; max over ranks.  Under
+torchrun every rank runs its own replica of the film (the single-film path has no exchange
+step).  Further legs in the same JSON line: the 256^2 int8 temperature scan (one film in one
+cluster's shared memory), batched films (512 ragged films, int8 and bit-packed) against the same
+films one per launch, a served Poisson job stream at a sustainable and at the stated rate, and
+the integer-issue ceilings the rooflines divide by, measured in the same run.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -33,26 +40,23 @@ UNIT = "attempts/s"
 # Philox4x32-10 block (10 rounds x (2 32x32->64 multiplies + 4 XORs + 2 key adds) / 4 = 25), the
 # 12-neighbour sum (12) and the acceptance test and update (5).
 OPS_PER_ATTEMPT = 40
-SMS, LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
-ALU_PEAK_TOPS = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12    # 40.3 T int32 lane-ops/s
+LANES_PER_SM = 128          # int32 lanes: 4 sub-partitions x 32, one warp instruction per clock each
 
 
 def workload(name: str):
     from paper_1205_5588_gb300 import workloads as W
+    if name == "fractal2048":
+        return W.fractal2048_hysteresis()
     if name == "fractal256":
         return W.fractal256_tscan()
     if name == "flat16":
         return W.flat16_hysteresis()
-    if name == "fractal2048":
-        return W.fractal2048_hysteresis()
     raise SystemExit(f"unknown workload {name}")
 
 
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+KERNEL_OF_PATH = {"global": "k_sweep (global-memory persistent kernel, all SMs)",
+                  "resident": "k_resident (film in one cluster's shared memory)",
+                  "slabs": "k_slabs (row bands in shared memory)"}
 
 
 class Clocks:
@@ -109,6 +113,160 @@ def attempts_of(spec, n_occ):
     return int(n_occ) * int(s["eq"].sum() + s["meas"].sum())
 
 
+def events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+# ---------------------------------------------------------------- integer-issue ceilings ----
+def probe_peaks(I, stream, target_s=0.05, reps=3) -> dict:
+    """The integer-issue ceilings of this GPU (isf_peak_probe), each the best of `reps` timed
+    launches (CUDA events on `stream`) of about target_s seconds, after a warm-up launch."""
+    import torch
+    out = {}
+    for mode, threads, key, unit in ((I.PEAK_LOP3, 1024, "lop3_lane_ops_per_s", "lane-ops"),
+                                     (I.PEAK_MIX, 1024, "mix_lane_ops_per_s", "lane-ops"),
+                                     (I.PEAK_PHILOX, 512, "philox_blocks_per_s", "blocks"),
+                                     (I.PEAK_ATTEMPT, 512, "attempts_per_s_arithmetic", "attempts")):
+        iters = 64
+        best = 0.0
+        for rep in range(reps + 8):
+            a, b = events()
+            a.record(stream)
+            units = I.peak_probe(mode, 0, threads, iters, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            dt = a.elapsed_time(b) / 1e3
+            if dt < 0.5 * target_s and rep < 8:        # grow the launch until it runs ~target_s
+                iters = int(iters * min(64.0, max(2.0, target_s / max(dt, 1e-6))))
+                continue
+            best = max(best, units / dt)
+        out[key] = best
+    torch.cuda.synchronize()
+    return out
+
+
+def roofline(attempts_per_launch, t_launch, peaks, sms, sm_max_mhz, kernel, shape, traffic, inst_per_attempt):
+    """ALU roofline of one sweep launch: achieved = 40 algorithmic int-ops per attempt / launch
+    time; peak = the integer-op mix rate measured in this run (isf_peak_probe)."""
+    rate = attempts_per_launch / t_launch
+    achieved = OPS_PER_ATTEMPT * rate / 1e12
+    peak = peaks["mix_lane_ops_per_s"] / 1e12
+    derived = sms * LANES_PER_SM * sm_max_mhz * 1e6 if sm_max_mhz else None
+    ceil = {
+        "sms": sms, "sm_max_mhz": sm_max_mhz,
+        "lane_issue_lop3_Tops": peaks["lop3_lane_ops_per_s"] / 1e12,
+        "lane_issue_mix_Tops": peaks["mix_lane_ops_per_s"] / 1e12,
+        "lane_issue_derived_Tops": derived / 1e12 if derived else None,
+        "philox_blocks_per_s": peaks["philox_blocks_per_s"],
+        "attempts_per_s_if_every_attempt_draws_a_word": 4.0 * peaks["philox_blocks_per_s"],
+        "attempts_per_s_arithmetic": peaks["attempts_per_s_arithmetic"],
+        "frac_of_philox_ceiling": rate / (4.0 * peaks["philox_blocks_per_s"]),
+        "frac_of_arithmetic_ceiling": rate / peaks["attempts_per_s_arithmetic"],
+        "inst_per_attempt": inst_per_attempt,
+        "frac_of_lop3_issue_by_instructions": (inst_per_attempt * rate / peaks["lop3_lane_ops_per_s"]
+                                               if inst_per_attempt else None),
+    }
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": kernel, "launch": shape, "ops_per_attempt": OPS_PER_ATTEMPT,
+            "peak_from": "measured in this run on this GPU: the integer op mix of the random-number work "
+                         "(32x32->64 multiply, XOR3, majority, add; one instruction each) register-only on "
+                         "all SMs (isf_peak_probe ISF_PEAK_MIX), CUDA events, best of 3",
+            "ceilings": ceil}
+
+
+# ---------------------------------------------------------------- one film, timed ----
+def time_film(I, spec, seed, steps, warmup, stream, l2buf, path="auto"):
+    """W warm-up and K timed passes of the whole schedule of one film; returns per-step seconds
+    (CUDA events on `stream`), attempts per step, launch shape, records and a sweep-kernel launch
+    count of the timed region."""
+    import torch
+    sched = spec["schedule"]
+    lat = I.Lattice(spec["heights"], spec["layers"], periodic_x=spec["periodic_x"], periodic_y=spec["periodic_y"],
+                    packed=spec["packed"], seed=seed, init=spec["init"], stream=stream)
+    if path != "auto":
+        lat.set_path(path)
+    n_occ = lat.info()["n_occ"]
+    per_step = attempts_of(spec, n_occ)
+    times = []
+    for i in range(warmup + steps):
+        lat.set_schedule(sched["T"], sched["h"], sched["eq"], sched["meas"], J=spec["J"])
+        if i >= warmup:
+            flush_l2(l2buf)
+        a, b = events()
+        a.record(stream)
+        lat.run(-1, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        if i >= warmup:
+            times.append(a.elapsed_time(b) / 1e3)
+    torch.cuda.synchronize()
+    shape = lat.launch_info()
+    recs = lat.observables()
+    lat.close()
+    return {"times": times, "per_step": per_step, "n_occ": n_occ, "shape": shape, "recs": recs}
+
+
+def e2e_film(I, spec, seed, steps, stream):
+    """End to end through the public C ABI from host buffers, every step: isf_lattice_create
+    from the pinned host height map, isf_set_schedule from host arrays, isf_run_sweeps,
+    isf_read_observables back to the host.  The first pass warms the path."""
+    import torch
+    sched = spec["schedule"]
+    heights_pinned = torch.from_numpy(spec["heights"]).pin_memory().numpy()
+    ts = []
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L2 = I.Lattice(heights_pinned, spec["layers"], periodic_x=spec["periodic_x"],
+                       periodic_y=spec["periodic_y"], packed=spec["packed"], seed=seed, init=spec["init"],
+                       stream=stream)
+        L2.set_schedule(sched["T"], sched["h"], sched["eq"], sched["meas"], J=spec["J"])
+        L2.run(-1, stream=stream)
+        out = L2.observables()
+        t1 = time.perf_counter()
+        L2.close()
+        assert len(out) == len(sched["T"])
+        if i > 0:
+            ts.append(t1 - t0)
+    h2d = int(spec["heights"].nbytes) + len(sched["T"]) * (52 * 4 + 8)    # heights; per step: table, eq, total
+    d2h = len(sched["T"]) * 96 + 4                                        # per-step records + status word
+    return {"seconds": ts, "h2d": h2d, "d2h": d2h}
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one bench launch of the dominant kernel, and
+# its thread-instructions per attempt (smsp__inst_executed.sum x threads per instruction /
+# attempts), from the ncu captures summarised in profiles/; each valid while the kernel's sources
+# hash to the recorded value (None: not captured for the current sources).
+NCU_RECORDS = {
+    "fractal256": {"sources": ["kernels_resident.cu", "sweep_core.cuh", "device_common.cuh"],
+                   "sources_sha256": "f36ebbab1af1299b3c47ee70d982d7ff64c27ea00cc75d4b1f52033a3fddf4b6",
+                   "bytes_per_launch": 1309952.0, "inst_per_attempt": None},
+    "fractal2048": {"sources": ["kernels_sweep.cu", "sweep_core.cuh", "device_common.cuh"],
+                    "sources_sha256": "1eaef32c6540c29532335150a443768566022045f45b69e381857ffcc1ad8d5d",
+                    "bytes_per_launch": 21053440.0 + 2549504.0, "inst_per_attempt": 27.3},
+}
+
+
+def kernel_sources_sha256(names) -> str:
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_1205_5588_gb300", "csrc", name), "rb") as fp:
+            h.update(fp.read())
+    return h.hexdigest()
+
+
+def ncu_record(workload_name, key):
+    rec = NCU_RECORDS.get(workload_name)
+    if not rec or rec["sources_sha256"] != kernel_sources_sha256(rec["sources"]):
+        return None
+    return rec[key]
+
+
+def load_traffic(workload_name):
+    return ncu_record(workload_name, "bytes_per_launch")
+
+
 def run_impl(args):
     import torch
     from paper_1205_5588_gb300 import distributed as D
@@ -125,97 +283,60 @@ def run_impl(args):
     sched = spec["schedule"]
     seed = D.replica_seed(spec["seed"], rank)   # a single film does not shard: one replica per rank
     stream = torch.cuda.current_stream()
-    lat = I.Lattice(spec["heights"], spec["layers"], periodic_x=spec["periodic_x"], periodic_y=spec["periodic_y"],
-                    packed=spec["packed"], seed=seed, init=spec["init"], stream=stream)
-    if args.ctas or args.threads:
-        lat.set_launch(args.ctas, args.threads)
-    n_occ = lat.info()["n_occ"]
-    per_step = attempts_of(spec, n_occ)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     l2buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    peaks = probe_peaks(I, stream)
 
-    def one_step():
-        lat.set_schedule(sched["T"], sched["h"], sched["eq"], sched["meas"], J=spec["J"])
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        lat.run(-1, stream=stream)
-        b.record(stream)
-        return a, b
-
-    for _ in range(args.warmup):
-        one_step()
-    torch.cuda.synchronize()
     D.barrier(ranks)
     clocks = Clocks(dev) if rank == 0 else None
-    times = []
-    for _ in range(args.steps):
-        flush_l2(l2buf)
-        a, b = one_step()
-        b.synchronize()
-        times.append(a.elapsed_time(b) / 1e3)
-    torch.cuda.synchronize()
+    leg = time_film(I, spec, seed, args.steps, args.warmup, stream, l2buf, path=args.path)
     clk = clocks.stop() if clocks else None
-    total = D.max_over_ranks(sum(times), ranks, device="cuda")
+    total = D.max_over_ranks(sum(leg["times"]), ranks, device="cuda")
     D.barrier(ranks)
-    recs = lat.observables()
-    shape = lat.launch_info()
-    lat.close()
+    per_step = leg["per_step"]
     value = per_step * args.steps * ws / total
+    t_launch = sum(leg["times"]) / len(leg["times"])
+    shape = leg["shape"]
+    sm_max = (clk or {}).get("sm_max_mhz")
+    e2e = e2e_film(I, spec, seed, args.e2e_steps, stream)
+    e2e_value = per_step * ws / statistics.mean(e2e["seconds"])
 
-    # end to end through the public API with host buffers: create from the host height map,
-    # upload the schedule, run, read the observables back, every step
-    e2e_times = []
-    h2d = int(spec["heights"].nbytes) + int(sched["T"].nbytes + sched["h"].nbytes + sched["eq"].nbytes
-                                             + sched["meas"].nbytes) + len(sched["T"]) * 52 * 4
-    d2h = len(sched["T"]) * 96 + 4          # exact per-step records + the kernel status word
-    heights_pinned = torch.from_numpy(spec["heights"]).pin_memory().numpy()
-    for i in range(args.e2e_steps + 1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        L2 = I.Lattice(heights_pinned, spec["layers"], periodic_x=spec["periodic_x"],
-                       periodic_y=spec["periodic_y"], packed=spec["packed"], seed=seed, init=spec["init"],
-                       stream=stream)
-        L2.set_schedule(sched["T"], sched["h"], sched["eq"], sched["meas"], J=spec["J"])
-        L2.run(-1, stream=stream)
-        out = L2.observables()
-        t1 = time.perf_counter()
-        L2.close()
-        assert len(out) == len(sched["T"])
-        if i > 0:                      # first one warms the path
-            e2e_times.append(t1 - t0)
-    e2e_value = per_step * ws / statistics.mean(e2e_times)
-
-    ms = total / args.steps * 1e3
-    achieved_tops = OPS_PER_ATTEMPT * per_step / (total / args.steps) / 1e12
-    traffic = load_traffic(args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int8" if not spec["packed"] else "u32 (1 bit/spin)",
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 (1 bit/spin, 32 spins per word)" if spec["packed"] else "int8",
         "data": "synthetic (seeded fractal height map stands in for the STM image)",
         "config": {"workload": spec["name"], "rows": int(spec["heights"].shape[0]),
-                   "cols": int(spec["heights"].shape[1]), "layers": spec["layers"], "occupied_sites": n_occ,
-                   "schedule_steps": int(len(sched["T"])), "sweeps_per_step_of_bench": int(sched["eq"].sum() + sched["meas"].sum()),
-                   "attempts_per_step": per_step, "l2": "flushed between timed steps (256 MiB write)",
+                   "cols": int(spec["heights"].shape[1]), "layers": spec["layers"], "occupied_sites": leg["n_occ"],
+                   "schedule_steps": int(len(sched["T"])),
+                   "sweeps_per_step_of_bench": int(sched["eq"].sum() + sched["meas"].sum()),
+                   "attempts_per_step": per_step, "spins": "bit-packed" if spec["packed"] else "int8",
+                   "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
-                   "final_abs_m_at_lowest_T": recs[0]["abs_m"] if recs else None},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "what": "isf_lattice_create from host heights + isf_set_schedule + isf_run_sweeps + isf_read_observables"},
+                   "final_m": leg["recs"][-1]["m"] if leg["recs"] else None},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                "steps": args.e2e_steps,
+                "what": "isf_lattice_create from pinned host heights + isf_set_schedule + isf_run_sweeps + "
+                        "isf_read_observables, every step"},
         "gpu_launches": args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
-                     "frac": achieved_tops / ALU_PEAK_TOPS, "traffic": traffic,
-                     "kernel": ("k_resident (film in one cluster's shared memory)" if shape["path"] == "resident"
-                                else "k_sweep (global-memory persistent kernel)"),
-                     "launch": shape,
-                     "sms_usable": shape["ctas"] if shape["path"] == "resident" else 152,
-                     "peak_from": "152 SMs x 128 int32 lanes x 2070 MHz (issue-rate ceiling)",
-                     "ops_per_attempt": OPS_PER_ATTEMPT},
+        "roofline": roofline(per_step, t_launch, peaks, sms, sm_max, KERNEL_OF_PATH.get(shape["path"], shape["path"]),
+                             shape, load_traffic(args.workload), ncu_record(args.workload, "inst_per_attempt")),
         "clocks": clk,
     }
-    if not args.no_multispin and args.workload != "fractal2048":
-        m = measure_multispin(I, ranks)
+    if not args.no_tscan and args.workload != "fractal256":
+        t = time_film(I, workload("fractal256"), D.replica_seed(1, rank), args.leg_steps, 3, stream, l2buf)
+        tl = sum(t["times"]) / len(t["times"])
+        tot = D.max_over_ranks(sum(t["times"]), ranks, device="cuda")
         if rank == 0:
-            line["multispin"] = m
+            line["tscan256"] = {
+                "workload": "fractal256x256x6_tscan", "value": t["per_step"] * len(t["times"]) * ws / tot,
+                "unit": UNIT, "dtype": "int8", "occupied_sites": t["n_occ"], "attempts_per_step": t["per_step"],
+                "seconds_per_step": tl, "steps": len(t["times"]), "warmup": 3,
+                "roofline": roofline(t["per_step"], tl, peaks, sms, sm_max,
+                                     KERNEL_OF_PATH.get(t["shape"]["path"], t["shape"]["path"]), t["shape"],
+                                     load_traffic("fractal256"), ncu_record("fractal256", "inst_per_attempt"))}
+    del l2buf
     if not args.no_batched:
         # independent films: each rank runs its own share of the list (weak scaling)
         b = measure_batched(I, n_films=args.batch_films, sweeps_per_step=args.batch_sweeps, ranks=ranks,
@@ -227,6 +348,8 @@ def run_impl(args):
             line["batched_packed"] = bp
     if rank == 0 and not args.no_served:
         line["served"] = measure_served(I, rate=args.serve_rate, duration=args.serve_seconds)
+        line["served_sustainable"] = measure_served(I, rate=args.serve_rate_sustainable,
+                                                    duration=args.serve_seconds_sustainable)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, budget_s=args.cpu_seconds)
     if rank == 0:
@@ -234,78 +357,37 @@ def run_impl(args):
     D.finish(ranks)
 
 
-def measure_multispin(I, ranks, steps=2, warmup=1):
-    """The bit-packed multispin sweep on the 2048x2048x(2..6) film: one timed step is the whole
-    hysteresis loop (641 field steps x 200 sweeps at T = 2), one k_sweep launch, L2 flushed
-    between steps.  Under several ranks each rank runs its own replica."""
-    import torch
-    from paper_1205_5588_gb300 import distributed as D
-    spec = workload("fractal2048")
-    sched = spec["schedule"]
-    lat = I.Lattice(spec["heights"], spec["layers"], packed=True, seed=D.replica_seed(spec["seed"], ranks.rank),
-                    init=spec["init"])
-    n_occ = lat.info()["n_occ"]
-    per_step = attempts_of(spec, n_occ)
-    l2buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.current_stream()
-    times = []
-    for i in range(warmup + steps):
-        lat.set_schedule(sched["T"], sched["h"], sched["eq"], sched["meas"], J=spec["J"])
-        flush_l2(l2buf)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        lat.run(-1, stream=stream)
-        b.record(stream)
-        b.synchronize()
-        if i >= warmup:
-            times.append(a.elapsed_time(b) / 1e3)
-    shape = lat.launch_info()
-    recs = lat.observables()
-    lat.close()
-    del l2buf
-    total = D.max_over_ranks(sum(times), ranks, device="cuda")
-    t_launch = sum(times) / len(times)
-    achieved = OPS_PER_ATTEMPT * per_step / t_launch / 1e12
-    return {"workload": spec["name"], "value": per_step * steps * ranks.world / total, "unit": UNIT,
-            "dtype": "u32 (1 bit/spin)", "occupied_sites": n_occ, "attempts_per_step": per_step,
-            "seconds_per_step": t_launch, "steps": steps, "warmup": warmup,
-            "final_m": recs[-1]["m"] if recs else None,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
-                         "frac": achieved / ALU_PEAK_TOPS, "traffic": load_traffic("fractal2048"),
-                         "kernel": "k_sweep<packed> (global-memory persistent kernel)", "launch": shape,
-                         "ops_per_attempt": OPS_PER_ATTEMPT}}
-
-
-def measure_batched(I, n_films=128, sweeps_per_step=20, seed=4, plain=True, ranks=None, packed=False):
+def measure_batched(I, n_films=512, sweeps_per_step=100, seed=4, plain=True, ranks=None, packed=False,
+                    plain_every=8):
     """Batched films (ragged sizes 64..1024, 1..8 layers, own T and field loop each) advanced to
-    the end of their schedules by isf_batch_run, against the same films run one per launch; int8
-    or bit-packed spins.  Under several ranks each rank runs its round-robin share of the films."""
+    the end of their schedules by isf_batch_run, int8 or bit-packed spins, against the same films
+    run one per launch on every `plain_every`-th film (a sample, to bound the time).  Under several
+    ranks each rank runs its round-robin share of the films."""
     import torch
     from paper_1205_5588_gb300 import distributed as D
     from paper_1205_5588_gb300 import workloads as W
     ranks = ranks or D.env_ranks()
     films = W.batch_films(n_films, seed=seed, sweeps_per_step=sweeps_per_step)
     films = [films[i] for i in D.shard(len(films), ranks.rank, ranks.world)]
-    lats = []
-    for f in films:
-        L = I.Lattice(f["heights"], f["layers"], seed=f["seed"], packed=packed)
-        lats.append(L)
-    att = sum(L.info()["n_occ"] * int(f["schedule"]["eq"].sum() + f["schedule"]["meas"].sum())
-              for L, f in zip(lats, films))
+    lats = [I.Lattice(f["heights"], f["layers"], seed=f["seed"], packed=packed) for f in films]
+    atts = [L.info()["n_occ"] * int(f["schedule"]["eq"].sum() + f["schedule"]["meas"].sum())
+            for L, f in zip(lats, films)]
+    att = sum(atts)
 
-    def reset():
-        for L, f in zip(lats, films):
-            sc = f["schedule"]
-            L.set_schedule(sc["T"], sc["h"], sc["eq"], sc["meas"])
+    def reset(sel=None):
+        for i, (L, f) in enumerate(zip(lats, films)):
+            if sel is None or i in sel:
+                sc = f["schedule"]
+                L.set_schedule(sc["T"], sc["h"], sc["eq"], sc["meas"])
 
     reset()
     b = I.Batch(lats, graph=True)
     b.tune()
-    b.run()                       # warm: kernels loaded, graph captured
+    b.run(max_sweeps=sweeps_per_step)     # warm: kernels loaded, graph captured (one step's sweeps)
     torch.cuda.synchronize()
     reset()
     D.barrier(ranks)
-    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a, e = events()
     a.record()
     b.run()
     e.record()
@@ -318,25 +400,30 @@ def measure_batched(I, n_films=128, sweeps_per_step=20, seed=4, plain=True, rank
            "ranks": ranks.world, "scaling": "weak (films dealt out across ranks)"}
     b.close()
     if plain:
-        reset()
+        sel = set(range(0, len(films), plain_every))
+        reset(sel)
         torch.cuda.synchronize()
         a.record()
-        for L in lats:
-            L.run(-1)
+        for i in sorted(sel):
+            lats[i].run(-1)
         e.record()
         e.synchronize()
         t_plain = a.elapsed_time(e) / 1e3
-        out["plain_one_film_per_launch"] = {"value": att / t_plain, "unit": UNIT, "seconds": t_plain}
-        out["speedup_vs_plain"] = t_plain / t_batch
+        att_plain = sum(atts[i] for i in sel)
+        out["plain_one_film_per_launch"] = {"value": att_plain / t_plain, "unit": UNIT, "seconds": t_plain,
+                                            "films": len(sel), "attempts": att_plain,
+                                            "sample": f"every {plain_every}th film of the batch"}
+        out["speedup_vs_plain"] = out["value"] / (att_plain / t_plain)
     for L in lats:
         L.close()
     return out
 
 
-def measure_served(I, rate=200.0, duration=5.0, seed=5, pool=24, budget_gb=40.0, sweeps_per_tick=50, packed=True):
+def measure_served(I, rate=200.0, duration=60.0, seed=5, pool=128, budget_gb=40.0, sweeps_per_tick=50, packed=True):
     """Poisson stream of hysteresis-loop and temperature-scan jobs (50/50) on films with
     log-normal side length (median 256, 64..2048) and 1..8 layers, bit-packed spins, served with
-    continuous batching; latency is submit -> completion."""
+    continuous batching; latency is submit -> completion.  Films come from a pool of `pool`
+    seeded maps (each job with its own seed, temperature and schedule)."""
     import torch
     from paper_1205_5588_gb300 import workloads as W
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -355,6 +442,10 @@ def measure_served(I, rate=200.0, duration=5.0, seed=5, pool=24, budget_gb=40.0,
         else:
             sc = W.schedule(np.linspace(0.5, 12.0, 24), 0.0, 200, 200)
         jobs.append((H, L, sc, 10000 + k))
+    offered = 0
+    for H, L, sc, _ in jobs:
+        n_sites = int(np.minimum(H, L).sum())
+        offered += n_sites * int(sc["eq"].sum() + sc["meas"].sum())
     srv = I.Server(int(budget_gb * (1 << 30)), sweeps_per_tick=sweeps_per_tick)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -366,7 +457,7 @@ def measure_served(I, rate=200.0, duration=5.0, seed=5, pool=24, budget_gb=40.0,
         ids.append(srv.submit(H, L, sc["T"], sc["h"], sc["eq"], sc["meas"], seed=sd, packed=packed))
     lat = []
     for jid in ids:
-        state = srv.wait(jid, timeout=600.0)
+        state = srv.wait(jid, timeout=900.0)
         if state != "done":
             raise RuntimeError(f"served job {jid} ended {state}")
         _, _, l = srv.result(jid)
@@ -378,39 +469,11 @@ def measure_served(I, rate=200.0, duration=5.0, seed=5, pool=24, budget_gb=40.0,
     lat = np.array(lat)
     return {"value": st["attempts_done"] / wall, "unit": UNIT, "jobs": len(ids), "rate_per_s": rate,
             "arrival_window_s": duration, "wall_s": wall,
-            "offered": st["attempts_done"] / duration, "p50_latency_s": float(np.percentile(lat, 50)),
-            "p99_latency_s": float(np.percentile(lat, 99)), "ticks": st["ticks"], "sweeps_per_tick": sweeps_per_tick,
-            "gpu_busy_s": st["busy_s"], "peak_device_bytes": st["peak_bytes"],
+            "offered": offered / duration, "sustained": bool(wall < duration * 1.1 + 2.0),
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "ticks": st["ticks"], "sweeps_per_tick": sweeps_per_tick,
+            "gpu_busy_s": st["busy_s"], "peak_device_bytes": st["peak_bytes"], "map_pool": pool,
             "spins": "u32 (1 bit/spin)" if packed else "int8"}
-
-
-# dram__bytes_read.sum + dram__bytes_write.sum of one bench launch of the dominant kernel, from
-# the ncu captures summarised in profiles/, valid while the kernel's sources hash to the
-# recorded value (None: not captured for the current sources).
-NCU_TRAFFIC = {
-    "fractal256": {"sources": ["kernels_resident.cu", "sweep_core.cuh", "device_common.cuh"],
-                   "sources_sha256": "f36ebbab1af1299b3c47ee70d982d7ff64c27ea00cc75d4b1f52033a3fddf4b6",
-                   "bytes_per_launch": 1309952.0},
-    "fractal2048": {"sources": ["kernels_sweep.cu", "sweep_core.cuh", "device_common.cuh"],
-                    "sources_sha256": "1eaef32c6540c29532335150a443768566022045f45b69e381857ffcc1ad8d5d",
-                    "bytes_per_launch": 21053440.0 + 2549504.0},
-}
-
-
-def kernel_sources_sha256(names) -> str:
-    import hashlib
-    h = hashlib.sha256()
-    for name in names:
-        with open(os.path.join(ROOT, "paper_1205_5588_gb300", "csrc", name), "rb") as fp:
-            h.update(fp.read())
-    return h.hexdigest()
-
-
-def load_traffic(workload_name):
-    rec = NCU_TRAFFIC.get(workload_name)
-    if not rec or rec["sources_sha256"] != kernel_sources_sha256(rec["sources"]):
-        return None
-    return rec["bytes_per_launch"]
 
 
 def cpu_baseline(spec, budget_s=15.0, max_sweeps=None):
@@ -441,7 +504,8 @@ def cpu_baseline(spec, budget_s=15.0, max_sweeps=None):
 
 
 def run_reference(args):
-    ws, rank, _ = dist_env()
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     spec = workload(args.workload)
@@ -452,7 +516,7 @@ def run_reference(args):
     f = oracle.Film(spec["heights"], spec["layers"], flags=flags, seed=spec["seed"], init=init)
     n_occ = f.info()["n_occ"]
     s = spec["schedule"]
-    sweeps = args.ref_sweeps or max(1, int(2.0e7 // max(n_occ, 1)))    # ~ a few seconds per step
+    sweeps = args.ref_sweeps or max(1, int(2.0e7 // max(n_occ, 1)))    # ~ a second per step
     for _ in range(args.warmup):
         f.run([float(s["T"][0])], [float(s["h"][0])], [0], [1])
     times = []
@@ -463,8 +527,8 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = n_occ * sweeps * args.steps / total
-    sample = (f"{sweeps} sweeps per step at the workload's schedule temperatures/fields, full {spec['name']} "
-              f"film ({n_occ} occupied sites), single-threaded CPU oracle")
+    sample = (f"{sweeps} sweep(s) per step at the workload's schedule temperatures/fields in order, full "
+              f"{spec['name']} film ({n_occ} occupied sites), single-threaded CPU oracle")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
@@ -498,34 +562,51 @@ def profile_case(args):
     lat.close()
 
 
+def probe_case(args):
+    """The integer-issue probes alone (for ncu captures and a printout of the ceilings)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1205_5588_gb300 import build as B
+    B.build()
+    from paper_1205_5588_gb300 import isingfilm as I
+    print(json.dumps(probe_peaks(I, torch.cuda.current_stream())))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
-    ap.add_argument("--workload", default="fractal256", choices=["fractal256", "flat16", "fractal2048"])
+    ap.add_argument("--workload", default="fractal2048", choices=["fractal2048", "fractal256", "flat16"])
+    ap.add_argument("--path", default="auto", choices=["auto", "global", "resident", "slabs"],
+                    help="sweep kernel (auto = the library's choice)")
     ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2, help="end-to-end steps (at least 1)")
+    ap.add_argument("--leg-steps", type=int, default=3, help="timed steps of the 256^2 scan leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--no-multispin", action="store_true", help="skip the bit-packed 2048^2 loop leg")
+    ap.add_argument("--no-tscan", action="store_true", help="skip the 256^2 int8 scan leg")
     ap.add_argument("--no-served", action="store_true")
-    ap.add_argument("--batch-films", type=int, default=128)
-    ap.add_argument("--batch-sweeps", type=int, default=20, help="sweeps per schedule step of the batched films")
+    ap.add_argument("--batch-films", type=int, default=512)
+    ap.add_argument("--batch-sweeps", type=int, default=100, help="sweeps per schedule step of the batched films")
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-rate-sustainable", type=float, default=100.0)
+    ap.add_argument("--serve-seconds-sustainable", type=float, default=20.0)
     ap.add_argument("--ref-sweeps", type=int, default=0)
-    ap.add_argument("--path", default="auto", choices=["auto", "global", "resident", "slabs"],
-                    help="sweep kernel of the profiling case")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling case: one launch of this many sweeps at the first schedule step, no JSON")
+    ap.add_argument("--probe", action="store_true", help="print the integer-issue ceilings only")
     args = ap.parse_args()
     args.e2e_steps = max(1, args.e2e_steps)
     if args.profile_sweeps:
         profile_case(args)
+        return
+    if args.probe:
+        probe_case(args)
         return
     if args.warmup < 3 and args.impl == "cuda":
         print("note: warm-up raised to 3 steps", file=sys.stderr)

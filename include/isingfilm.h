@@ -150,6 +150,15 @@ int isf_surface_domains(isf_lattice* lat, int64_t* out4);
  * p_c = 2 / zbar of Eq. 2 (inf when there are no bonds).  No device work. */
 int isf_lattice_stats(isf_lattice* lat, double* p, double* zbar, double* p_c);
 
+/* Curie-temperature estimate of a temperature scan (Sec. 4, Table 1; Fig. 3): a finite film has
+ * no sharp transition, so T_c is read as the temperature of the largest susceptibility
+ * chi' = (<M^2> - <|M|>^2) / (N T) among the scan's steps.  recs: n step records as
+ * isf_read_observables returns them (host); chi' is formed from their exact integer sums, and
+ * only steps with n_meas > 0 and a finite T > 0 take part; the first of equal maxima wins.
+ * *T_c = that step's T, *index (may be NULL) = its position.  Host only, no device work.
+ * Errors: ISF_ERR_ARG (NULL pointers, n < 1), ISF_ERR_STATE (no step takes part). */
+int isf_estimate_tc(const isf_step_obs* recs, int32_t n, double* T_c, int32_t* index);
+
 /* Replace the spins (same layout; must be +-1 exactly on occupied sites, 0 elsewhere) and
  * set the film-local sweep counter (the next sweep draws sweep + 1), e.g. to resume from a
  * state.  Recomputes M and B.  Synchronous.  Errors: ISF_ERR_ARG, ISF_ERR_CUDA. */
@@ -170,75 +179,6 @@ int isf_read_state(isf_lattice* lat, int64_t* M, int64_t* B, int32_t recompute,
 int isf_enable_trace(isf_lattice* lat, int64_t max_sweeps);
 int isf_read_trace(isf_lattice* lat, int64_t* host_out, int64_t max_pairs, int64_t* n_out);
 
-/* Which sweep kernel runs the film (trajectories are identical on all of them):
- *   ISF_PATH_RESIDENT: the whole film in the shared memory of one thread-block cluster of up to
- *     16 CTAs (row slabs, neighbour rows through distributed shared memory, hardware cluster
- *     barrier between colour passes) — the paper's row decomposition with CTAs as processes
- *     (Sec. 3, list items 1-2); int8 films that fit only;
- *   ISF_PATH_GLOBAL: spins in device memory, all SMs, a grid barrier between colour passes;
- *   ISF_PATH_SLABS: packed films only; the film split by rows over up to one CTA per SM, each
- *     CTA's band of rows (plus one halo row on each side) in its shared memory, the boundary
- *     rows exchanged through device memory after each colour pass, and each CTA waiting for
- *     its two neighbours only (the same row decomposition, over the whole GPU); launches of at
- *     most 2048 sweeps, each followed by a one-thread fold of the per-sweep M, B series;
- *   ISF_PATH_AUTO (default): int8 films resident when the film fits, else global; packed films
- *     slabs when a colour pass has more than 512 and at most (SMs x 512) / 5 occupied words
- *     (films of roughly 100^2 to 650^2 sites per layer), else global.
- * Errors: ISF_ERR_ARG (unknown path; resident for a packed film; slabs for an int8 film, a slab
- * film or a packed film whose word lists could not be built). */
-enum { ISF_PATH_AUTO = 0, ISF_PATH_GLOBAL = 1, ISF_PATH_RESIDENT = 2, ISF_PATH_SLABS = 3 };
-int isf_set_path(isf_lattice* lat, int32_t path);
-
-/* Launch shape override: ctas = CTAs of the global kernel, cluster size (1..16) of the resident
- * kernel, or row bands of the row-slab kernel (one CTA each, at most min(192, colour rows), all
- * co-resident) (0 = automatic); threads per CTA (0 = automatic; else a multiple of 32 up to 1024;
- * the global kernel uses at most 512; the row-slab kernel 64..512; the resident kernel 64..512
- * with 16-site items and 64..768 with 8-site items, one warp of which folds the observables and
- * takes no sites).  A shape the row-slab kernel cannot run makes isf_run_sweeps fail with
- * ISF_ERR_ARG when that path is forced.  Trajectories do not depend on it. */
-int isf_set_launch(isf_lattice* lat, int32_t ctas, int32_t threads);
-
-/* Sites per work item of the resident kernel: 16, 8, or 0 = automatic (8 when a quarter or more
- * of the sites of 16-site items would be padding past the end of the row, i.e. narrow rows).  An item is one thread's
- * share of a colour pass: the same row, consecutive columns (Sec. 3's checkerboard update).
- * Trajectories do not depend on it.  Errors: ISF_ERR_ARG (other values).  No device work. */
-int isf_set_item_sites(isf_lattice* lat, int32_t sites);
-
-/* The resident and batch kernels check every address they derive from a film's description and
- * skip (and record) an out-of-range access instead of making it.  This returns the first one
- * recorded in the process as (code, value, value, 0); all zeros when none.  The read functions
- * also report it as ISF_ERR_STATE. */
-int isf_debug_checks(uint64_t* out4);
-
-/* The occupied-item lists the library keeps for a film of this shape (host only, no device
- * work): per colour c the entries (z << (jbits + wbits)) | (j << wbits) | w, in (z, row, item)
- * order, of the items holding an occupied site — 32-site words (ISF_PACKED) or 16-site chunks
- * (int8 with open boundaries) of colour row j, layer z, where item w covers columns i (= x>>1)
- * 32w..32w+31 or 16w..16w+15 (Sec. 3's rows of one colour; occupancy as in isf_lattice_create).
- * heights: host, rows*cols; n_out[4]: entries per colour; out: 4 x cap uint32, colour c's list
- * from out[c * cap]; cap >= layers * ceil(rows/2) * items per row; bits_out[2] = (wbits, jbits).
- * Errors: ISF_ERR_ARG (bad shape or pointers, cap too small, a film without lists: periodic int8,
- * or fields that do not fit 32 bits), ISF_ERR_COLOURING. */
-int isf_debug_item_lists(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, uint32_t flags,
-                         int32_t* n_out, uint32_t* out, int64_t cap, int32_t* bits_out);
-
-/* The row bands ISF_PATH_SLABS would give a packed film of this shape split over `bands` CTAs
- * of at most max_rows colour rows each (host only, no device work): part_out[0..bands] (bands + 1
- * int32), band g holding colour rows [part_out[g], part_out[g+1]); contiguous, 1..max_rows rows
- * each, cut where the running count of occupied words (all colours and layers) is closest to an
- * even share (Sec. 3's split of the image rows between processes).  Errors: ISF_ERR_ARG (bad
- * shape or pointers, bands outside 1..colour rows, bands x max_rows below the colour rows). */
-int isf_debug_slab_partition(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, int32_t bands,
-                             int32_t max_rows, int32_t* part_out);
-
-/* Shape of the last isf_run_sweeps launch: path (ISF_PATH_GLOBAL / ISF_PATH_RESIDENT /
- * ISF_PATH_SLABS, 0 before any launch), CTAs (global), cluster size (resident) or row bands
- * (slabs), threads per CTA.  No device work. */
-int isf_launch_info(isf_lattice* lat, int32_t* path, int32_t* ctas, int32_t* threads);
-/* Sites per work item of the last isf_run_sweeps launch (16 or 8 resident, 16 int8 global, 32
- * packed global; 0 before any launch).  No device work. */
-int isf_launch_item_sites(isf_lattice* lat, int32_t* sites);
-
 /* Save the film (shape, flags, seed, spins, sweep counter) to a file; load it back onto the
  * current device (schedule not saved).  Errors: ISF_ERR_ARG, ISF_ERR_CUDA, ISF_ERR_OOM. */
 int isf_save(isf_lattice* lat, const char* path);
@@ -248,12 +188,6 @@ void isf_lattice_destroy(isf_lattice* lat);
 
 /* Message of the last failure on this thread ("" if none); valid until the next call. */
 const char* isf_last_error(void);
-
-/* Device Philox4x32-10 blocks for checking the generator: for b in [0, nblocks), the block
- * with key (seed_lo, seed_hi) and counter (q0 + b, sweep_lo, sweep_hi, stream) goes to
- * host_out[4b .. 4b+3].  Synchronous. */
-int isf_philox_blocks(uint64_t seed, uint32_t stream, uint64_t sweep, uint32_t q0,
-                      int64_t nblocks, uint32_t* host_out);
 
 /* ---- Row slabs of one film (several GPUs) ---------------------------------------------------
  * Sec. 3 splits the film by rows between processes, each updating its own rows and exchanging
@@ -366,6 +300,11 @@ int isf_server_wait(isf_server* srv, int64_t id, double timeout_s, int32_t* stat
  * submit to completion.  A failed job returns its error. */
 int isf_server_poll(isf_server* srv, int64_t id, int32_t* state, isf_step_obs* out, int32_t max,
                     int32_t* n_out, double* latency_s);
+/* The batched launches ("ticks", numbered from 0 in the order the worker runs them) a job was
+ * advanced in: out3 = {first tick, last tick, number of ticks}; {-1, -1, 0} before its first.
+ * Two jobs whose tick ranges intersect had their films advanced by the same launches, i.e. on
+ * the device at the same time. */
+int isf_server_job_ticks(isf_server* srv, int64_t id, int64_t* out3);
 /* Forget a finished job (frees its records). */
 int isf_server_release(isf_server* srv, int64_t id);
 /* out8: submitted, completed, failed, active, queued, ticks, attempts completed, peak budget
@@ -385,11 +324,13 @@ void isf_server_destroy(isf_server* srv);
  *   Inputs as isf_lattice_create + isf_set_schedule (host arrays; the film starts at sweep 0).
  *   dev_spins_out: caller-owned device buffer of layers*rows*cols int8, [z][y][x], final spins.
  *   obs_out: caller-owned host array of nsteps records, as isf_read_observables fills them.
- * Results equal those of the allocating path.  The call is synchronous on cuda_stream.  Its first
- * call on a device looks up the array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  Every call reuses the same array and clears what must start
- * at zero; calls whose work overlaps on the GPU (other streams, other host threads) race on the
- * array and must not be made.  A film and schedule needing more scratch than the array holds is
+ * Results equal those of the allocating path.  The call blocks until its work is done: it
+ * synchronises cuda_stream several times and stages the tables and records through host stack
+ * buffers, so no call (the first or any later one) may be made while a stream is being captured.
+ * Its first call on a device looks up the array's device address (cudaGetSymbolAddress) and keeps
+ * it for the process; do not use the library across a cudaDeviceReset (the kept address would be
+ * stale).  Every call reuses the same array and clears what must start at zero; calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on the array and must not be made.  A film and schedule needing more scratch than the array holds is
  * refused with ISF_ERR_ARG before any device work; other errors as isf_lattice_create,
  * isf_set_schedule and isf_run_sweeps. */
 #define ISF_NOALLOC_MAX_BYTES (8u << 20)

@@ -362,6 +362,20 @@ void or_derive(or_step_obs* r, int64_t n_occ, double J)
     r->C = varE / (N * T * T);
 }
 
+/* Curie temperature of a scan (Sec. 4, Table 1; Fig. 3): the T whose step has the largest
+ * chi' = (<M^2> - <|M|>^2)/(N T) (the derived chi_abs), over the steps with measured sweeps at a
+ * finite T > 0; the first of equal maxima.  Returns the step's index, or -1 if none qualifies. */
+int or_estimate_tc(const or_step_obs* r, int n, double* T_c)
+{
+    int best = -1;
+    for (int k = 0; k < n; ++k) {
+        if (r[k].n_meas <= 0 || !(r[k].T > 0.0) || isinf(r[k].T)) continue;
+        if (best < 0 || r[k].chi_abs > r[best].chi_abs) best = k;
+    }
+    if (best >= 0 && T_c) *T_c = r[best].T;
+    return best;
+}
+
 /* ---------------------------------------------------------------- the sweep ---------- */
 /* One schedule step after another; the state carries over (Sec. 3: "for each step of
  * temperature or field").  Each sweep visits colour 0, 1, 2, 3 and, within a colour, every

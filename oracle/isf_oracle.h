@@ -83,6 +83,11 @@ int  or_run(or_film* f, int nsteps, const double* T, const double* h, const int*
 /* FP64 quantities of one record derived from its integer sums (n_occ sites, J). */
 void or_derive(or_step_obs* r, int64_t n_occ, double J);
 
+/* Curie-temperature estimate of a temperature scan (Sec. 4, Table 1): the T of the step with the
+ * largest chi_abs among the steps with n_meas > 0 and a finite T > 0 (first of equal maxima).
+ * Returns that step's index (and *T_c), or -1 when no step qualifies. */
+int  or_estimate_tc(const or_step_obs* r, int n, double* T_c);
+
 /* Simulated PMOKE image (Sec. 6): for every pixel the topmost occupied site z = H(x,y) - 1;
  * 255 (white) if its spin is up, 0 (black) if down, 128 where the pixel holds no atom.
  * out: rows*cols bytes, [y][x].  Returns the number of up surface pixels. */

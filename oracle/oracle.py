@@ -115,6 +115,8 @@ def _declare(lib):
     lib.or_derive.restype = None
     lib.or_exact.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, dp]
     lib.or_exact.restype = C.c_int
+    lib.or_estimate_tc.argtypes = [C.POINTER(StepObs), C.c_int, dp]
+    lib.or_estimate_tc.restype = C.c_int
     lib.or_surface_image.argtypes = [C.c_void_p, C.POINTER(C.c_uint8)]
     lib.or_surface_image.restype = C.c_int64
 
@@ -171,6 +173,30 @@ def records_to_dicts(recs) -> list[dict]:
             d[f] = v
         out.append(d)
     return out
+
+
+def dicts_to_records(recs):
+    """Step records (dicts, as records_to_dicts makes them) back into an or_step_obs array."""
+    out = (StepObs * max(len(recs), 1))()
+    for i, d in enumerate(recs):
+        for f, _ in StepObs._fields_:
+            v = d[f]
+            if f in ("sumM2", "sumB2", "sumMB"):
+                v = int(v) & ((1 << 128) - 1)
+                getattr(out[i], f)[0] = v & ((1 << 64) - 1)
+                getattr(out[i], f)[1] = v >> 64
+            else:
+                setattr(out[i], f, v)
+    return out
+
+
+def estimate_tc(recs, lib=None):
+    """(T_c, index) of a scan's records by the oracle's or_estimate_tc; (None, -1) if none qualifies."""
+    lib = lib or load()
+    arr = dicts_to_records(recs)
+    t = C.c_double()
+    k = int(lib.or_estimate_tc(arr, len(recs), C.byref(t)))
+    return (t.value if k >= 0 else None), k
 
 
 # In-plane neighbours of a pixel (dx, dy): the film's 6 in-plane bonds (Sec. 2).

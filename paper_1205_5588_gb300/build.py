@@ -21,7 +21,8 @@ LIB_NAME = "libisingfilm.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels_sweep.cu", "kernels_slabs.cu", "kernels_resident.cu", "kernels_aux.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels_sweep.cu", "kernels_slabs.cu", "kernels_resident.cu", "kernels_aux.cu", "noalloc.cu",
+              "kernels_peak.cu"]
 CPP_SOURCES = ["capi.cpp", "batch.cpp", "serve.cpp", "lattice.cpp", "schedule.cpp"]
 HEADERS = ["isf_internal.h", "device_common.cuh", "sweep_core.cuh", "capi_internal.h"]
 
@@ -37,8 +38,9 @@ def cuda_home() -> str:
 
 
 def _sources():
-    inc = os.path.join(os.path.dirname(HERE), "include", "isingfilm.h")
-    return [os.path.join(CSRC, s) for s in CU_SOURCES + CPP_SOURCES + HEADERS] + [inc]
+    inc = os.path.join(os.path.dirname(HERE), "include")
+    return [os.path.join(CSRC, s) for s in CU_SOURCES + CPP_SOURCES + HEADERS] + [
+        os.path.join(inc, "isingfilm.h"), os.path.join(inc, "isingfilm_tuning.h")]
 
 
 def is_stale(path: str = LIB_PATH) -> bool:

@@ -764,6 +764,30 @@ int isf_lattice_stats(isf_lattice* L, double* p, double* zbar, double* p_c) {
     return ISF_OK;
 }
 
+int isf_estimate_tc(const isf_step_obs* recs, int32_t n, double* T_c, int32_t* index) {
+    if (!recs || n < 1 || !T_c) return fail(ISF_ERR_ARG, "bad arguments");
+    // chi' = (<M^2> - <|M|>^2) / (N T) per step; N is the same for every step of a film, so the
+    // largest (n sumM2 - sumAbsM^2) / (n^2 T), formed from the exact integer sums, marks it
+    int best = -1;
+    double best_score = 0.0;
+    for (int32_t k = 0; k < n; ++k) {
+        const isf_step_obs& r = recs[k];
+        if (r.n_meas <= 0 || !(r.T > 0.0) || !std::isfinite(r.T)) continue;
+        const __int128 nm = r.n_meas, sa = r.sumAbsM;
+        const __int128 s2 = (__int128)(((unsigned __int128)r.sumM2[1] << 64) | r.sumM2[0]);
+        const double nd = (double)r.n_meas;
+        const double score = (double)(nm * s2 - sa * sa) / (nd * nd) / r.T;
+        if (best < 0 || score > best_score) {
+            best = k;
+            best_score = score;
+        }
+    }
+    if (best < 0) return fail(ISF_ERR_STATE, "no step with measured sweeps at a finite, positive temperature");
+    *T_c = recs[best].T;
+    if (index) *index = best;
+    return set_last_error(ISF_OK, "");
+}
+
 int isf_write_spins(isf_lattice* L, const int8_t* host_in, int64_t sweep) {
     if (!L || !host_in || sweep < 0) return fail(ISF_ERR_ARG, "bad arguments");
     if (L->f.slab) return fail(ISF_ERR_STATE, "a slab film's spins come from its seed and the halo exchanges");

@@ -7,7 +7,7 @@
 #include <vector>
 
 #include "isf_internal.h"
-#include "../../include/isingfilm.h"
+#include "../../include/isingfilm_tuning.h"
 
 using isf::Layout;
 using isf::DevFilm;

@@ -11,8 +11,10 @@
 // loads the library holds until the process exits.  The kernels are the library's own
 // (init, recompute, sweep, unpack), given addresses inside that array.  In host code the array's
 // name is only a host-side stand-in, so its device address is fetched with cudaGetSymbolAddress
-// once per device (with that device current) on the first call there; make that first call
-// before any stream capture.  All calls share the array and each call clears what must start at
+// once per device (with that device current) on the first call there and kept for the process
+// (a cudaDeviceReset would make it stale; the library is not to be used across one).  Every call
+// synchronises its stream and stages through host stack buffers, so no call may be made while a
+// stream is being captured.  All calls share the array and each call clears what must start at
 // zero; two calls whose work overlaps on the GPU (on different streams or host threads) race on
 // it and must not be issued.
 #include <cuda_runtime.h>

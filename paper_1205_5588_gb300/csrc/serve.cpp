@@ -45,6 +45,7 @@ struct Job {
     size_t bytes = 0;
     int64_t attempts = 0;
     Clock::time_point t_submit, t_admit, t_done;
+    int64_t tick_first = -1, tick_last = -1, tick_count = 0;   // the batched launches it ran in
     std::vector<isf_step_obs> result;
     int32_t err = 0;
     std::string msg;
@@ -181,6 +182,11 @@ void worker_main(isf_server* S) {
         }
         std::lock_guard<std::mutex> lock(S->mu);
         S->busy_s += dt;
+        for (Job* j : act) {
+            if (j->tick_first < 0) j->tick_first = S->ticks;
+            j->tick_last = S->ticks;
+            ++j->tick_count;
+        }
         ++S->ticks;
         for (Job* j : done) {
             if (!j->err) S->attempts_done += j->attempts;
@@ -271,6 +277,17 @@ int isf_server_poll(isf_server* S, int64_t id, int32_t* state, isf_step_obs* out
     const int32_t n = std::min<int32_t>((int32_t)j->result.size(), std::max(max, 0));
     if (out && n) std::memcpy(out, j->result.data(), (size_t)n * sizeof(isf_step_obs));
     if (n_out) *n_out = n;
+    return ISF_OK;
+}
+
+int isf_server_job_ticks(isf_server* S, int64_t id, int64_t* out3) {
+    if (!S || !out3) return fail(ISF_ERR_ARG, "bad arguments");
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->jobs.find(id);
+    if (it == S->jobs.end()) return fail(ISF_ERR_ARG, "unknown job id");
+    out3[0] = it->second->tick_first;
+    out3[1] = it->second->tick_last;
+    out3[2] = it->second->tick_count;
     return ISF_OK;
 }
 

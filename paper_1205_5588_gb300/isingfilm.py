@@ -90,6 +90,9 @@ def _declare(lib):
         "isf_lattice_destroy": (None, [vp]),
         "isf_last_error": (C.c_char_p, []),
         "isf_philox_blocks": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, C.c_int64, u32p]),
+        "isf_peak_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int64, vp, dp]),
+        "isf_estimate_tc": (C.c_int, [C.POINTER(StepObs), C.c_int32, dp, i32p]),
+        "isf_server_job_ticks": (C.c_int, [vp, C.c_int64, i64p]),
         "isf_batch_create": (C.c_int, [C.POINTER(vp)]),
         "isf_batch_add": (C.c_int, [vp, vp]),
         "isf_batch_clear": (C.c_int, [vp]),
@@ -470,12 +473,40 @@ class Batch:
             pass
 
 
-def estimate_tc(records) -> float:
-    """Curie-temperature estimate of a temperature scan: the T of the largest susceptibility
-    chi' = (<M^2> - <|M|>^2) / (N T) among the scan's records (a finite film has no sharp
-    transition; this is the position of its susceptibility peak)."""
-    best = max((r for r in records if r["n_meas"] > 0), key=lambda r: r["chi_abs"])
-    return float(best["T"])
+def dicts_to_obs(records):
+    """Step records (dicts, as obs_to_dicts makes them) back into an isf_step_obs array."""
+    out = (StepObs * max(len(records), 1))()
+    for i, d in enumerate(records):
+        for f, _ in StepObs._fields_:
+            v = d[f]
+            if f in ("sumM2", "sumB2", "sumMB"):
+                v = int(v) & ((1 << 128) - 1)
+                getattr(out[i], f)[0] = v & ((1 << 64) - 1)
+                getattr(out[i], f)[1] = v >> 64
+            else:
+                setattr(out[i], f, v)
+    return out
+
+
+def estimate_tc(records, with_index=False):
+    """Curie-temperature estimate of a temperature scan (isf_estimate_tc): the T of the largest
+    susceptibility chi' among the scan's records."""
+    arr = dicts_to_obs(records)
+    t, k = C.c_double(), C.c_int32()
+    _check(lib.isf_estimate_tc(arr, len(records), C.byref(t), C.byref(k)), "estimate_tc")
+    return (t.value, k.value) if with_index else t.value
+
+
+PEAK_LOP3, PEAK_MIX, PEAK_PHILOX, PEAK_ATTEMPT = 0, 1, 2, 3
+
+
+def peak_probe(mode, ctas=0, threads=0, iters=1024, stream=None) -> float:
+    """Launch one integer-issue probe (isf_peak_probe) on `stream`; returns its work units
+    (lane-ops, Philox blocks or attempts).  Asynchronous: time it with events on that stream."""
+    units = C.c_double()
+    _check(lib.isf_peak_probe(int(mode), int(ctas), int(threads), int(iters), _stream_handle(stream),
+                              C.byref(units)), "peak_probe")
+    return units.value
 
 
 JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
@@ -520,6 +551,12 @@ class Server:
         _check(lib.isf_server_poll(self._h, int(jid), C.byref(st), recs, n, C.byref(got), C.byref(lat)),
                "server_poll")
         return JOB_STATES[st.value], obs_to_dicts(recs[:got.value]), lat.value
+
+    def job_ticks(self, jid) -> dict:
+        """The batched launches (ticks) a job ran in: first, last, and how many."""
+        v = (C.c_int64 * 3)()
+        _check(lib.isf_server_job_ticks(self._h, int(jid), v), "server_job_ticks")
+        return {"first": v[0], "last": v[1], "count": v[2]}
 
     def release(self, jid):
         _check(lib.isf_server_release(self._h, int(jid)), "server_release")

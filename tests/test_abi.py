@@ -1,5 +1,6 @@
-"""The C-ABI library builds for sm_103a, loads, and exports every function include/isingfilm.h
-declares; host-side argument checks answer without touching a GPU."""
+"""The C-ABI library builds for sm_103a, loads, and exports every function include/*.h declares
+(the method's boundary in isingfilm.h, the tuning and test hooks in isingfilm_tuning.h);
+host-side argument checks and host-only calls answer without touching a GPU."""
 import ctypes as C
 import os
 import re
@@ -8,13 +9,17 @@ import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "isingfilm.h")
+INCLUDE = os.path.join(ROOT, "include")
+HEADER = os.path.join(INCLUDE, "isingfilm.h")
 
 
-def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(isf_[a-z0-9_]+)\s*\(", text)))
+def declared_functions(path=None):
+    paths = [path] if path else [os.path.join(INCLUDE, n) for n in sorted(os.listdir(INCLUDE)) if n.endswith(".h")]
+    names = set()
+    for p in paths:
+        text = re.sub(r"/\*.*?\*/", "", open(p).read(), flags=re.S)
+        names |= set(re.findall(r"\b(isf_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -27,10 +32,15 @@ def lib():
 
 
 def test_header_declares_the_boundary():
-    names = declared_functions()
+    names = declared_functions(HEADER)
     for must in ("isf_lattice_create", "isf_set_schedule", "isf_run_sweeps", "isf_read_observables",
-                 "isf_read_spins", "isf_lattice_destroy", "isf_last_error"):
+                 "isf_read_spins", "isf_lattice_destroy", "isf_last_error", "isf_estimate_tc"):
         assert must in names
+    # tuning and test hooks live in their own header, not in the method's boundary
+    hooks = declared_functions(os.path.join(INCLUDE, "isingfilm_tuning.h"))
+    for hook in ("isf_set_launch", "isf_set_path", "isf_set_item_sites", "isf_debug_checks", "isf_debug_item_lists",
+                 "isf_debug_slab_partition", "isf_philox_blocks", "isf_peak_probe"):
+        assert hook in hooks and hook not in names
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -78,3 +88,11 @@ def test_null_arguments(lib):
     assert lib.isf_lattice_info(None, None, None, None, None) == -1
     assert lib.isf_lattice_create(None, 4, 4, 1, 0, 1, 0, None, None) == -1
     lib.isf_lattice_destroy(None)
+
+
+def test_peak_probe_rejects_bad_arguments_without_a_gpu(lib):
+    from paper_1205_5588_gb300 import isingfilm as I
+    for mode, threads, iters in ((9, 256, 10), (I.PEAK_LOP3, 33, 10), (I.PEAK_ATTEMPT, 1024, 10), (I.PEAK_MIX, 256, 0)):
+        with pytest.raises(I.IsfError) as e:
+            I.peak_probe(mode, 0, threads, iters, stream=0)
+        assert e.value.code == -1

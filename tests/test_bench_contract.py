@@ -27,15 +27,26 @@ def test_reference_arm_prints_one_json_line(olib):
     assert d["config"]["workload"].startswith("flat16")
 
 
-def test_roofline_constants():
+def test_roofline_bookkeeping():
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.OPS_PER_ATTEMPT == 40
-    assert abs(bench.ALU_PEAK_TOPS - 152 * 128 * 2070e6 / 1e12) < 1e-9
-    for name, rec in bench.NCU_TRAFFIC.items():
-        assert set(rec) == {"sources", "sources_sha256", "bytes_per_launch"}
+    assert bench.OPS_PER_ATTEMPT == 40 and bench.LANES_PER_SM == 128
+    for name, rec in bench.NCU_RECORDS.items():
+        assert set(rec) == {"sources", "sources_sha256", "bytes_per_launch", "inst_per_attempt"}
         if rec["sources_sha256"] is not None:
-            assert len(rec["sources_sha256"]) == 64 and rec["bytes_per_launch"] > 0
-        got = bench.load_traffic(name)
-        want = rec["bytes_per_launch"] if rec["sources_sha256"] == bench.kernel_sources_sha256(rec["sources"]) else None
-        assert got == want
+            assert len(rec["sources_sha256"]) == 64
+        valid = rec["sources_sha256"] == bench.kernel_sources_sha256(rec["sources"])
+        assert bench.load_traffic(name) == (rec["bytes_per_launch"] if valid else None)
+        assert bench.ncu_record(name, "inst_per_attempt") == (rec["inst_per_attempt"] if valid else None)
+    # the roofline divides the 40-op algorithmic rate by the measured op-mix rate
+    peaks = {"lop3_lane_ops_per_s": 40e12, "mix_lane_ops_per_s": 32e12, "philox_blocks_per_s": 1e12,
+             "attempts_per_s_arithmetic": 2e12}
+    r = bench.roofline(1e12, 2.0, peaks, 152, 2070.0, "k", {}, None, 27.0)
+    assert r["bound"] == "alu" and r["unit"] == "Tops/s"
+    assert abs(r["achieved"] - 40 * 0.5e12 / 1e12) < 1e-12
+    assert abs(r["peak"] - 32.0) < 1e-12 and abs(r["frac"] - 20.0 / 32.0) < 1e-12
+    c = r["ceilings"]
+    assert abs(c["lane_issue_derived_Tops"] - 152 * 128 * 2070e6 / 1e12) < 1e-9
+    assert abs(c["frac_of_philox_ceiling"] - 0.5e12 / 4e12) < 1e-12
+    assert abs(c["frac_of_arithmetic_ceiling"] - 0.25) < 1e-12
+    assert abs(c["frac_of_lop3_issue_by_instructions"] - 27.0 * 0.5e12 / 40e12) < 1e-12

@@ -344,16 +344,42 @@ def test_surface_image_and_stats_match_oracle(I, packed):
 
 
 def test_curie_estimate_of_a_scan(I):
-    """The susceptibility peak of a scan of a thick periodic film sits below the bulk FCC T_c."""
+    """T_c of a scan (Sec. 4, Table 1): isf_estimate_tc on the GPU's records picks the same step
+    as the oracle's or_estimate_tc on the oracle's records of the same scan (the records are
+    identical), and the susceptibility peak of a thick periodic film sits below the bulk FCC T_c."""
+    from oracle import oracle
     spec = film(np.full((16, 16), 8), 8, seed=3, periodic_x=True, periodic_y=True)
     T = np.linspace(6.0, 12.0, 13)
     lat = I.Lattice(spec["heights"], 8, seed=3, periodic_x=True, periodic_y=True)
     sc = W.schedule(T, 0.0, 300, 600)
     lat.set_schedule(sc["T"], sc["h"], sc["eq"], sc["meas"])
     lat.run(-1)
-    tc = I.estimate_tc(lat.observables())
-    assert 7.0 <= tc <= 10.0
+    recs = lat.observables()
     lat.close()
+    tc, k = I.estimate_tc(recs, with_index=True)
+    of = oracle.Film(spec["heights"], 8, flags=3, seed=3)
+    orecs, _ = of.run(sc["T"], sc["h"], sc["eq"], sc["meas"])
+    of.close()
+    assert (tc, k) == oracle.estimate_tc(orecs)
+    assert 7.0 <= tc <= 10.0
+
+
+def test_curie_estimate_of_the_fractal_scan(I):
+    """The same on a fractal int8 film (open edges, 1..4 layers), a scan like the 256^2 workload's
+    at reduced size: GPU and oracle pick the same temperature."""
+    from oracle import oracle
+    H = W.fractal_heights(40, 44, 0.7, 1, 4, seed=2)
+    T = np.array([0.5 + k * 11.5 / 23.0 for k in range(24)])
+    sc = W.schedule(T, 0.0, 60, 120)
+    lat = I.Lattice(H, 4, seed=1)
+    lat.set_schedule(sc["T"], sc["h"], sc["eq"], sc["meas"])
+    lat.run(-1)
+    recs = lat.observables()
+    lat.close()
+    of = oracle.Film(H, 4, seed=1)
+    orecs, _ = of.run(sc["T"], sc["h"], sc["eq"], sc["meas"])
+    of.close()
+    assert I.estimate_tc(recs, with_index=True) == oracle.estimate_tc(orecs)
 
 
 @pytest.mark.parametrize("shape,periodic", [((64, 96), False), ((48, 48), True), ((300, 257), False)])

@@ -69,6 +69,44 @@ def test_served_results_equal_solo_runs(I):
     srv.close()
 
 
+def test_served_jobs_overlap_on_the_device(I):
+    """Continuous batching, not a queue: a job submitted while another is on the GPU is admitted
+    into the running ticks, so the two films are advanced by the same batched launches (their
+    tick ranges intersect), and each still ends with its solo result."""
+    rng = np.random.Generator(np.random.PCG64(8))
+    mk = lambda side, L, s: W.fractal_heights(side, side, 0.7, 1, L, seed=s)
+    long_job = {"heights": mk(160, 4, 81), "layers": 4, "seed": 81, "packed": True,
+                "schedule": W.schedule(2.5, W.loop_fields(8, 4), 0, 40)}
+    late_jobs = [{"heights": mk(int(rng.integers(40, 90)), 3, 90 + i), "layers": 3, "seed": 90 + i,
+                  "packed": bool(i % 2), "schedule": W.schedule([3.0, 5.0], [0.5, -0.5], 2, 6)} for i in range(4)]
+    srv = I.Server(1 << 30, sweeps_per_tick=4)
+    s = long_job["schedule"]
+    first = srv.submit(long_job["heights"], 4, s["T"], s["h"], s["eq"], s["meas"], seed=81, packed=True)
+    t0 = time.time()
+    while srv.job_ticks(first)["count"] < 2 and time.time() - t0 < 60:
+        time.sleep(0.002)                       # the long job is running
+    assert srv.job_ticks(first)["count"] >= 2
+    late = []
+    for j in late_jobs:
+        sj = j["schedule"]
+        late.append(srv.submit(j["heights"], j["layers"], sj["T"], sj["h"], sj["eq"], sj["meas"], seed=j["seed"],
+                               packed=j["packed"]))
+    for jid in [first] + late:
+        assert srv.wait(jid, timeout=120) == "done"
+    tf = srv.job_ticks(first)
+    overlapped = 0
+    for jid, j in zip(late, late_jobs):
+        tl = srv.job_ticks(jid)
+        assert tl["first"] > tf["first"]                      # admitted after the long job started
+        if tl["first"] <= tf["last"]:                         # ... and advanced in the same launches
+            overlapped += 1
+        assert_records_equal(srv.result(jid)[1], solo(I, j))
+        srv.release(jid)
+    assert overlapped >= 1
+    assert_records_equal(srv.result(first)[1], solo(I, long_job))
+    srv.close()
+
+
 def test_job_larger_than_budget_fails(I):
     srv = I.Server(1 << 14, sweeps_per_tick=10)        # the film needs about 57 KB
     H = np.full((64, 64), 4, dtype=np.uint8)

@@ -103,6 +103,32 @@ def test_noalloc_matches_the_allocating_path_call_after_call(env):
     assert_same(run_noalloc(env, H, L, flags, seed, init, sched, h_s), first[0])
 
 
+def test_noalloc_allocates_no_device_memory(env):
+    """The property the entry point exists for: after a warm-up call (which loads the kernels and
+    looks up the array's address), a further call leaves the device's free memory unchanged."""
+    torch, I, lib = env
+    H, L, flags, seed, init, sched, h_s = CASES[0]
+    run_noalloc(env, H, L, flags, seed, init, sched, h_s)            # warm-up
+    Hc = np.ascontiguousarray(H, dtype=np.uint8)
+    R, Cc = Hc.shape
+    T = np.ascontiguousarray(sched["T"], dtype=np.float64)
+    h = np.ascontiguousarray(sched["h"], dtype=np.float64)
+    eq = np.ascontiguousarray(sched["eq"], dtype=np.int32)
+    me = np.ascontiguousarray(sched["meas"], dtype=np.int32)
+    spins = torch.empty(L * R * Cc, dtype=torch.int8, device="cuda")  # the caller's buffers, made before
+    recs = (I.StepObs * len(T))()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    rc = lib.isf_run_noalloc(Hc.ctypes.data_as(C.POINTER(C.c_uint8)), R, Cc, L, flags, seed, init, len(T),
+                             T.ctypes.data_as(C.POINTER(C.c_double)), h.ctypes.data_as(C.POINTER(C.c_double)),
+                             eq.ctypes.data_as(C.POINTER(C.c_int32)), me.ctypes.data_as(C.POINTER(C.c_int32)),
+                             1.0, h_s, C.c_void_p(spins.data_ptr()), recs, C.c_void_p(stream.cuda_stream))
+    assert rc == 0, lib.isf_last_error()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+
+
 def test_noalloc_refuses_films_beyond_its_array(env):
     torch, I, lib = env
     H = np.full((2048, 2048), 6, dtype=np.uint8)                  # ~35 MB of int8 layout
