@@ -40,7 +40,7 @@ UNIT = "attempts/s"
 # Philox4x32-10 block (10 rounds x (2 32x32->64 multiplies + 4 XORs + 2 key adds) / 4 = 25), the
 # 12-neighbour sum (12) and the acceptance test and update (5).
 OPS_PER_ATTEMPT = 40
-LANES_PER_SM = 128          # int32 lanes: 4 sub-partitions x 32, one warp instruction per clock each
+LANES_PER_SM = 128          # dispatch: 4 sub-partitions x one 32-lane warp instruction per clock
 
 
 def workload(name: str):
@@ -147,11 +147,12 @@ def probe_peaks(I, stream, target_s=0.05, reps=3) -> dict:
 
 
 def roofline(attempts_per_launch, t_launch, peaks, sms, sm_max_mhz, kernel, shape, traffic, inst_per_attempt):
-    """ALU roofline of one sweep launch: achieved = 40 algorithmic int-ops per attempt / launch
-    time; peak = the integer-op mix rate measured in this run (isf_peak_probe)."""
+    """ALU roofline of one sweep launch, both sides in the algorithmic unit (40 int-ops per
+    attempt): achieved = 40 x attempts / launch time; peak = 40 x the attempts/s this GPU reaches
+    on the per-attempt arithmetic alone (isf_peak_probe ISF_PEAK_ATTEMPT, measured in this run)."""
     rate = attempts_per_launch / t_launch
     achieved = OPS_PER_ATTEMPT * rate / 1e12
-    peak = peaks["mix_lane_ops_per_s"] / 1e12
+    peak = OPS_PER_ATTEMPT * peaks["attempts_per_s_arithmetic"] / 1e12
     derived = sms * LANES_PER_SM * sm_max_mhz * 1e6 if sm_max_mhz else None
     ceil = {
         "sms": sms, "sm_max_mhz": sm_max_mhz,
@@ -166,12 +167,15 @@ def roofline(attempts_per_launch, t_launch, peaks, sms, sm_max_mhz, kernel, shap
         "inst_per_attempt": inst_per_attempt,
         "frac_of_lop3_issue_by_instructions": (inst_per_attempt * rate / peaks["lop3_lane_ops_per_s"]
                                                if inst_per_attempt else None),
+        "frac_of_dispatch_by_instructions": (inst_per_attempt * rate / derived if inst_per_attempt and derived
+                                             else None),
     }
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": kernel, "launch": shape, "ops_per_attempt": OPS_PER_ATTEMPT,
-            "peak_from": "measured in this run on this GPU: the integer op mix of the random-number work "
-                         "(32x32->64 multiply, XOR3, majority, add; one instruction each) register-only on "
-                         "all SMs (isf_peak_probe ISF_PEAK_MIX), CUDA events, best of 3",
+            "peak_from": "measured in this run on this GPU: 40 x the attempts/s of the per-attempt integer "
+                         "arithmetic alone (a 32-site word's 8 Philox4x32-10 blocks, bit-sliced neighbour count, "
+                         "table lookups and compares; registers only, all SMs, no film loads, no barriers; "
+                         "isf_peak_probe ISF_PEAK_ATTEMPT), CUDA events, best of 3",
             "ceilings": ceil}
 
 
@@ -563,13 +567,26 @@ def profile_case(args):
 
 
 def probe_case(args):
-    """The integer-issue probes alone (for ncu captures and a printout of the ceilings)."""
+    """The integer-issue probes alone: the ceilings as the bench measures them, or (with
+    --probe-iters) one launch of each probe of that many iterations, for ncu captures."""
     import torch
     torch.cuda.set_device(0)
     from paper_1205_5588_gb300 import build as B
     B.build()
     from paper_1205_5588_gb300 import isingfilm as I
-    print(json.dumps(probe_peaks(I, torch.cuda.current_stream())))
+    stream = torch.cuda.current_stream()
+    if not args.probe_iters:
+        print(json.dumps(probe_peaks(I, stream)))
+        return
+    out = {}
+    for mode, threads in ((I.PEAK_LOP3, 1024), (I.PEAK_MIX, 1024), (I.PEAK_PHILOX, 512), (I.PEAK_ATTEMPT, 512)):
+        a, b = events()
+        a.record(stream)
+        units = I.peak_probe(mode, 0, threads, args.probe_iters, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        out[mode] = {"units": units, "seconds": a.elapsed_time(b) / 1e3}
+    print(json.dumps(out))
 
 
 def main():
@@ -600,12 +617,14 @@ def main():
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling case: one launch of this many sweeps at the first schedule step, no JSON")
     ap.add_argument("--probe", action="store_true", help="print the integer-issue ceilings only")
+    ap.add_argument("--probe-iters", type=int, default=0,
+                    help="with --probe: one launch of each probe of this many iterations per thread")
     args = ap.parse_args()
     args.e2e_steps = max(1, args.e2e_steps)
     if args.profile_sweeps:
         profile_case(args)
         return
-    if args.probe:
+    if args.probe or args.probe_iters:
         probe_case(args)
         return
     if args.warmup < 3 and args.impl == "cuda":

@@ -400,6 +400,155 @@ __global__ void __launch_bounds__(kBlock) k_sweep(const __grid_constant__ SweepA
     sweep_body<MODE>(a, gridDim.x, blockIdx.x);
 }
 
+// ---- packed films with occupied-word lists on the whole grid: random words drawn ahead -----
+// A colour pass of a packed film is half Philox arithmetic (8 blocks per 32-site word), and
+// the counters of a pass's words are known before the pass: they depend on the word and the
+// sweep, not on the spins.  So while a CTA waits at the grid barrier that ends pass c, its
+// threads draw the Philox blocks of their words of pass c + 1 into shared memory (the first
+// four blocks of each word, and the last four too when the step's table says nearly every word
+// needs them), and the pass itself only loads, counts, looks up and compares.  A thread keeps
+// kAheadSlots words this way; further words of a pass (small grids) draw in the pass.
+constexpr int kAheadSlots = 2;
+
+// Bytes of dynamic shared memory of k_words with this block size.
+constexpr size_t ahead_bytes(int threads) { return (size_t)kAheadSlots * 8 * (size_t)threads * sizeof(uint4); }
+
+// The Philox blocks of this thread's first kAheadSlots words of colour c at `sweep` into its
+// slots of `ahead` ([slot][block][thread] uint4); the second four blocks only when `both`.
+__device__ __forceinline__ void draw_ahead(const DevFilm& f, int c, unsigned long long sweep, bool both, int it0,
+                                           int stride, uint4* ahead) {
+    const uint2* ent = reinterpret_cast<const uint2*>(f.ient) + (int64_t)c * f.item_cap;
+    const int n = f.nitems[c];
+    const int bd = blockDim.x, tid = threadIdx.x;
+    int it = it0;
+#pragma unroll 1
+    for (int slot = 0; slot < kAheadSlots && it < n; ++slot, it += stride) {
+        const uint32_t q = ent[it].y;
+        uint4 u[4];
+        philox10_xn<4>(q, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) ahead[(slot * 8 + v) * bd + tid] = u[v];
+        if (both) {
+            philox10_xn<4>(q + 4, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) ahead[(slot * 8 + 4 + v) * bd + tid] = u[v];
+        }
+    }
+}
+
+// One colour pass over this thread's listed words it0, it0 + stride, ... (their random words
+// drawn ahead in `ahead` for the first kAheadSlots; `both`: the second four blocks too).
+template <bool GATE>
+__device__ __forceinline__ void pass_words(const DevFilm& f, int c, unsigned long long sweep, const uint32_t* tab,
+                                           uint32_t gthr, bool always_draw, bool both, int it0, int stride,
+                                           const uint4* ahead, int& dM, int& dB) {
+    const uint2* ent = reinterpret_cast<const uint2*>(f.ient) + (int64_t)c * f.item_cap;
+    const uint4* vq = reinterpret_cast<const uint4*>(f.ivq) + (int64_t)c * f.item_cap;
+    const int n = f.nitems[c];
+    const int bd = blockDim.x, tid = threadIdx.x;
+    int slot = 0;
+#pragma unroll 1
+    for (int it = it0; it < n; it += stride, ++slot) {
+        const uint2 pq = ent[it];
+        const int64_t base = (int64_t)(pq.x & 0x7FFFFFFFu);
+        const NbrClass& nc = f.nb[c][pq.x >> 31];
+        uint32_t S, O, up[12], V[4];
+        packed_loads<true>(f, nc, base, S, O, up);
+        const uint4 v4 = vq[it];
+        V[0] = v4.x; V[1] = v4.y; V[2] = v4.z; V[3] = v4.w;
+        uint4 uf[4], us[4];
+        const bool drawn = slot < kAheadSlots;
+        if (drawn) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) uf[v] = ahead[(slot * 8 + v) * bd + tid];
+            if (both) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) us[v] = ahead[(slot * 8 + 4 + v) * bd + tid];
+            }
+        } else {
+            philox10_xn<4>(pq.y, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, uf);
+        }
+        const uint32_t F = packed_decide<GATE>(S, O, up, V, pq.y, sweep, tab, gthr, always_draw, f.key0, f.key1, uf,
+                                               dM, dB, (drawn && both) ? us : nullptr);
+        if (F) f.sp[base] = S ^ F;
+    }
+}
+
+template <bool GATE>
+__global__ void __launch_bounds__(kBlock) k_words(const __grid_constant__ SweepArgs a) {
+    extern __shared__ uint4 ahead[];                 // [kAheadSlots][8][blockDim]
+    __shared__ uint32_t tab[128];
+    __shared__ uint32_t gate_s[2];
+    __shared__ long long red[64];
+    __shared__ int ok_s;
+    __shared__ RunState rs;                          // touched by the folding thread only
+    const DevFilm& f = a.f;
+    FilmState* st = a.st;
+    const unsigned G = gridDim.x, cta = blockIdx.x;
+    unsigned target = 0;
+    int k = a.k0, pos = a.pos0;
+    const bool folder = cta == 0 && threadIdx.x == 0;
+    int k_eq = 0, k_tot = 0;
+    if (folder) {
+        load_run_state(st, rs);
+        k_eq = a.step_eq[k];
+        k_tot = a.step_total[k];
+    }
+    const int it0 = first_item(G, cta);
+    const int stride = (int)G * blockDim.x;
+    auto step_draws_all = [&](int kk) {
+        return (a.tables[(size_t)kk * kTableStride + kFlagSlot] & kFlagAlwaysDraw) != 0u;
+    };
+    // the first pass's random words
+    {
+        const int kf = a.pos0 == a.step_total[a.k0] ? a.k0 + 1 : a.k0;
+        if (a.nsweeps > 0) draw_ahead(f, 0, (unsigned long long)(a.sweep0 + 1), step_draws_all(kf), it0, stride, ahead);
+    }
+    stage_table<true>(a.tables, k, tab, gate_s);
+    for (long long t = 0; t < a.nsweeps; ++t) {
+        if (pos == a.step_total[k]) {
+            ++k;
+            pos = 0;
+            stage_table<true>(a.tables, k, tab, gate_s);
+            if (folder) { k_eq = a.step_eq[k]; k_tot = a.step_total[k]; }
+        }
+        const unsigned long long sweep = (unsigned long long)(a.sweep0 + t + 1);
+        const uint32_t gthr = gate_s[0];
+        const bool always_draw = (gate_s[1] & kFlagAlwaysDraw) != 0;
+        // the step of the next sweep (for the random words of its first pass)
+        const int k_next = pos + 1 == a.step_total[k] ? k + 1 : k;
+        int dM = 0, dB = 0;
+        for (int c = 0; c < 4; ++c) {
+            pass_words<GATE>(f, c, sweep, tab, gthr, always_draw, always_draw, it0, stride, ahead, dM, dB);
+            if (c == 3) {
+                long long sM = dM, sB = dB;
+                block_sum2(sM, sB, red);
+                if (threadIdx.x == 0 && (sM | sB)) {
+                    unsigned long long* acc = reinterpret_cast<unsigned long long*>(&st->acc[sweep & 1][0]);
+                    atomicAdd(acc, (unsigned long long)sM);
+                    atomicAdd(acc + 1, (unsigned long long)sB);
+                }
+            }
+            grid_arrive(st, G, target);
+            // while the other CTAs finish this pass: the random words of the next one
+            if (c < 3) {
+                draw_ahead(f, c + 1, sweep, always_draw, it0, stride, ahead);
+            } else if (t + 1 < a.nsweeps) {
+                draw_ahead(f, 0, sweep + 1, step_draws_all(k_next), it0, stride, ahead);
+            }
+            if (!grid_wait(st, G, target, &ok_s)) return;
+        }
+        if (folder) {
+            unsigned long long* acc = reinterpret_cast<unsigned long long*>(&st->acc[sweep & 1][0]);
+            const long long sM = (long long)atomicExch(acc, 0ull);
+            const long long sB = (long long)atomicExch(acc + 1, 0ull);
+            fold_sweep(a, rs, k, pos, k_eq, k_tot, sM, sB, t);
+        }
+        ++pos;
+    }
+    if (folder) store_run_state(st, rs);
+}
+
 __device__ __forceinline__ int mode_of_film(const DevFilm& f);
 
 // Batched films one thread-block cluster of K CTAs each, with their state in global memory:
@@ -456,6 +605,14 @@ __global__ void __launch_bounds__(kBlock) k_batch_global(const SweepArgs* films,
     }
 }
 
+// k_words runs packed whole films with word lists over several CTAs (grid barrier, whole sweeps).
+inline bool words_path(const DevFilm& f) { return f.packed && f.ient != nullptr && !f.slab; }
+
+template <bool GATE>
+cudaError_t words_smem_attr(int threads) {
+    return cudaFuncSetAttribute(k_words<GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ahead_bytes(threads));
+}
+
 template <int MODE>
 int launch_mode(const SweepArgs& a, int ctas, int threads, cudaStream_t s) {
     if (threads % 32 || threads < 32 || threads > kBlock) return (int)cudaErrorInvalidValue;   // whole warps
@@ -466,15 +623,34 @@ int launch_mode(const SweepArgs& a, int ctas, int threads, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(&a.st->bar_count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return (int)e;
     void* args[] = {const_cast<SweepArgs*>(&a)};
+    if (MODE == MODE_PACKED && words_path(a.f) && !a.pass_plus1) {
+        const size_t smem = ahead_bytes(threads);
+        const void* fn = a.use_gate ? (const void*)k_words<true> : (const void*)k_words<false>;
+        e = a.use_gate ? words_smem_attr<true>(threads) : words_smem_attr<false>(threads);
+        if (e != cudaSuccess) return (int)e;
+        return (int)cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(threads), args, smem, s);
+    }
     return (int)cudaLaunchCooperativeKernel((const void*)k_sweep<MODE>, dim3(ctas), dim3(threads), args, 0, s);
 }
 
 template <int MODE>
-int max_ctas_mode(int threads, int* out) {
+int max_ctas_mode(const DevFilm& f, int threads, int* out) {
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<MODE>, threads, 0);
+    if (MODE == MODE_PACKED && words_path(f)) {
+        // the gate and no-gate kernels have the same shared memory; take the smaller residency
+        int per_g = 0;
+        if (e == cudaSuccess) e = words_smem_attr<false>(threads);
+        if (e == cudaSuccess) e = words_smem_attr<true>(threads);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_words<false>, threads, ahead_bytes(threads));
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_g, k_words<true>, threads, ahead_bytes(threads));
+        per = per < per_g ? per : per_g;
+    } else if (e == cudaSuccess) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<MODE>, threads, 0);
+    }
     *out = sms * per;
     return (int)e;
 }
@@ -497,9 +673,9 @@ int launch_sweeps(const SweepArgs& a, int ctas, int threads, void* stream) {
 
 int sweep_max_ctas_for(const DevFilm& f, int threads, int* max_ctas) {
     switch (mode_of(f)) {
-        case MODE_INT8: return max_ctas_mode<MODE_INT8>(threads, max_ctas);
-        case MODE_GENERIC: return max_ctas_mode<MODE_GENERIC>(threads, max_ctas);
-        default: return max_ctas_mode<MODE_PACKED>(threads, max_ctas);
+        case MODE_INT8: return max_ctas_mode<MODE_INT8>(f, threads, max_ctas);
+        case MODE_GENERIC: return max_ctas_mode<MODE_GENERIC>(f, threads, max_ctas);
+        default: return max_ctas_mode<MODE_PACKED>(f, threads, max_ctas);
     }
 }
 

@@ -217,13 +217,15 @@ __device__ __forceinline__ void popcount12(const uint32_t* x, uint32_t& b0, uint
 // S, O: the word's spin and occupancy bits; up: the 12 neighbours' up bits per lane; V: the
 // bit-sliced count of vacant neighbours.  X = n + 12 = 2 (#up) + (#vacant) as 5 bit-planes; an
 // 8x32 bit-plane transpose gives each lane its table entry's byte offset; u_first: the word's
-// first four Philox blocks (lanes 0-15), drawn by the caller.  Returns the flip mask (vacant
-// lanes cleared) and adds the flips' dM, dB.
+// first four Philox blocks (lanes 0-15), drawn by the caller; u_second (may be null): the last
+// four (lanes 16-31) when the caller drew them too, else they are drawn here when a lane needs
+// them.  Returns the flip mask (vacant lanes cleared) and adds the flips' dM, dB.
 template <bool GATE>
 __device__ __forceinline__ uint32_t packed_decide(uint32_t S, uint32_t O, const uint32_t up[12], const uint32_t V[4],
                                                   uint32_t q0, unsigned long long sweep, const uint32_t* tab,
                                                   uint32_t gthr, bool always_draw, uint32_t key0, uint32_t key1,
-                                                  const uint4 (&u_first)[4], int& dM, int& dB) {
+                                                  const uint4 (&u_first)[4], int& dM, int& dB,
+                                                  const uint4* u_second = nullptr) {
     // X = n + 12 = 2 * (#up) + (#vacant) over the 12 neighbours, 5 bit-planes
     uint32_t U0, U1, U2, U3;
     popcount12(up, U0, U1, U2, U3);
@@ -274,9 +276,9 @@ __device__ __forceinline__ uint32_t packed_decide(uint32_t S, uint32_t O, const 
             }
         }
         // the second half draws its words only if a lane needs one (unless the step's table
-        // says nearly every group does)
+        // says nearly every group does, or the caller drew them)
         if (g) {
-            if (always_draw) {
+            if (always_draw || u_second) {
                 need = true;
             } else {
 #pragma unroll
@@ -287,6 +289,9 @@ __device__ __forceinline__ uint32_t packed_decide(uint32_t S, uint32_t O, const 
         if (g == 0) {
 #pragma unroll
             for (int vv = 0; vv < 4; ++vv) u[vv] = u_first[vv];
+        } else if (u_second) {
+#pragma unroll
+            for (int vv = 0; vv < 4; ++vv) u[vv] = u_second[vv];
         } else {
 #pragma unroll
             for (int vv = 0; vv < 4; ++vv) u[vv] = make_uint4(0, 0, 0, 0);

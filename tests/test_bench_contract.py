@@ -38,13 +38,13 @@ def test_roofline_bookkeeping():
         valid = rec["sources_sha256"] == bench.kernel_sources_sha256(rec["sources"])
         assert bench.load_traffic(name) == (rec["bytes_per_launch"] if valid else None)
         assert bench.ncu_record(name, "inst_per_attempt") == (rec["inst_per_attempt"] if valid else None)
-    # the roofline divides the 40-op algorithmic rate by the measured op-mix rate
+    # the roofline divides the 40-op algorithmic rate by 40 x the measured arithmetic-only attempt rate
     peaks = {"lop3_lane_ops_per_s": 40e12, "mix_lane_ops_per_s": 32e12, "philox_blocks_per_s": 1e12,
              "attempts_per_s_arithmetic": 2e12}
     r = bench.roofline(1e12, 2.0, peaks, 152, 2070.0, "k", {}, None, 27.0)
     assert r["bound"] == "alu" and r["unit"] == "Tops/s"
     assert abs(r["achieved"] - 40 * 0.5e12 / 1e12) < 1e-12
-    assert abs(r["peak"] - 32.0) < 1e-12 and abs(r["frac"] - 20.0 / 32.0) < 1e-12
+    assert abs(r["peak"] - 80.0) < 1e-12 and abs(r["frac"] - 20.0 / 80.0) < 1e-12
     c = r["ceilings"]
     assert abs(c["lane_issue_derived_Tops"] - 152 * 128 * 2070e6 / 1e12) < 1e-9
     assert abs(c["frac_of_philox_ceiling"] - 0.5e12 / 4e12) < 1e-12
