@@ -38,6 +38,10 @@ constexpr int kFlagSlot = 51;
 // kernels skip the test of whether a group needs them.  A scheduling hint only: the words
 // drawn and the decisions are the same either way.
 constexpr uint32_t kFlagAlwaysDraw = 1u;
+// Step flag: no threshold of the step is 0 ("never").  The packed kernel then decides a lane by
+// the carry of u + (2^32 - thr) (no carry: accepted; "always" is stored as 0), which cannot
+// encode "never".  The decisions are the same either way.
+constexpr uint32_t kFlagNoNever = 2u;
 constexpr int kMaxThreads = 1024;
 constexpr int kMaxSlabCTAs = 192;     // row-slab kernel: most CTAs (one per SM)
 constexpr int kSeriesChunk = 2048;    // row-slab kernel: most sweeps per launch

@@ -6,9 +6,10 @@
 //   MIX     the integer mix of the sweep kernels' random-number work, one op per instruction:
 //           32x32 -> 64-bit multiplies, three-input XOR / majority, 32-bit adds;
 //   PHILOX  Philox4x32-10 blocks, four interleaved per thread (the same code the sweeps use);
-//   ATTEMPT the whole arithmetic of a bit-packed 32-site word with every random word drawn
-//           (packed_decide: 8 Philox blocks, the bit-sliced neighbour count, the transpose to
-//           table offsets, 32 table lookups and comparisons, the flip mask, dM and dB).
+//   ATTEMPT the whole arithmetic of a bit-packed 32-site word with every random word drawn,
+//           in the form the packed sweep uses (8 Philox blocks with precomputed round keys and
+//           sweep parts; packed_decide: the bit-sliced neighbour count, the transpose to table
+//           offsets, 32 table lookups and carry comparisons, the flip mask, dM and dB).
 // Every chain feeds a final value that is stored only when it equals a host-chosen word, so
 // nothing is dead code and nothing but that one conditional store touches memory.
 #include <cuda_runtime.h>
@@ -100,21 +101,30 @@ __global__ void __launch_bounds__(max_threads<MODE>()) k_peak(long long iters, u
         // the packed word update of the sweep kernels, on words made from its own random draws
         __shared__ uint32_t tab[128];
         __shared__ uint32_t gate_s[2];
-        for (int t = threadIdx.x; t < 128; t += blockDim.x) tab[t] = 0x40000000u + (uint32_t)t * 0x01000193u;
-        if (threadIdx.x == 0) { gate_s[0] = kAlways; gate_s[1] = kFlagAlwaysDraw; }
+        // thresholds in 0..63, their negations (the carry form) in 64..127, as the sweeps stage them
+        for (int t = threadIdx.x; t < 128; t += blockDim.x) {
+            const uint32_t thr = 0x40000000u + (uint32_t)(t & 63) * 0x01000193u;
+            tab[t] = t < 64 ? thr : 0u - thr;
+        }
+        if (threadIdx.x == 0) { gate_s[0] = kAlways; gate_s[1] = kFlagAlwaysDraw | kFlagNoNever; }
         __syncthreads();
-        const uint32_t k0 = seed, k1 = seed ^ 0xA5A5A5A5u;
+        uint32_t rk[20];
+        round_keys(seed, seed ^ 0xA5A5A5A5u, rk);
         uint32_t q0 = tid * 8u, S = tid ^ seed;
         int dM = 0, dB = 0;
         for (long long i = 0; i < iters; ++i) {
+            // a word's 8 blocks as the packed sweep draws them (sweep-only parts once per sweep)
             const unsigned long long sweep = (unsigned long long)i + 1ull;
-            uint4 uf[4];
-            philox10_xn<4>(q0, (uint32_t)sweep, 0u, 0u, k0, k1, uf);
+            const SweepConst sc = sweep_const(sweep, rk);
+            uint4 uf[4], us[4];
+            philox10_sc<4>(q0, 0u, sc, rk, uf);
+            philox10_sc<4>(q0 + 4, 0u, sc, rk, us);
             const uint32_t up[12] = {uf[0].x, uf[0].y, uf[0].z, uf[0].w, uf[1].x, uf[1].y,
                                      uf[1].z, uf[1].w, uf[2].x, uf[2].y, uf[2].z, uf[2].w};
             const uint32_t V[4] = {uf[3].x, uf[3].y, uf[3].z, uf[3].w & 0x0F0F0F0Fu};
-            const uint32_t F = packed_decide<false>(S, 0xFFFFFFFFu, up, V, q0, sweep, tab, gate_s[0],
-                                                    (gate_s[1] & kFlagAlwaysDraw) != 0, k0, k1, uf, dM, dB);
+            const uint32_t F = packed_decide<false, true>(S, 0xFFFFFFFFu, up, V, q0, sweep, tab, gate_s[0],
+                                                          (gate_s[1] & kFlagAlwaysDraw) != 0, rk[0], rk[1], uf, dM, dB,
+                                                          us);
             S ^= F;
             q0 += 0x20000u;
         }

@@ -403,11 +403,14 @@ __global__ void __launch_bounds__(kBlock) k_sweep(const __grid_constant__ SweepA
 // ---- packed films with occupied-word lists on the whole grid: random words drawn ahead -----
 // A colour pass of a packed film is half Philox arithmetic (8 blocks per 32-site word), and
 // the counters of a pass's words are known before the pass: they depend on the word and the
-// sweep, not on the spins.  So while a CTA waits at the grid barrier that ends pass c, its
-// threads draw the Philox blocks of their words of pass c + 1 into shared memory (the first
-// four blocks of each word, and the last four too when the step's table says nearly every word
-// needs them), and the pass itself only loads, counts, looks up and compares.  A thread keeps
-// kAheadSlots words this way; further words of a pass (small grids) draw in the pass.
+// sweep, not on the spins.  So once a warp has decided its words of pass c it arrives at the
+// grid barrier (through a per-CTA counter, without waiting for the CTA's other warps) and draws
+// the Philox blocks of its words of pass c + 1 into shared memory (the first four blocks of each
+// word, and the last four too when the step's table says nearly every word needs them), and the
+// pass itself only loads, counts, looks up and compares.  The threads with fewer words in a pass
+// thus fill the time the others need for their extra word, and everyone fills the barrier's
+// latency.  A thread keeps kAheadSlots words this way; further words of a pass (small grids)
+// draw in the pass.
 constexpr int kAheadSlots = 2;
 
 // Bytes of dynamic shared memory of k_words with this block size.
@@ -416,7 +419,8 @@ constexpr size_t ahead_bytes(int threads) { return (size_t)kAheadSlots * 8 * (si
 // The Philox blocks of this thread's first kAheadSlots words of colour c at `sweep` into its
 // slots of `ahead` ([slot][block][thread] uint4); the second four blocks only when `both`.
 __device__ __forceinline__ void draw_ahead(const DevFilm& f, int c, unsigned long long sweep, bool both, int it0,
-                                           int stride, uint4* ahead) {
+                                           int stride, uint4* ahead, const uint32_t (&rk)[20]) {
+    const SweepConst sc = sweep_const(sweep, rk);
     const uint2* ent = reinterpret_cast<const uint2*>(f.ient) + (int64_t)c * f.item_cap;
     const int n = f.nitems[c];
     const int bd = blockDim.x, tid = threadIdx.x;
@@ -425,11 +429,11 @@ __device__ __forceinline__ void draw_ahead(const DevFilm& f, int c, unsigned lon
     for (int slot = 0; slot < kAheadSlots && it < n; ++slot, it += stride) {
         const uint32_t q = ent[it].y;
         uint4 u[4];
-        philox10_xn<4>(q, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u);
+        philox10_sc<4>(q, 0u, sc, rk, u);
 #pragma unroll
         for (int v = 0; v < 4; ++v) ahead[(slot * 8 + v) * bd + tid] = u[v];
         if (both) {
-            philox10_xn<4>(q + 4, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u);
+            philox10_sc<4>(q + 4, 0u, sc, rk, u);
 #pragma unroll
             for (int v = 0; v < 4; ++v) ahead[(slot * 8 + 4 + v) * bd + tid] = u[v];
         }
@@ -440,8 +444,8 @@ __device__ __forceinline__ void draw_ahead(const DevFilm& f, int c, unsigned lon
 // drawn ahead in `ahead` for the first kAheadSlots; `both`: the second four blocks too).
 template <bool GATE>
 __device__ __forceinline__ void pass_words(const DevFilm& f, int c, unsigned long long sweep, const uint32_t* tab,
-                                           uint32_t gthr, bool always_draw, bool both, int it0, int stride,
-                                           const uint4* ahead, int& dM, int& dB) {
+                                           uint32_t gthr, bool always_draw, bool both, bool no_never, int it0,
+                                           int stride, const uint4* ahead, int& dM, int& dB) {
     const uint2* ent = reinterpret_cast<const uint2*>(f.ient) + (int64_t)c * f.item_cap;
     const uint4* vq = reinterpret_cast<const uint4*>(f.ivq) + (int64_t)c * f.item_cap;
     const int n = f.nitems[c];
@@ -468,8 +472,13 @@ __device__ __forceinline__ void pass_words(const DevFilm& f, int c, unsigned lon
         } else {
             philox10_xn<4>(pq.y, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, uf);
         }
-        const uint32_t F = packed_decide<GATE>(S, O, up, V, pq.y, sweep, tab, gthr, always_draw, f.key0, f.key1, uf,
-                                               dM, dB, (drawn && both) ? us : nullptr);
+        const uint4* u2 = (drawn && both) ? us : nullptr;
+        const uint32_t F =
+            (!GATE && no_never)
+                ? packed_decide<false, true>(S, O, up, V, pq.y, sweep, tab, gthr, always_draw, f.key0, f.key1, uf,
+                                             dM, dB, u2)
+                : packed_decide<GATE>(S, O, up, V, pq.y, sweep, tab, gthr, always_draw, f.key0, f.key1, uf, dM, dB,
+                                      u2);
         if (F) f.sp[base] = S ^ F;
     }
 }
@@ -479,12 +488,20 @@ __global__ void __launch_bounds__(kBlock) k_words(const __grid_constant__ SweepA
     extern __shared__ uint4 ahead[];                 // [kAheadSlots][8][blockDim]
     __shared__ uint32_t tab[128];
     __shared__ uint32_t gate_s[2];
-    __shared__ long long red[64];
     __shared__ int ok_s;
     __shared__ RunState rs;                          // touched by the folding thread only
+    __shared__ unsigned warps_in;                    // warps that finished a pass (grows through the launch)
+    __shared__ long long acc_s[2];                   // the CTA's dM, dB of the current sweep
     const DevFilm& f = a.f;
     FilmState* st = a.st;
     const unsigned G = gridDim.x, cta = blockIdx.x;
+    const unsigned nwarps = blockDim.x >> 5;
+    unsigned pass_no = 0;
+    if (threadIdx.x == 0) {         // published by stage_table's barrier below
+        warps_in = 0;
+        acc_s[0] = 0;
+        acc_s[1] = 0;
+    }
     unsigned target = 0;
     int k = a.k0, pos = a.pos0;
     const bool folder = cta == 0 && threadIdx.x == 0;
@@ -496,13 +513,16 @@ __global__ void __launch_bounds__(kBlock) k_words(const __grid_constant__ SweepA
     }
     const int it0 = first_item(G, cta);
     const int stride = (int)G * blockDim.x;
+    uint32_t rk[20];
+    round_keys(f.key0, f.key1, rk);
     auto step_draws_all = [&](int kk) {
         return (a.tables[(size_t)kk * kTableStride + kFlagSlot] & kFlagAlwaysDraw) != 0u;
     };
     // the first pass's random words
     {
         const int kf = a.pos0 == a.step_total[a.k0] ? a.k0 + 1 : a.k0;
-        if (a.nsweeps > 0) draw_ahead(f, 0, (unsigned long long)(a.sweep0 + 1), step_draws_all(kf), it0, stride, ahead);
+        if (a.nsweeps > 0)
+            draw_ahead(f, 0, (unsigned long long)(a.sweep0 + 1), step_draws_all(kf), it0, stride, ahead, rk);
     }
     stage_table<true>(a.tables, k, tab, gate_s);
     for (long long t = 0; t < a.nsweeps; ++t) {
@@ -519,22 +539,45 @@ __global__ void __launch_bounds__(kBlock) k_words(const __grid_constant__ SweepA
         const int k_next = pos + 1 == a.step_total[k] ? k + 1 : k;
         int dM = 0, dB = 0;
         for (int c = 0; c < 4; ++c) {
-            pass_words<GATE>(f, c, sweep, tab, gthr, always_draw, always_draw, it0, stride, ahead, dM, dB);
+            pass_words<GATE>(f, c, sweep, tab, gthr, always_draw, always_draw, (gate_s[1] & kFlagNoNever) != 0, it0,
+                             stride, ahead, dM, dB);
+            // each warp arrives as soon as its own words are done: the CTA's last warp to finish
+            // (release / acquire on a shared counter orders every warp's stores before it) adds
+            // the CTA's (dM, dB) of the sweep and arrives at the grid barrier with release semantics
+            const int lane = threadIdx.x & 31;
             if (c == 3) {
-                long long sM = dM, sB = dB;
-                block_sum2(sM, sB, red);
-                if (threadIdx.x == 0 && (sM | sB)) {
-                    unsigned long long* acc = reinterpret_cast<unsigned long long*>(&st->acc[sweep & 1][0]);
-                    atomicAdd(acc, (unsigned long long)sM);
-                    atomicAdd(acc + 1, (unsigned long long)sB);
+                const long long wM = warp_sum((long long)dM), wB = warp_sum((long long)dB);
+                if (lane == 0 && (wM | wB)) {
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&acc_s[0]), (unsigned long long)wM);
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&acc_s[1]), (unsigned long long)wB);
                 }
             }
-            grid_arrive(st, G, target);
-            // while the other CTAs finish this pass: the random words of the next one
+            __syncwarp();
+            ++pass_no;
+            if (lane == 0) {
+                unsigned old;
+                asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;"
+                             : "=r"(old) : "r"((unsigned)__cvta_generic_to_shared(&warps_in)) : "memory");
+                if (old == pass_no * nwarps - 1u) {
+                    if (c == 3) {
+                        const long long sM = acc_s[0], sB = acc_s[1];
+                        acc_s[0] = 0;
+                        acc_s[1] = 0;
+                        if (sM | sB) {
+                            unsigned long long* acc = reinterpret_cast<unsigned long long*>(&st->acc[sweep & 1][0]);
+                            atomicAdd(acc, (unsigned long long)sM);
+                            atomicAdd(acc + 1, (unsigned long long)sB);
+                        }
+                    }
+                    if (G > 1) red_release_add_u32(&st->bar_count, 1u);
+                }
+            }
+            target += G;
+            // while the other warps and CTAs finish this pass: the random words of the next one
             if (c < 3) {
-                draw_ahead(f, c + 1, sweep, always_draw, it0, stride, ahead);
+                draw_ahead(f, c + 1, sweep, always_draw, it0, stride, ahead, rk);
             } else if (t + 1 < a.nsweeps) {
-                draw_ahead(f, 0, sweep + 1, step_draws_all(k_next), it0, stride, ahead);
+                draw_ahead(f, 0, sweep + 1, step_draws_all(k_next), it0, stride, ahead, rk);
             }
             if (!grid_wait(st, G, target, &ok_s)) return;
         }

@@ -42,7 +42,9 @@ void build_step_table(double T, double h, double J, double h_s, uint32_t* out52)
     // aligned sites: n = +12 with s = +1, n = -12 with s = -1
     auto needs_word = [](uint32_t t) { return t != 0u && t != kAlways; };
     const bool always = needs_word(out52[(12 + 12) * 2 + 1]) || needs_word(out52[(-12 + 12) * 2 + 0]);
-    out52[kFlagSlot] = always ? kFlagAlwaysDraw : 0u;
+    bool never = false;
+    for (int i = 0; i < 50; ++i) never |= out52[i] == 0u;
+    out52[kFlagSlot] = (always ? kFlagAlwaysDraw : 0u) | (never ? 0u : kFlagNoNever);
 }
 
 namespace {

@@ -12,7 +12,9 @@ namespace isf {
 // Table of the current step in shared memory, indexed by the per-site byte a pass forms:
 //   int8   : (stored byte << 5) | (n + 12), stored byte 0 = down, 1 = vacancy, 2 = up;
 //            vacancies map to 0 ("never"), so they never flip and never draw a random word
-//   packed : (up << 5) | (n + 12); the packed kernel masks vacant sites out of the flips itself
+//   packed : (up << 5) | (n + 12); the packed kernel masks vacant sites out of the flips itself.
+//            Entries 64..127 hold the same thresholds negated, 2^32 - thr ("always": 0), for
+//            the carry form of the comparison (kFlagNoNever).
 template <bool PACKED>
 __device__ __forceinline__ void stage_table(const uint32_t* tables, int k, uint32_t* tab, uint32_t* gate) {
     const uint32_t* src = tables + (size_t)k * kTableStride;
@@ -21,7 +23,8 @@ __device__ __forceinline__ void stage_table(const uint32_t* tables, int k, uint3
         const int X = t & 31;
         if (X <= 24) {
             if (PACKED) {
-                if (t < 64) v = src[X * 2 + (t >> 5)];
+                const uint32_t thr = src[X * 2 + ((t >> 5) & 1)];
+                v = t < 64 ? thr : (thr == kAlways ? 0u : 0u - thr);
             } else {
                 const int sb = t >> 5;
                 if (sb == 0) v = src[X * 2 + 0];
@@ -61,6 +64,16 @@ __device__ __forceinline__ uint32_t gate_block(uint32_t lanes, uint32_t gthr, ui
     return lanes & keep;
 }
 
+// Rejected-lane bits of the carry form of the comparison: with neg = 2^32 - thr (0 for
+// "always"), u + neg carries out exactly when u >= thr, i.e. when the flip is rejected; the carry
+// is shifted in below R (R = 2R + carry), so after 32 lanes lane 0 sits in bit 31.
+__device__ __forceinline__ uint32_t shift_in_reject(uint32_t R, uint32_t u, uint32_t neg) {
+    uint32_t out;
+    asm("{\n\t.reg .u32 t;\n\tadd.cc.u32 t, %1, %2;\n\taddc.u32 %0, %3, %3;\n\t}"
+        : "=r"(out) : "r"(u), "r"(neg), "r"(R));
+    return out;
+}
+
 // NW Philox4x32-10 blocks at consecutive counters, interleaved so that their dependency chains
 // overlap (same rounds as philox10).
 template <int NW>
@@ -83,6 +96,60 @@ __device__ __forceinline__ void philox10_xn(uint32_t q0, uint32_t s_lo, uint32_t
         }
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
+    }
+#pragma unroll
+    for (int v = 0; v < NW; ++v) out[v] = make_uint4(c0[v], c1[v], c2[v], c3[v]);
+}
+
+// Philox4x32-10 with its round keys precomputed (rk[2r], rk[2r+1]: the key of round r) and the
+// parts of rounds 1 and 2 that depend on the sweep only (the counter's words 1 and 2 are the
+// sweep, word 0 varies), computed once per sweep: the same blocks as philox10_xn.
+struct SweepConst {
+    uint32_t A, B;      // counter words 0 and 1 after round 1
+    uint32_t C, D;      // high and low words of M0 * A (round 2)
+};
+__device__ __forceinline__ void round_keys(uint32_t k0, uint32_t k1, uint32_t (&rk)[20]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        rk[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+}
+__device__ __forceinline__ SweepConst sweep_const(unsigned long long sweep, const uint32_t (&rk)[20]) {
+    SweepConst sc;
+    uint32_t lo, hi;
+    mul_wide(0xCD9E8D57u, (uint32_t)(sweep >> 32), lo, hi);
+    sc.A = hi ^ (uint32_t)sweep ^ rk[0];
+    sc.B = lo;
+    mul_wide(0xD2511F53u, sc.A, sc.D, sc.C);
+    return sc;
+}
+template <int NW>
+__device__ __forceinline__ void philox10_sc(uint32_t q0, uint32_t stream, const SweepConst& sc,
+                                            const uint32_t (&rk)[20], uint4 out[NW]) {
+    uint32_t c0[NW], c1[NW], c2[NW], c3[NW];
+#pragma unroll
+    for (int v = 0; v < NW; ++v) {
+        uint32_t lo0, hi0, lo1, hi1;
+        mul_wide(0xD2511F53u, q0 + v, lo0, hi0);          // round 1; its other half is sc.A, sc.B
+        mul_wide(0xCD9E8D57u, hi0 ^ stream ^ rk[1], lo1, hi1);   // round 2; M0 * sc.A = sc.C:sc.D
+        c0[v] = hi1 ^ sc.B ^ rk[2];
+        c1[v] = lo1;
+        c2[v] = sc.C ^ lo0 ^ rk[3];
+        c3[v] = sc.D;
+    }
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+#pragma unroll
+        for (int v = 0; v < NW; ++v) {
+            uint32_t lo0, hi0, lo1, hi1;
+            mul_wide(0xD2511F53u, c0[v], lo0, hi0);
+            mul_wide(0xCD9E8D57u, c2[v], lo1, hi1);
+            c0[v] = hi1 ^ c1[v] ^ rk[2 * r];
+            c1[v] = lo1;
+            c2[v] = hi0 ^ c3[v] ^ rk[2 * r + 1];
+            c3[v] = lo0;
+        }
     }
 #pragma unroll
     for (int v = 0; v < NW; ++v) out[v] = make_uint4(c0[v], c1[v], c2[v], c3[v]);
@@ -219,8 +286,11 @@ __device__ __forceinline__ void popcount12(const uint32_t* x, uint32_t& b0, uint
 // 8x32 bit-plane transpose gives each lane its table entry's byte offset; u_first: the word's
 // first four Philox blocks (lanes 0-15), drawn by the caller; u_second (may be null): the last
 // four (lanes 16-31) when the caller drew them too, else they are drawn here when a lane needs
-// them.  Returns the flip mask (vacant lanes cleared) and adds the flips' dM, dB.
-template <bool GATE>
+// them.  CARRY (steps without a "never" threshold, no gate): each lane's decision is the carry of
+// u + (2^32 - thr), shifted into a rejection mask (two instructions a lane instead of a minimum,
+// a compare, a select and an or).  Returns the flip mask (vacant lanes cleared) and adds the
+// flips' dM, dB.
+template <bool GATE, bool CARRY = false>
 __device__ __forceinline__ uint32_t packed_decide(uint32_t S, uint32_t O, const uint32_t up[12], const uint32_t V[4],
                                                   uint32_t q0, unsigned long long sweep, const uint32_t* tab,
                                                   uint32_t gthr, bool always_draw, uint32_t key0, uint32_t key1,
@@ -258,7 +328,9 @@ __device__ __forceinline__ uint32_t packed_decide(uint32_t S, uint32_t O, const 
         P[p + 1] ^= t;
         P[p] ^= t << 1;
     }
-    uint32_t F = 0;
+    static_assert(!(GATE && CARRY), "the gate needs the accepted lanes of each block");
+    uint32_t F = 0, R = 0;
+    const uint8_t* tabb = reinterpret_cast<const uint8_t*>(tab) + (CARRY ? 256 : 0);
     // two halves of 16 lanes (4 Philox blocks each): all 16 lookups first, then the half's four
     // blocks interleaved when any of its lanes needs a word
 #pragma unroll
@@ -271,7 +343,7 @@ __device__ __forceinline__ uint32_t packed_decide(uint32_t S, uint32_t O, const 
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const uint32_t t = *reinterpret_cast<const uint32_t*>(
-                    reinterpret_cast<const uint8_t*>(tab) + ((P[4 * (v & 1) + b] >> (8 * (v >> 1))) & 0xFFu));
+                    tabb + ((P[4 * (v & 1) + b] >> (8 * (v >> 1))) & 0xFFu));
                 thr[4 * vv + b] = t;
             }
         }
@@ -282,7 +354,7 @@ __device__ __forceinline__ uint32_t packed_decide(uint32_t S, uint32_t O, const 
                 need = true;
             } else {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) need |= needs_word(thr[i]);
+                for (int i = 0; i < 16; ++i) need |= CARRY ? thr[i] != 0u : needs_word(thr[i]);
             }
         }
         uint4 u[4];
@@ -297,16 +369,24 @@ __device__ __forceinline__ uint32_t packed_decide(uint32_t S, uint32_t O, const 
             for (int vv = 0; vv < 4; ++vv) u[vv] = make_uint4(0, 0, 0, 0);
             if (need) philox10_xn<4>(q0 + 4, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, key0, key1, u);
         }
+        if (CARRY) {
 #pragma unroll
-        for (int vv = 0; vv < 4; ++vv) {
-            uint32_t lanes = 0;
+            for (int vv = 0; vv < 4; ++vv)
 #pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if (metropolis_accept(word_of(u[vv], b), thr[4 * vv + b])) lanes |= 1u << b;
-            if (GATE) lanes = gate_block(lanes, gthr, q0 + 4 * g + vv, sweep, key0, key1);
-            F |= lanes << (4 * (4 * g + vv));
+                for (int b = 0; b < 4; ++b) R = shift_in_reject(R, word_of(u[vv], b), thr[4 * vv + b]);
+        } else {
+#pragma unroll
+            for (int vv = 0; vv < 4; ++vv) {
+                uint32_t lanes = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (metropolis_accept(word_of(u[vv], b), thr[4 * vv + b])) lanes |= 1u << b;
+                if (GATE) lanes = gate_block(lanes, gthr, q0 + 4 * g + vv, sweep, key0, key1);
+                F |= lanes << (4 * (4 * g + vv));
+            }
         }
     }
+    if (CARRY) F = ~__brev(R);  // lanes 0..31 were shifted in first to last
     F &= O;                     // vacant sites never flip
     if (F) {
         const uint32_t Fu = F & S, Fd = F & ~S;        // flipped up -> down, down -> up
