@@ -413,21 +413,25 @@ __global__ void __launch_bounds__(kBlock) k_sweep(const __grid_constant__ SweepA
 // draw in the pass.
 constexpr int kAheadSlots = 2;
 
-// Bytes of dynamic shared memory of k_words with this block size.
-constexpr size_t ahead_bytes(int threads) { return (size_t)kAheadSlots * 8 * (size_t)threads * sizeof(uint4); }
+// Bytes of dynamic shared memory of k_words with this block size: the random words drawn ahead
+// ([slot][block][thread] uint4) and the thread's list entries of every colour ([colour][slot]
+// [thread] uint2; a thread takes the same words in every sweep, so they are read once a launch).
+constexpr size_t ahead_bytes(int threads) {
+    return (size_t)kAheadSlots * 8 * (size_t)threads * sizeof(uint4) + (size_t)4 * kAheadSlots * threads * sizeof(uint2);
+}
 
 // The Philox blocks of this thread's first kAheadSlots words of colour c at `sweep` into its
-// slots of `ahead` ([slot][block][thread] uint4); the second four blocks only when `both`.
+// slots of `ahead`; the second four blocks only when `both`.  ents: the entries cached in shared
+// memory.
 __device__ __forceinline__ void draw_ahead(const DevFilm& f, int c, unsigned long long sweep, bool both, int it0,
-                                           int stride, uint4* ahead, const uint32_t (&rk)[20]) {
+                                           int stride, uint4* ahead, const uint2* ents, const uint32_t (&rk)[20]) {
     const SweepConst sc = sweep_const(sweep, rk);
-    const uint2* ent = reinterpret_cast<const uint2*>(f.ient) + (int64_t)c * f.item_cap;
     const int n = f.nitems[c];
     const int bd = blockDim.x, tid = threadIdx.x;
     int it = it0;
 #pragma unroll 1
     for (int slot = 0; slot < kAheadSlots && it < n; ++slot, it += stride) {
-        const uint32_t q = ent[it].y;
+        const uint32_t q = ents[(c * kAheadSlots + slot) * bd + tid].y;
         uint4 u[4];
         philox10_sc<4>(q, 0u, sc, rk, u);
 #pragma unroll
@@ -445,7 +449,7 @@ __device__ __forceinline__ void draw_ahead(const DevFilm& f, int c, unsigned lon
 template <bool GATE>
 __device__ __forceinline__ void pass_words(const DevFilm& f, int c, unsigned long long sweep, const uint32_t* tab,
                                            uint32_t gthr, bool always_draw, bool both, bool no_never, int it0,
-                                           int stride, const uint4* ahead, int& dM, int& dB) {
+                                           int stride, const uint4* ahead, const uint2* ents, int& dM, int& dB) {
     const uint2* ent = reinterpret_cast<const uint2*>(f.ient) + (int64_t)c * f.item_cap;
     const uint4* vq = reinterpret_cast<const uint4*>(f.ivq) + (int64_t)c * f.item_cap;
     const int n = f.nitems[c];
@@ -453,7 +457,8 @@ __device__ __forceinline__ void pass_words(const DevFilm& f, int c, unsigned lon
     int slot = 0;
 #pragma unroll 1
     for (int it = it0; it < n; it += stride, ++slot) {
-        const uint2 pq = ent[it];
+        // the entry from shared memory, so the word's loads leave at once
+        const uint2 pq = slot < kAheadSlots ? ents[(c * kAheadSlots + slot) * bd + tid] : ent[it];
         const int64_t base = (int64_t)(pq.x & 0x7FFFFFFFu);
         const NbrClass& nc = f.nb[c][pq.x >> 31];
         uint32_t S, O, up[12], V[4];
@@ -485,7 +490,7 @@ __device__ __forceinline__ void pass_words(const DevFilm& f, int c, unsigned lon
 
 template <bool GATE>
 __global__ void __launch_bounds__(kBlock) k_words(const __grid_constant__ SweepArgs a) {
-    extern __shared__ uint4 ahead[];                 // [kAheadSlots][8][blockDim]
+    extern __shared__ uint4 ahead[];                 // [kAheadSlots][8][blockDim], then the entries
     __shared__ uint32_t tab[128];
     __shared__ uint32_t gate_s[2];
     __shared__ int ok_s;
@@ -515,6 +520,14 @@ __global__ void __launch_bounds__(kBlock) k_words(const __grid_constant__ SweepA
     const int stride = (int)G * blockDim.x;
     uint32_t rk[20];
     round_keys(f.key0, f.key1, rk);
+    uint2* ents = reinterpret_cast<uint2*>(ahead + (size_t)kAheadSlots * 8 * blockDim.x);
+    for (int c = 0; c < 4; ++c) {
+        const uint2* ent = reinterpret_cast<const uint2*>(f.ient) + (int64_t)c * f.item_cap;
+        for (int slot = 0; slot < kAheadSlots; ++slot) {
+            const int it = it0 + slot * stride;
+            ents[(c * kAheadSlots + slot) * blockDim.x + threadIdx.x] = it < f.nitems[c] ? ent[it] : make_uint2(0u, 0u);
+        }
+    }
     auto step_draws_all = [&](int kk) {
         return (a.tables[(size_t)kk * kTableStride + kFlagSlot] & kFlagAlwaysDraw) != 0u;
     };
@@ -522,7 +535,7 @@ __global__ void __launch_bounds__(kBlock) k_words(const __grid_constant__ SweepA
     {
         const int kf = a.pos0 == a.step_total[a.k0] ? a.k0 + 1 : a.k0;
         if (a.nsweeps > 0)
-            draw_ahead(f, 0, (unsigned long long)(a.sweep0 + 1), step_draws_all(kf), it0, stride, ahead, rk);
+            draw_ahead(f, 0, (unsigned long long)(a.sweep0 + 1), step_draws_all(kf), it0, stride, ahead, ents, rk);
     }
     stage_table<true>(a.tables, k, tab, gate_s);
     for (long long t = 0; t < a.nsweeps; ++t) {
@@ -540,7 +553,7 @@ __global__ void __launch_bounds__(kBlock) k_words(const __grid_constant__ SweepA
         int dM = 0, dB = 0;
         for (int c = 0; c < 4; ++c) {
             pass_words<GATE>(f, c, sweep, tab, gthr, always_draw, always_draw, (gate_s[1] & kFlagNoNever) != 0, it0,
-                             stride, ahead, dM, dB);
+                             stride, ahead, ents, dM, dB);
             // each warp arrives as soon as its own words are done: the CTA's last warp to finish
             // (release / acquire on a shared counter orders every warp's stores before it) adds
             // the CTA's (dM, dB) of the sweep and arrives at the grid barrier with release semantics
@@ -575,9 +588,9 @@ __global__ void __launch_bounds__(kBlock) k_words(const __grid_constant__ SweepA
             target += G;
             // while the other warps and CTAs finish this pass: the random words of the next one
             if (c < 3) {
-                draw_ahead(f, c + 1, sweep, always_draw, it0, stride, ahead, rk);
+                draw_ahead(f, c + 1, sweep, always_draw, it0, stride, ahead, ents, rk);
             } else if (t + 1 < a.nsweeps) {
-                draw_ahead(f, 0, sweep + 1, step_draws_all(k_next), it0, stride, ahead, rk);
+                draw_ahead(f, 0, sweep + 1, step_draws_all(k_next), it0, stride, ahead, ents, rk);
             }
             if (!grid_wait(st, G, target, &ok_s)) return;
         }

@@ -66,7 +66,7 @@ __device__ __forceinline__ uint32_t gate_block(uint32_t lanes, uint32_t gthr, ui
 
 // Rejected-lane bits of the carry form of the comparison: with neg = 2^32 - thr (0 for
 // "always"), u + neg carries out exactly when u >= thr, i.e. when the flip is rejected; the carry
-// is shifted in below R (R = 2R + carry), so after 32 lanes lane 0 sits in bit 31.
+// is shifted in below R (R = 2R + carry).
 __device__ __forceinline__ uint32_t shift_in_reject(uint32_t R, uint32_t u, uint32_t neg) {
     uint32_t out;
     asm("{\n\t.reg .u32 t;\n\tadd.cc.u32 t, %1, %2;\n\taddc.u32 %0, %3, %3;\n\t}"
@@ -288,8 +288,9 @@ __device__ __forceinline__ void popcount12(const uint32_t* x, uint32_t& b0, uint
 // four (lanes 16-31) when the caller drew them too, else they are drawn here when a lane needs
 // them.  CARRY (steps without a "never" threshold, no gate): each lane's decision is the carry of
 // u + (2^32 - thr), shifted into a rejection mask (two instructions a lane instead of a minimum,
-// a compare, a select and an or).  Returns the flip mask (vacant lanes cleared) and adds the
-// flips' dM, dB.
+// a compare, a select and an or), in four independent 8-lane chains (highest lane first, so that
+// chain j ends with lane 8j + i in bit i) joined at the end.  Returns the flip mask (vacant
+// lanes cleared) and adds the flips' dM, dB.
 template <bool GATE, bool CARRY = false>
 __device__ __forceinline__ uint32_t packed_decide(uint32_t S, uint32_t O, const uint32_t up[12], const uint32_t V[4],
                                                   uint32_t q0, unsigned long long sweep, const uint32_t* tab,
@@ -329,7 +330,8 @@ __device__ __forceinline__ uint32_t packed_decide(uint32_t S, uint32_t O, const 
         P[p] ^= t << 1;
     }
     static_assert(!(GATE && CARRY), "the gate needs the accepted lanes of each block");
-    uint32_t F = 0, R = 0;
+    uint32_t F = 0;
+    uint32_t R[4] = {0u, 0u, 0u, 0u};       // CARRY: rejected lanes 8j..8j+7 of chain j
     const uint8_t* tabb = reinterpret_cast<const uint8_t*>(tab) + (CARRY ? 256 : 0);
     // two halves of 16 lanes (4 Philox blocks each): all 16 lookups first, then the half's four
     // blocks interleaved when any of its lanes needs a word
@@ -370,10 +372,15 @@ __device__ __forceinline__ uint32_t packed_decide(uint32_t S, uint32_t O, const 
             if (need) philox10_xn<4>(q0 + 4, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, key0, key1, u);
         }
         if (CARRY) {
+            // lanes 16g + 4vv + b; chain 2g + (vv >> 1) takes its 8 lanes from the highest down
 #pragma unroll
-            for (int vv = 0; vv < 4; ++vv)
+            for (int i = 7; i >= 0; --i) {
 #pragma unroll
-                for (int b = 0; b < 4; ++b) R = shift_in_reject(R, word_of(u[vv], b), thr[4 * vv + b]);
+                for (int h = 0; h < 2; ++h) {
+                    const int vv = 2 * h + (i >> 2), b = i & 3;
+                    R[2 * g + h] = shift_in_reject(R[2 * g + h], word_of(u[vv], b), thr[4 * vv + b]);
+                }
+            }
         } else {
 #pragma unroll
             for (int vv = 0; vv < 4; ++vv) {
@@ -386,7 +393,7 @@ __device__ __forceinline__ uint32_t packed_decide(uint32_t S, uint32_t O, const 
             }
         }
     }
-    if (CARRY) F = ~__brev(R);  // lanes 0..31 were shifted in first to last
+    if (CARRY) F = ~(R[0] | (R[1] << 8) | (R[2] << 16) | (R[3] << 24));
     F &= O;                     // vacant sites never flip
     if (F) {
         const uint32_t Fu = F & S, Fd = F & ~S;        // flipped up -> down, down -> up

@@ -150,6 +150,27 @@ def test_launch_shape_does_not_change_the_trajectory(I, packed, path, sites):
             assert g["launch"]["item_sites"] == sites
 
 
+@pytest.mark.parametrize("h_s", [0.0, 3.0])
+def test_packed_word_kernel_every_step_kind(I, h_s):
+    """The packed multi-CTA kernel decides a step's lanes in two ways (the carry form when no
+    threshold of the step is "never", the plain comparison otherwise, and always the plain one
+    under the Eq. 9 gate) and draws a word's random blocks ahead (both halves when nearly every
+    word needs them, else the second half lazily; words past the drawn-ahead slots in the pass).
+    One schedule mixes all of them: T = 0.6 and 0.9 (never thresholds, lazy), T = 3, 1.4 and 2 with
+    a strong field (carry, all drawn), T = inf (every flip "always": carry, lazy), T = 1.2 with
+    h = 4 (never thresholds, all drawn); on launch shapes from 3 words per thread to less than
+    one; bit-exact against the oracle."""
+    spec = film(W.fractal_heights(64, 256, 0.7, 1, 3, seed=77), 3, seed=19)
+    sched = W.schedule([0.6, 3.0, float("inf"), 1.4, 2.0, 0.9, 1.2], [0.5, -1.0, 0.0, 2.0, -6.0, 0.2, 4.0],
+                       [1, 2, 0, 1, 0, 2, 1], [3, 3, 2, 4, 3, 2, 3])
+    ref = run_oracle(spec, sched, h_s=h_s)
+    for launch in [(4, 32), (3, 64), (8, 64), (2, 512), (0, 0)]:
+        g = run_gpu(I, spec, sched, packed=True, launch=launch, path="global", h_s=h_s)
+        assert_same_run(g, ref)
+        if launch[0] > 1:
+            assert g["launch"]["ctas"] == launch[0] and g["launch"]["path"] == "global", g["launch"]
+
+
 @pytest.mark.parametrize("sites", [16, 8])
 @pytest.mark.parametrize("name", ["flat16", "periodic_y_only", "periodic_x_only", "cube4", "ragged", "f256_prefix",
                                   "ragged_x9"])
