@@ -64,8 +64,10 @@ int isf_debug_checks(uint64_t* out4);
  * 32w..32w+31 or 16w..16w+15 (Sec. 3's rows of one colour; occupancy as in isf_lattice_create).
  * heights: host, rows*cols; n_out[4]: entries per colour; out: 4 x cap uint32, colour c's list
  * from out[c * cap]; cap >= layers * ceil(rows/2) * items per row; bits_out[2] = (wbits, jbits).
+ * The same checks as isf_lattice_create: a film it would refuse, or one it would keep without
+ * lists, is refused here too.
  * Errors: ISF_ERR_ARG (bad shape or pointers, cap too small, a film without lists: periodic int8,
- * or fields that do not fit 32 bits), ISF_ERR_COLOURING. */
+ * or offsets or fields that do not fit 32 bits), ISF_ERR_COLOURING. */
 int isf_debug_item_lists(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, uint32_t flags,
                          int32_t* n_out, uint32_t* out, int64_t cap, int32_t* bits_out);
 
@@ -74,7 +76,8 @@ int isf_debug_item_lists(const uint8_t* heights, int32_t rows, int32_t cols, int
  * int32), band g holding colour rows [part_out[g], part_out[g+1]); contiguous, 1..max_rows rows
  * each, cut where the running count of occupied words (all colours and layers) is closest to an
  * even share (Sec. 3's split of the image rows between processes).  Errors: ISF_ERR_ARG (bad
- * shape or pointers, bands outside 1..colour rows, bands x max_rows below the colour rows). */
+ * shape or pointers, bands outside 1..colour rows, bands x max_rows below the colour rows, a film
+ * the library keeps without word lists, which the row-slab path refuses). */
 int isf_debug_slab_partition(const uint8_t* heights, int32_t rows, int32_t cols, int32_t layers, int32_t bands,
                              int32_t max_rows, int32_t* part_out);
 

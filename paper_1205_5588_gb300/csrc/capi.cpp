@@ -13,6 +13,15 @@
 
 using namespace isf;
 
+namespace isf {
+// The item lists (and their per-entry records) are kept only for films whose word or byte
+// offsets, neighbour offsets included, fit 32 bits.
+bool lists_fit_32_bits(const Layout& lay) {
+    return lay.packed ? (4 * lay.csw + 2 * lay.lsw) < ((int64_t)1 << 31)
+                      : (4 * lay.cs8 + 2 * lay.ls8) < ((int64_t)1 << 31);
+}
+}  // namespace isf
+
 namespace {
 
 thread_local std::string g_err;
@@ -130,8 +139,7 @@ int create_common(const uint8_t* heights, int32_t rows, int32_t cols, int32_t la
     }
     // item lists (with their per-entry records) for films whose indices and neighbour offsets
     // fit 32 bits; the kernels walk every item of the others
-    f.narrow = lay.packed ? ((4 * lay.csw + 2 * lay.lsw) < ((int64_t)1 << 31) ? 1 : 0)
-                          : ((4 * lay.cs8 + 2 * lay.ls8) < ((int64_t)1 << 31) ? 1 : 0);
+    f.narrow = lists_fit_32_bits(lay) ? 1 : 0;
     std::vector<uint32_t> items;
     if (f.narrow && build_word_items(lay, heights, items, f.nitems, &f.item_wbits, &f.item_jbits,
                                      sw ? sw->jlo : 0, sw ? sw->jhi : lay.Rh,
@@ -899,7 +907,11 @@ int isf_debug_item_lists(const uint8_t* heights, int32_t rows, int32_t cols, int
     const char* why = "";
     int rc = make_layout(rows, cols, layers, flags, &lay, &why);
     if (rc) return fail(rc, why);
+    rc = check_colouring(lay, &why);
+    if (rc) return fail(rc, why);
     if (lay.items_cap == 0) return fail(ISF_ERR_ARG, "this film has no item lists (periodic int8)");
+    if (!lists_fit_32_bits(lay))
+        return fail(ISF_ERR_ARG, "this film keeps no lists: its neighbour offsets do not fit 32 bits");
     if (cap < lay.items_cap) return fail(ISF_ERR_ARG, "cap is smaller than layers x colour rows x items per row");
     std::vector<uint32_t> items;
     int32_t n[4], wb = 0, jb = 0;
@@ -922,6 +934,8 @@ int isf_debug_slab_partition(const uint8_t* heights, int32_t rows, int32_t cols,
     const char* why = "";
     int rc = make_layout(rows, cols, layers, ISF_PACKED, &lay, &why);
     if (rc) return fail(rc, why);
+    if (!lists_fit_32_bits(lay))
+        return fail(ISF_ERR_ARG, "the row-slab path needs word lists: this film's neighbour offsets do not fit 32 bits");
     if (bands < 1 || bands > lay.Rh || max_rows < 1 || (int64_t)max_rows * bands < lay.Rh)
         return fail(ISF_ERR_ARG, "need 1 <= bands <= colour rows and bands x max_rows >= colour rows");
     std::vector<uint32_t> items;

@@ -169,6 +169,8 @@ int check_colouring(const Layout& lay, const char** why);
 bool build_word_items(const Layout& lay, const uint8_t* heights, std::vector<uint32_t>& out, int32_t n[4],
                       int32_t* wbits, int32_t* jbits, int32_t jlo, int32_t jhi, std::vector<int32_t>* roff = nullptr);
 void fill_neighbour_classes(const Layout& lay, DevFilm* f);
+// Whether a film of this layout keeps item lists: its offsets, neighbours included, fit 32 bits.
+bool lists_fit_32_bits(const Layout& lay);
 
 // Host threshold table (schedule.cpp): thr[n+12][s'] for one step, plus the gate slot.
 void build_step_table(double T, double h, double J, double h_s, uint32_t* out52);

@@ -344,8 +344,9 @@ __device__ __forceinline__ uint32_t packed_decide(uint32_t S, uint32_t O, const 
             const int v = 4 * g + vv;
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
+                // byte v >> 1 of the transposed word, zero-extended (one byte permute)
                 const uint32_t t = *reinterpret_cast<const uint32_t*>(
-                    tabb + ((P[4 * (v & 1) + b] >> (8 * (v >> 1))) & 0xFFu));
+                    tabb + __byte_perm(P[4 * (v & 1) + b], 0u, 0x4440u + (uint32_t)(v >> 1)));
                 thr[4 * vv + b] = t;
             }
         }

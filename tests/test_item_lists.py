@@ -113,3 +113,13 @@ def test_slab_partition_refusals(I):
         with pytest.raises(I.IsfError) as e:
             I.slab_partition(H, 3, bands, max_rows)
         assert e.value.code == -1
+
+
+def test_debug_exports_refuse_what_the_library_refuses():
+    """The debug exports apply isf_lattice_create's checks: a film whose periodic colouring would
+    conflict is refused with ISF_ERR_COLOURING, not given lists the library never builds."""
+    from paper_1205_5588_gb300 import isingfilm as I
+    H = np.full((5, 8), 2, dtype=np.uint8)          # periodic y with an odd number of rows
+    with pytest.raises(I.IsfError) as e:
+        I.item_lists(H, 2, flags=I.PERIODIC_Y)
+    assert e.value.code == -4
