@@ -43,15 +43,22 @@ OPS_PER_ATTEMPT = 40
 LANES_PER_SM = 128          # dispatch: 4 sub-partitions x one 32-lane warp instruction per clock
 
 
-def workload(name: str):
+def workload(name: str, schedule_steps: int = 0):
+    """The named workload; schedule_steps > 0 keeps only the first steps of its schedule (quick
+    timings of the same kernel on the same film; not a bench value)."""
     from paper_1205_5588_gb300 import workloads as W
     if name == "fractal2048":
-        return W.fractal2048_hysteresis()
-    if name == "fractal256":
-        return W.fractal256_tscan()
-    if name == "flat16":
-        return W.flat16_hysteresis()
-    raise SystemExit(f"unknown workload {name}")
+        spec = W.fractal2048_hysteresis()
+    elif name == "fractal256":
+        spec = W.fractal256_tscan()
+    elif name == "flat16":
+        spec = W.flat16_hysteresis()
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if schedule_steps > 0:
+        spec["schedule"] = {k: v[:schedule_steps].copy() for k, v in spec["schedule"].items()}
+        spec["name"] += f"_first{schedule_steps}steps"
+    return spec
 
 
 KERNEL_OF_PATH = {"global": "k_sweep (global-memory persistent kernel, all SMs)",
@@ -283,7 +290,7 @@ def run_impl(args):
     B.build()
     from paper_1205_5588_gb300 import isingfilm as I
 
-    spec = workload(args.workload)
+    spec = workload(args.workload, args.schedule_steps)
     sched = spec["schedule"]
     seed = D.replica_seed(spec["seed"], rank)   # a single film does not shard: one replica per rank
     stream = torch.cuda.current_stream()
@@ -614,6 +621,8 @@ def main():
     ap.add_argument("--serve-rate-sustainable", type=float, default=100.0)
     ap.add_argument("--serve-seconds-sustainable", type=float, default=20.0)
     ap.add_argument("--ref-sweeps", type=int, default=0)
+    ap.add_argument("--schedule-steps", type=int, default=0,
+                    help="time only the first N steps of the workload's schedule (quick kernel timings)")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling case: one launch of this many sweeps at the first schedule step, no JSON")
     ap.add_argument("--probe", action="store_true", help="print the integer-issue ceilings only")

@@ -21,10 +21,10 @@ LIB_NAME = "libisingfilm.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels_sweep.cu", "kernels_slabs.cu", "kernels_resident.cu", "kernels_aux.cu", "noalloc.cu",
-              "kernels_peak.cu"]
+CU_SOURCES = ["kernels_sweep.cu", "kernels_words.cu", "kernels_slabs.cu", "kernels_resident.cu", "kernels_aux.cu",
+              "noalloc.cu", "kernels_peak.cu"]
 CPP_SOURCES = ["capi.cpp", "batch.cpp", "serve.cpp", "lattice.cpp", "schedule.cpp"]
-HEADERS = ["isf_internal.h", "device_common.cuh", "sweep_core.cuh", "capi_internal.h"]
+HEADERS = ["isf_internal.h", "device_common.cuh", "sweep_core.cuh", "grid_sync.cuh", "capi_internal.h"]
 
 
 def cuda_home() -> str:

@@ -195,6 +195,10 @@ int launch_surface_domains(const DevFilm& f, const uint8_t* dev_img, int* dev_sc
 int launch_philox_blocks(uint64_t seed, uint32_t stream_id, uint64_t sweep, uint32_t q0,
                          int64_t nblocks, uint32_t* dev_out, void* stream);
 int sweep_max_ctas_for(const DevFilm& f, int threads, int* max_ctas);  // co-resident CTAs
+// The packed word-list kernel (kernels_words.cu): a cooperative launch of ctas >= 2 CTAs for a
+// bit-packed whole film with occupied-word lists; co-resident CTAs with this block size.
+int launch_words(const SweepArgs& a, int ctas, int threads, void* stream);
+int words_max_ctas(int threads, int* out);
 
 // Row slabs in shared memory (kernels_slabs.cu): a packed film split by rows over G co-resident
 // CTAs, each holding its rows and one halo row on each side in shared memory.  A CTA updates its

@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(kSlabBlock, 1) k_slabs(const __grid_constant__
         const unsigned long long sweep = (unsigned long long)(a.sweep0 + t + 1);
         const uint32_t gthr = gate_s[0];
         const bool always_draw = (gate_s[1] & kFlagAlwaysDraw) != 0;
+        const bool carry = !GATE && (gate_s[1] & kFlagNoNever) != 0;
         int dM = 0, dB = 0;
         for (int c = 0; c < 4; ++c) {
             const int P = (int)(4 * t) + c, buf = P & 1;
@@ -312,7 +313,10 @@ __global__ void __launch_bounds__(kSlabBlock, 1) k_slabs(const __grid_constant__
                     uint4 u_first[4];
                     philox10_xn<4>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u_first);
                     const uint32_t F =
-                        packed_decide<GATE>(S, O, up, V, q0, sweep, tab, gthr, always_draw, f.key0, f.key1, u_first, dM, dB);
+                        carry ? packed_decide<false, true>(S, O, up, V, q0, sweep, tab, gthr, always_draw, f.key0, f.key1,
+                                                           u_first, dM, dB)
+                              : packed_decide<GATE>(S, O, up, V, q0, sweep, tab, gthr, always_draw, f.key0, f.key1,
+                                                    u_first, dM, dB);
                     if (F) {
                         const uint32_t Sn = S ^ F;
                         spin32[2 * at] = Sn;

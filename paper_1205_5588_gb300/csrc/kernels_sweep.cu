@@ -15,7 +15,7 @@
 
 #include <algorithm>
 
-#include "sweep_core.cuh"
+#include "grid_sync.cuh"
 
 namespace isf {
 
@@ -23,82 +23,6 @@ namespace {
 
 enum { MODE_INT8 = 0, MODE_GENERIC = 1, MODE_PACKED = 2 };
 constexpr int kBlock = 512;      // largest CTA of the global kernel (<= 128 registers per thread)
-constexpr unsigned kSpinLimit = 1u << 22;   // ~ seconds of waiting, then give up
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ int ld_volatile_i32(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
-
-// Barrier over the G co-resident CTAs of a cooperative launch.  The arrival counter only grows
-// during a launch (the host zeroes it before each launch): barrier b is passed once it reaches
-// b * G.  Thread 0 of each CTA adds 1 with release semantics and polls with acquire loads; the
-// wait is bounded, and on expiry the kernel records ISF_ERR_TIMEOUT and every CTA returns.
-__device__ __forceinline__ bool grid_barrier(FilmState* st, unsigned G, unsigned& target, int* ok_s) {
-    __syncthreads();
-    if (G > 1) {
-        if (threadIdx.x == 0) {
-            int ok = 1;
-            target += G;
-            red_release_add_u32(&st->bar_count, 1u);
-            unsigned spins = 0;
-            while ((int)(ld_acquire_u32(&st->bar_count) - target) < 0) {
-                ++spins;
-                if ((spins & 15u) == 0 && ld_volatile_i32(&st->error)) { ok = 0; break; }
-                if (spins > kSpinLimit) {
-                    atomicCAS(&st->error, 0, (int)ISF_ERR_TIMEOUT);
-                    st->error_where = 1;
-                    ok = 0;
-                    break;
-                }
-                if (spins > 64) __nanosleep(32);
-            }
-            *ok_s = ok;
-        }
-        __syncthreads();
-        return *ok_s != 0;
-    }
-    return true;
-}
-
-// The barrier in two halves, so that work needing no other CTA's writes of the pass (the next
-// pass's first random words) can run while thread 0 waits.
-__device__ __forceinline__ void grid_arrive(FilmState* st, unsigned G, unsigned& target) {
-    __syncthreads();
-    if (G > 1 && threadIdx.x == 0) {
-        target += G;
-        red_release_add_u32(&st->bar_count, 1u);
-    }
-}
-__device__ __forceinline__ bool grid_wait(FilmState* st, unsigned G, unsigned target, int* ok_s) {
-    if (G > 1) {
-        if (threadIdx.x == 0) {
-            int ok = 1;
-            unsigned spins = 0;
-            while ((int)(ld_acquire_u32(&st->bar_count) - target) < 0) {
-                ++spins;
-                if ((spins & 15u) == 0 && ld_volatile_i32(&st->error)) { ok = 0; break; }
-                if (spins > kSpinLimit) {
-                    atomicCAS(&st->error, 0, (int)ISF_ERR_TIMEOUT);
-                    st->error_where = 1;
-                    ok = 0;
-                    break;
-                }
-                if (spins > 64) __nanosleep(32);
-            }
-            *ok_s = ok;
-        }
-        __syncthreads();
-        return *ok_s != 0;
-    }
-    return true;
-}
-
 // ---- int8 layout, open boundaries: one thread per 16-site chunk of a colour row ------------
 // The chunk at byte offset `base` of colour c (layer parity zp), Philox counter q0.
 template <bool GATE>
@@ -169,30 +93,6 @@ __device__ __forceinline__ void block_generic(const DevFilm& f, int c, int z, in
     }
 }
 
-// ---- packed layout: one thread per 32-site word --------------------------------------------
-// Loads of one packed word position: the own spin and occupancy words, the 12 neighbour spin
-// words (three of them shifted by one column, completed from the word before or after) as the
-// neighbours' up bits, and the position's precomputed bit-sliced count V of vacant neighbours.
-// NARROW: every offset fits 32 bits, so each address is one 32-bit offset from the own word's
-// pointer.
-template <bool NARROW>
-__device__ __forceinline__ void packed_loads(const DevFilm& f, const NbrClass& nc, int64_t base, uint32_t& S,
-                                             uint32_t& O, uint32_t up[12]) {
-    const uint32_t* spb = f.sp + base;
-    auto off = [&](int k) -> int64_t { return NARROW ? (int64_t)(int32_t)nc.off[k] : nc.off[k]; };
-    S = spb[0];
-    O = f.op[base];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) up[k] = spb[off(k)];
-    if (nc.sgn < 0) {
-#pragma unroll
-        for (int k = 9; k < 12; ++k) up[k] = __funnelshift_l(spb[off(k) - 1], spb[off(k)], 1);
-    } else {
-#pragma unroll
-        for (int k = 9; k < 12; ++k) up[k] = __funnelshift_r(spb[off(k)], spb[off(k) + 1], 1);
-    }
-}
-
 // The bit-sliced count of vacant neighbours from the 12 neighbour occupancy words (for words
 // that have no precomputed entry).
 template <bool NARROW>
@@ -213,12 +113,14 @@ __device__ __forceinline__ void packed_vacancies(const DevFilm& f, const NbrClas
 }
 
 // One packed word at word index `base` of colour c (layer parity zp), Philox counter q0.  vq: its
-// precomputed vacant-neighbour count (VQ), else counted from the occupancy words.
+// precomputed vacant-neighbour count (VQ), else counted from the occupancy words.  sflags: the
+// step's table flags (kFlagAlwaysDraw, kFlagNoNever).
 template <bool GATE, bool NARROW, bool VQ>
 __device__ __forceinline__ void word_packed_at(const DevFilm& f, int c, int zp, int64_t base, uint32_t q0,
                                                const uint4* vq, unsigned long long sweep, const uint32_t* tab,
-                                               uint32_t gthr, bool always_draw, int& dM, int& dB,
+                                               uint32_t gthr, uint32_t sflags, int& dM, int& dB,
                                                const uint4 (&pre)[4], bool use_pre) {
+    const bool always_draw = (sflags & kFlagAlwaysDraw) != 0;
     const NbrClass& nc = f.nb[c][zp];
     uint32_t S, O, up[12], V[4];
     packed_loads<NARROW>(f, nc, base, S, O, up);
@@ -241,31 +143,26 @@ __device__ __forceinline__ void word_packed_at(const DevFilm& f, int c, int zp, 
         philox10_xn<4>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, u_first);
     }
     if (!O) return;             // no occupied site in the word (tested after the loads are issued)
-    const uint32_t F = packed_decide<GATE>(S, O, up, V, q0, sweep, tab, gthr, always_draw, f.key0, f.key1, u_first, dM, dB);
+    const uint32_t F =
+        (!GATE && (sflags & kFlagNoNever))
+            ? packed_decide<false, true>(S, O, up, V, q0, sweep, tab, gthr, always_draw, f.key0, f.key1, u_first, dM, dB)
+            : packed_decide<GATE>(S, O, up, V, q0, sweep, tab, gthr, always_draw, f.key0, f.key1, u_first, dM, dB);
     if (F) f.sp[base] = S ^ F;
 }
 
 template <bool GATE, bool NARROW>
 __device__ __forceinline__ void word_packed(const DevFilm& f, int c, int z, int j, int w,
                                             unsigned long long sweep, const uint32_t* tab,
-                                            uint32_t gthr, bool always_draw, int& dM, int& dB, const uint4 (&pre)[4],
+                                            uint32_t gthr, uint32_t sflags, int& dM, int& dB, const uint4 (&pre)[4],
                                             bool use_pre) {
     word_packed_at<GATE, NARROW, false>(f, c, z & 1, addrw(f, c, z, j, w), block_counter(f, c, z, j, 32 * w), nullptr,
-                                        sweep, tab, gthr, always_draw, dM, dB, pre, use_pre);
-}
-
-// First work item of this thread in a pass.  Warps are numbered across CTAs first (warp w of
-// CTA b is warp w * G + b), so when a pass has fewer items than two per thread, the threads
-// that take one more item are spread evenly over all CTAs (and SMs); lanes stay consecutive,
-// so a warp still reads consecutive words.
-__device__ __forceinline__ int first_item(unsigned G, unsigned cta) {
-    return (((int)(threadIdx.x >> 5) * (int)G + (int)cta) << 5) + (int)(threadIdx.x & 31);
+                                        sweep, tab, gthr, sflags, dM, dB, pre, use_pre);
 }
 
 template <int MODE, bool GATE>
 __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned long long sweep,
                                             const uint32_t* tab, uint32_t gthr, int items,
-                                            ItemWalk w, unsigned G, unsigned cta, bool always_draw, int& dM, int& dB,
+                                            ItemWalk w, unsigned G, unsigned cta, uint32_t sflags, int& dM, int& dB,
                                             const uint4 (&pre)[4], bool have_pre) {
     const int stride = (int)G * blockDim.x;
     if (MODE == MODE_PACKED && f.ient) {
@@ -280,7 +177,7 @@ __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned lo
         for (int it = it0; it < n; it += stride) {
             const uint2 pq = ent[it];
             word_packed_at<GATE, true, true>(f, c, (int)(pq.x >> 31), (int64_t)(pq.x & 0x7FFFFFFFu), pq.y, vq + it, sweep,
-                                             tab, gthr, always_draw, dM, dB, pre, have_pre && it == it0);
+                                             tab, gthr, sflags, dM, dB, pre, have_pre && it == it0);
         }
         return;
     }
@@ -299,7 +196,7 @@ __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned lo
     for (int it = first_item(G, cta); it < items; it += stride, w.next()) {
         if (MODE == MODE_INT8) chunk_int8<GATE>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB);
         else if (MODE == MODE_GENERIC) block_generic<GATE>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB);
-        else word_packed<GATE, false>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, always_draw, dM, dB, pre, false);
+        else word_packed<GATE, false>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, sflags, dM, dB, pre, false);
     }
 }
 
@@ -348,11 +245,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
         }
         const unsigned long long sweep = (unsigned long long)(a.sweep0 + t + 1);
         const uint32_t gthr = gate_s[0];
-        const bool always_draw = (gate_s[1] & kFlagAlwaysDraw) != 0;
+        const uint32_t sflags = gate_s[1];
         int dM = 0, dB = 0;
         for (int c = c_begin; c < c_end; ++c) {
-            if (a.use_gate) colour_pass<MODE, true>(f, c, sweep, tab, gthr, items, walk0, G, cta, always_draw, dM, dB, pf, have_pf);
-            else colour_pass<MODE, false>(f, c, sweep, tab, gthr, items, walk0, G, cta, always_draw, dM, dB, pf, have_pf);
+            if (a.use_gate) colour_pass<MODE, true>(f, c, sweep, tab, gthr, items, walk0, G, cta, sflags, dM, dB, pf, have_pf);
+            else colour_pass<MODE, false>(f, c, sweep, tab, gthr, items, walk0, G, cta, sflags, dM, dB, pf, have_pf);
             if (c == c_end - 1) {
                 long long sM = dM, sB = dB;
                 block_sum2(sM, sB, red);
@@ -398,211 +295,6 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
 template <int MODE>
 __global__ void __launch_bounds__(kBlock) k_sweep(const __grid_constant__ SweepArgs a) {
     sweep_body<MODE>(a, gridDim.x, blockIdx.x);
-}
-
-// ---- packed films with occupied-word lists on the whole grid: random words drawn ahead -----
-// A colour pass of a packed film is half Philox arithmetic (8 blocks per 32-site word), and
-// the counters of a pass's words are known before the pass: they depend on the word and the
-// sweep, not on the spins.  So once a warp has decided its words of pass c it arrives at the
-// grid barrier (through a per-CTA counter, without waiting for the CTA's other warps) and draws
-// the Philox blocks of its words of pass c + 1 into shared memory (the first four blocks of each
-// word, and the last four too when the step's table says nearly every word needs them), and the
-// pass itself only loads, counts, looks up and compares.  The threads with fewer words in a pass
-// thus fill the time the others need for their extra word, and everyone fills the barrier's
-// latency.  A thread keeps kAheadSlots words this way; further words of a pass (small grids)
-// draw in the pass.
-constexpr int kAheadSlots = 2;
-
-// Bytes of dynamic shared memory of k_words with this block size: the random words drawn ahead
-// ([slot][block][thread] uint4) and the thread's list entries of every colour ([colour][slot]
-// [thread] uint2; a thread takes the same words in every sweep, so they are read once a launch).
-constexpr size_t ahead_bytes(int threads) {
-    return (size_t)kAheadSlots * 8 * (size_t)threads * sizeof(uint4) + (size_t)4 * kAheadSlots * threads * sizeof(uint2);
-}
-
-// The Philox blocks of this thread's first kAheadSlots words of colour c at `sweep` into its
-// slots of `ahead`; the second four blocks only when `both`.  ents: the entries cached in shared
-// memory.
-__device__ __forceinline__ void draw_ahead(const DevFilm& f, int c, unsigned long long sweep, bool both, int it0,
-                                           int stride, uint4* ahead, const uint2* ents, const uint32_t (&rk)[20]) {
-    const SweepConst sc = sweep_const(sweep, rk);
-    const int n = f.nitems[c];
-    const int bd = blockDim.x, tid = threadIdx.x;
-    int it = it0;
-#pragma unroll 1
-    for (int slot = 0; slot < kAheadSlots && it < n; ++slot, it += stride) {
-        const uint32_t q = ents[(c * kAheadSlots + slot) * bd + tid].y;
-        uint4 u[4];
-        philox10_sc<4>(q, 0u, sc, rk, u);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) ahead[(slot * 8 + v) * bd + tid] = u[v];
-        if (both) {
-            philox10_sc<4>(q + 4, 0u, sc, rk, u);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) ahead[(slot * 8 + 4 + v) * bd + tid] = u[v];
-        }
-    }
-}
-
-// One colour pass over this thread's listed words it0, it0 + stride, ... (their random words
-// drawn ahead in `ahead` for the first kAheadSlots; `both`: the second four blocks too).
-template <bool GATE>
-__device__ __forceinline__ void pass_words(const DevFilm& f, int c, unsigned long long sweep, const uint32_t* tab,
-                                           uint32_t gthr, bool always_draw, bool both, bool no_never, int it0,
-                                           int stride, const uint4* ahead, const uint2* ents, int& dM, int& dB) {
-    const uint2* ent = reinterpret_cast<const uint2*>(f.ient) + (int64_t)c * f.item_cap;
-    const uint4* vq = reinterpret_cast<const uint4*>(f.ivq) + (int64_t)c * f.item_cap;
-    const int n = f.nitems[c];
-    const int bd = blockDim.x, tid = threadIdx.x;
-    int slot = 0;
-#pragma unroll 1
-    for (int it = it0; it < n; it += stride, ++slot) {
-        // the entry from shared memory, so the word's loads leave at once
-        const uint2 pq = slot < kAheadSlots ? ents[(c * kAheadSlots + slot) * bd + tid] : ent[it];
-        const int64_t base = (int64_t)(pq.x & 0x7FFFFFFFu);
-        const NbrClass& nc = f.nb[c][pq.x >> 31];
-        uint32_t S, O, up[12], V[4];
-        packed_loads<true>(f, nc, base, S, O, up);
-        const uint4 v4 = vq[it];
-        V[0] = v4.x; V[1] = v4.y; V[2] = v4.z; V[3] = v4.w;
-        uint4 uf[4], us[4];
-        const bool drawn = slot < kAheadSlots;
-        if (drawn) {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) uf[v] = ahead[(slot * 8 + v) * bd + tid];
-            if (both) {
-#pragma unroll
-                for (int v = 0; v < 4; ++v) us[v] = ahead[(slot * 8 + 4 + v) * bd + tid];
-            }
-        } else {
-            philox10_xn<4>(pq.y, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, f.key0, f.key1, uf);
-        }
-        const uint4* u2 = (drawn && both) ? us : nullptr;
-        const uint32_t F =
-            (!GATE && no_never)
-                ? packed_decide<false, true>(S, O, up, V, pq.y, sweep, tab, gthr, always_draw, f.key0, f.key1, uf,
-                                             dM, dB, u2)
-                : packed_decide<GATE>(S, O, up, V, pq.y, sweep, tab, gthr, always_draw, f.key0, f.key1, uf, dM, dB,
-                                      u2);
-        if (F) f.sp[base] = S ^ F;
-    }
-}
-
-template <bool GATE>
-__global__ void __launch_bounds__(kBlock) k_words(const __grid_constant__ SweepArgs a) {
-    extern __shared__ uint4 ahead[];                 // [kAheadSlots][8][blockDim], then the entries
-    __shared__ uint32_t tab[128];
-    __shared__ uint32_t gate_s[2];
-    __shared__ int ok_s;
-    __shared__ RunState rs;                          // touched by the folding thread only
-    __shared__ unsigned warps_in;                    // warps that finished a pass (grows through the launch)
-    __shared__ long long acc_s[2];                   // the CTA's dM, dB of the current sweep
-    const DevFilm& f = a.f;
-    FilmState* st = a.st;
-    const unsigned G = gridDim.x, cta = blockIdx.x;
-    const unsigned nwarps = blockDim.x >> 5;
-    unsigned pass_no = 0;
-    if (threadIdx.x == 0) {         // published by stage_table's barrier below
-        warps_in = 0;
-        acc_s[0] = 0;
-        acc_s[1] = 0;
-    }
-    unsigned target = 0;
-    int k = a.k0, pos = a.pos0;
-    const bool folder = cta == 0 && threadIdx.x == 0;
-    int k_eq = 0, k_tot = 0;
-    if (folder) {
-        load_run_state(st, rs);
-        k_eq = a.step_eq[k];
-        k_tot = a.step_total[k];
-    }
-    const int it0 = first_item(G, cta);
-    const int stride = (int)G * blockDim.x;
-    uint32_t rk[20];
-    round_keys(f.key0, f.key1, rk);
-    uint2* ents = reinterpret_cast<uint2*>(ahead + (size_t)kAheadSlots * 8 * blockDim.x);
-    for (int c = 0; c < 4; ++c) {
-        const uint2* ent = reinterpret_cast<const uint2*>(f.ient) + (int64_t)c * f.item_cap;
-        for (int slot = 0; slot < kAheadSlots; ++slot) {
-            const int it = it0 + slot * stride;
-            ents[(c * kAheadSlots + slot) * blockDim.x + threadIdx.x] = it < f.nitems[c] ? ent[it] : make_uint2(0u, 0u);
-        }
-    }
-    auto step_draws_all = [&](int kk) {
-        return (a.tables[(size_t)kk * kTableStride + kFlagSlot] & kFlagAlwaysDraw) != 0u;
-    };
-    // the first pass's random words
-    {
-        const int kf = a.pos0 == a.step_total[a.k0] ? a.k0 + 1 : a.k0;
-        if (a.nsweeps > 0)
-            draw_ahead(f, 0, (unsigned long long)(a.sweep0 + 1), step_draws_all(kf), it0, stride, ahead, ents, rk);
-    }
-    stage_table<true>(a.tables, k, tab, gate_s);
-    for (long long t = 0; t < a.nsweeps; ++t) {
-        if (pos == a.step_total[k]) {
-            ++k;
-            pos = 0;
-            stage_table<true>(a.tables, k, tab, gate_s);
-            if (folder) { k_eq = a.step_eq[k]; k_tot = a.step_total[k]; }
-        }
-        const unsigned long long sweep = (unsigned long long)(a.sweep0 + t + 1);
-        const uint32_t gthr = gate_s[0];
-        const bool always_draw = (gate_s[1] & kFlagAlwaysDraw) != 0;
-        // the step of the next sweep (for the random words of its first pass)
-        const int k_next = pos + 1 == a.step_total[k] ? k + 1 : k;
-        int dM = 0, dB = 0;
-        for (int c = 0; c < 4; ++c) {
-            pass_words<GATE>(f, c, sweep, tab, gthr, always_draw, always_draw, (gate_s[1] & kFlagNoNever) != 0, it0,
-                             stride, ahead, ents, dM, dB);
-            // each warp arrives as soon as its own words are done: the CTA's last warp to finish
-            // (release / acquire on a shared counter orders every warp's stores before it) adds
-            // the CTA's (dM, dB) of the sweep and arrives at the grid barrier with release semantics
-            const int lane = threadIdx.x & 31;
-            if (c == 3) {
-                const long long wM = warp_sum((long long)dM), wB = warp_sum((long long)dB);
-                if (lane == 0 && (wM | wB)) {
-                    atomicAdd(reinterpret_cast<unsigned long long*>(&acc_s[0]), (unsigned long long)wM);
-                    atomicAdd(reinterpret_cast<unsigned long long*>(&acc_s[1]), (unsigned long long)wB);
-                }
-            }
-            __syncwarp();
-            ++pass_no;
-            if (lane == 0) {
-                unsigned old;
-                asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;"
-                             : "=r"(old) : "r"((unsigned)__cvta_generic_to_shared(&warps_in)) : "memory");
-                if (old == pass_no * nwarps - 1u) {
-                    if (c == 3) {
-                        const long long sM = acc_s[0], sB = acc_s[1];
-                        acc_s[0] = 0;
-                        acc_s[1] = 0;
-                        if (sM | sB) {
-                            unsigned long long* acc = reinterpret_cast<unsigned long long*>(&st->acc[sweep & 1][0]);
-                            atomicAdd(acc, (unsigned long long)sM);
-                            atomicAdd(acc + 1, (unsigned long long)sB);
-                        }
-                    }
-                    if (G > 1) red_release_add_u32(&st->bar_count, 1u);
-                }
-            }
-            target += G;
-            // while the other warps and CTAs finish this pass: the random words of the next one
-            if (c < 3) {
-                draw_ahead(f, c + 1, sweep, always_draw, it0, stride, ahead, ents, rk);
-            } else if (t + 1 < a.nsweeps) {
-                draw_ahead(f, 0, sweep + 1, step_draws_all(k_next), it0, stride, ahead, ents, rk);
-            }
-            if (!grid_wait(st, G, target, &ok_s)) return;
-        }
-        if (folder) {
-            unsigned long long* acc = reinterpret_cast<unsigned long long*>(&st->acc[sweep & 1][0]);
-            const long long sM = (long long)atomicExch(acc, 0ull);
-            const long long sB = (long long)atomicExch(acc + 1, 0ull);
-            fold_sweep(a, rs, k, pos, k_eq, k_tot, sM, sB, t);
-        }
-        ++pos;
-    }
-    if (folder) store_run_state(st, rs);
 }
 
 __device__ __forceinline__ int mode_of_film(const DevFilm& f);
@@ -664,11 +356,6 @@ __global__ void __launch_bounds__(kBlock) k_batch_global(const SweepArgs* films,
 // k_words runs packed whole films with word lists over several CTAs (grid barrier, whole sweeps).
 inline bool words_path(const DevFilm& f) { return f.packed && f.ient != nullptr && !f.slab; }
 
-template <bool GATE>
-cudaError_t words_smem_attr(int threads) {
-    return cudaFuncSetAttribute(k_words<GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ahead_bytes(threads));
-}
-
 template <int MODE>
 int launch_mode(const SweepArgs& a, int ctas, int threads, cudaStream_t s) {
     if (threads % 32 || threads < 32 || threads > kBlock) return (int)cudaErrorInvalidValue;   // whole warps
@@ -678,14 +365,8 @@ int launch_mode(const SweepArgs& a, int ctas, int threads, cudaStream_t s) {
     }
     cudaError_t e = cudaMemsetAsync(&a.st->bar_count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return (int)e;
+    if (MODE == MODE_PACKED && words_path(a.f) && !a.pass_plus1) return launch_words(a, ctas, threads, s);
     void* args[] = {const_cast<SweepArgs*>(&a)};
-    if (MODE == MODE_PACKED && words_path(a.f) && !a.pass_plus1) {
-        const size_t smem = ahead_bytes(threads);
-        const void* fn = a.use_gate ? (const void*)k_words<true> : (const void*)k_words<false>;
-        e = a.use_gate ? words_smem_attr<true>(threads) : words_smem_attr<false>(threads);
-        if (e != cudaSuccess) return (int)e;
-        return (int)cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(threads), args, smem, s);
-    }
     return (int)cudaLaunchCooperativeKernel((const void*)k_sweep<MODE>, dim3(ctas), dim3(threads), args, 0, s);
 }
 
@@ -695,15 +376,7 @@ int max_ctas_mode(const DevFilm& f, int threads, int* out) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (MODE == MODE_PACKED && words_path(f)) {
-        // the gate and no-gate kernels have the same shared memory; take the smaller residency
-        int per_g = 0;
-        if (e == cudaSuccess) e = words_smem_attr<false>(threads);
-        if (e == cudaSuccess) e = words_smem_attr<true>(threads);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_words<false>, threads, ahead_bytes(threads));
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_g, k_words<true>, threads, ahead_bytes(threads));
-        per = per < per_g ? per : per_g;
+        if (e == cudaSuccess) return words_max_ctas(threads, out);
     } else if (e == cudaSuccess) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<MODE>, threads, 0);
     }

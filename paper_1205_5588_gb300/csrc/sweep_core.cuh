@@ -411,6 +411,30 @@ __device__ __forceinline__ uint32_t packed_decide(uint32_t S, uint32_t O, const 
     return F;
 }
 
+// ---- packed layout: the loads of one 32-site word -------------------------------------------
+// Loads of one packed word position: the own spin and occupancy words, the 12 neighbour spin
+// words (three of them shifted by one column, completed from the word before or after) as the
+// neighbours' up bits, and the position's precomputed bit-sliced count V of vacant neighbours.
+// NARROW: every offset fits 32 bits, so each address is one 32-bit offset from the own word's
+// pointer.
+template <bool NARROW>
+__device__ __forceinline__ void packed_loads(const DevFilm& f, const NbrClass& nc, int64_t base, uint32_t& S,
+                                             uint32_t& O, uint32_t up[12]) {
+    const uint32_t* spb = f.sp + base;
+    auto off = [&](int k) -> int64_t { return NARROW ? (int64_t)(int32_t)nc.off[k] : nc.off[k]; };
+    S = spb[0];
+    O = f.op[base];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) up[k] = spb[off(k)];
+    if (nc.sgn < 0) {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) up[k] = __funnelshift_l(spb[off(k) - 1], spb[off(k)], 1);
+    } else {
+#pragma unroll
+        for (int k = 9; k < 12; ++k) up[k] = __funnelshift_r(spb[off(k)], spb[off(k) + 1], 1);
+    }
+}
+
 // Walks a thread's work items it, it + T, it + 2T, ... of a pass laid out as (z, row, chunk)
 // with nc chunks per row and nr rows per layer, by carries instead of divisions.
 struct ItemWalk {
