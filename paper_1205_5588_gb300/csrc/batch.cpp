@@ -344,6 +344,40 @@ int isf_batch_tune(isf_batch* b, void* cuda_stream) {
     return set_last_error(ISF_OK, "");
 }
 
+namespace {
+// Units of the four classes (in: what each could keep resident alone; out: its share of the GPU
+// by work: that share of its resident units, at least one, at most one per film; what the caps
+// leave over goes to the others by their work).
+void share_units(const std::vector<Item>& A, const std::vector<Item>& B, const std::vector<Item>& D,
+                 const std::vector<Item>& E, int* ua, int* ub, int* ud, int* ue) {
+    const std::vector<Item>* cls[4] = {&A, &B, &D, &E};
+    int* u[4] = {ua, ub, ud, ue};
+    double w[4] = {0.0, 0.0, 0.0, 0.0}, wt = 0.0;
+    int maxu[4], cap[4];
+    for (int x = 0; x < 4; ++x) {
+        for (const Item& it : *cls[x]) w[x] += it.work;
+        wt += w[x];
+        maxu[x] = *u[x];
+        cap[x] = std::min<int>(*u[x], (int)cls[x]->size());
+    }
+    if (wt <= 0.0) return;
+    double used = 0.0, w_open = 0.0;     // fraction of the GPU taken; work of the classes below their cap
+    for (int x = 0; x < 4; ++x) {
+        if (cls[x]->empty() || maxu[x] < 1) continue;
+        *u[x] = std::max(1, std::min(cap[x], (int)(w[x] / wt * maxu[x])));
+        used += (double)*u[x] / maxu[x];
+        if (*u[x] < cap[x]) w_open += w[x];
+    }
+    const double left = 1.0 - used;
+    if (left > 0.0 && w_open > 0.0) {
+        for (int x = 0; x < 4; ++x) {
+            if (cls[x]->empty() || maxu[x] < 1 || *u[x] >= cap[x]) continue;
+            *u[x] = std::min(cap[x], *u[x] + (int)(left * w[x] / w_open * maxu[x]));
+        }
+    }
+}
+}  // namespace
+
 int isf_batch_run(isf_batch* b, void* cuda_stream) { return isf_batch_run_sweeps(b, -1, cuda_stream); }
 
 int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
@@ -409,13 +443,11 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
     if (n_e) {
         int e = batch_cluster_global_units(kKE, kThreadsE, &units_e);
         if (e || units_e < 1) return fail(ISF_ERR_CUDA, "cluster global-memory batch kernel cannot be resident");
-        units_e = std::min(units_e, n_e);
     }
     int units_d = 0;
     if (n_d) {
         int e = batch_global_units(kThreadsD, &units_d);
         if (e || units_d < 1) return fail(ISF_ERR_CUDA, "global-memory batch kernel cannot be resident");
-        units_d = std::min(units_d, n_d);
     }
     uint32_t smem_a = 0, smem_b = 0;
     for (int i = 0; i < n_a; ++i) {
@@ -430,13 +462,24 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
     if (n_a) {
         int e = batch_units_possible(1, ta, smem_a, &units_a);
         if (e || units_a < 1) return fail(ISF_ERR_CUDA, "single-CTA batch kernel cannot be resident");
-        units_a = std::min(units_a, n_a);
     }
     if (n_b) {
         int e = batch_units_possible(K, tb, smem_b, &units_b);
         if (e || units_b < 1) return fail(ISF_ERR_CUDA, "cluster batch kernel cannot be resident");
-        units_b = std::min(units_b, n_b);
     }
+    // The persistent queue kernels run at once.  Sized alone, each would take the whole GPU, and
+    // the one the hardware places first would hold its SMs until its queue drains while the
+    // others wait, so the batch's time would depend on the placement.  When all the work is on the
+    // two global-memory classes (bit-packed, periodic-column or over-sized films: the same code
+    // per site, so work is a fair measure of time), the GPU is shared in proportion to their work
+    // and both kernels are resident from the start.  The resident int8 classes run several times
+    // faster per site than the global-memory ones, so there work is no measure of time; they keep
+    // whole-GPU grids.
+    if (A.empty() && B.empty()) share_units(A, B, D, E, &units_a, &units_b, &units_d, &units_e);
+    units_a = std::min(units_a, n_a);
+    units_b = std::min(units_b, n_b);
+    units_d = std::min(units_d, n_d);
+    units_e = std::min(units_e, n_e);
     if (n_a || n_b || n_d || n_e) {
         const int64_t sig[12] = {n_a, n_b, K, ta, tb, (int64_t)smem_a << 32 | smem_b, units_a, units_b, n_d, units_d,
                                  n_e, units_e};
