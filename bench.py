@@ -252,7 +252,7 @@ def e2e_film(I, spec, seed, steps, stream):
 NCU_RECORDS = {
     "fractal256": {"sources": ["kernels_resident.cu", "sweep_core.cuh", "device_common.cuh"],
                    "sources_sha256": "d574bb97950cbc05a389bc6df92c2722c877c9c503b0b4e9abaad1b845f40836",
-                   "bytes_per_launch": 766720.0, "inst_per_attempt": None},
+                   "bytes_per_launch": 1080064.0, "inst_per_attempt": None},
     "fractal2048": {"sources": ["kernels_words.cu", "sweep_core.cuh", "device_common.cuh", "grid_sync.cuh"],
                     "sources_sha256": "398dba028473de84ae47f72fcc5ebddbd022b1aef160b04808563df77a274f1a",
                     "bytes_per_launch": 20967936.0 + 623104.0, "inst_per_attempt": 25.85},
