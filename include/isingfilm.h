@@ -238,8 +238,9 @@ int isf_fold_series(int32_t nsteps, const double* T, const double* h, const int3
  * of the whole batch's work per such CTA, so that no film finishes last on its own CTA) or one
  * cluster of 8 CTAs (up to 2^24), all concurrently on forked streams (when only the two
  * global-memory classes have films, the SMs are shared between them in proportion to their work,
- * so that both are resident from the start); larger films run after them on the multi-CTA global
- * path.  Each film's
+ * so that both are resident from the start; a global-memory kernel whose own films are done
+ * takes the resident films of its size class that have not started, and runs them in global
+ * memory); larger films run after them on the multi-CTA global path.  Each film's
  * trajectory is the one it has alone.  Asynchronous on cuda_stream; read each film with
  * isf_read_observables / isf_read_spins afterwards. */
 typedef struct isf_batch isf_batch;

@@ -132,14 +132,18 @@ int enqueue(isf_batch* b, cudaStream_t s, int n_a, int n_b, int K, int ta, int t
     CUDA_TRY(cudaEventRecord(b->ev_fork, s), "fork");
     if (n_d) {
         CUDA_TRY(cudaStreamWaitEvent(b->sd, b->ev_fork, 0), "fork");
-        int e = launch_batch_global(b->d_gdesc, n_d, b->d_next + 2, kThreadsD, units_d, b->sd);
+        // once its own films are done, it takes the single-CTA resident films not yet started
+        const StealQueue steal{b->d_desc, n_a, b->d_next + 0};
+        int e = launch_batch_global(b->d_gdesc, n_d, b->d_next + 2, kThreadsD, units_d, b->sd, steal);
         if (e) return cuda_fail((cudaError_t)e, "batch launch (one CTA per film, global memory)");
         CUDA_TRY(cudaEventRecord(b->ev_d, b->sd), "join");
         CUDA_TRY(cudaStreamWaitEvent(s, b->ev_d, 0), "join");
     }
     if (n_e) {
         CUDA_TRY(cudaStreamWaitEvent(b->se, b->ev_fork, 0), "fork");
-        int e = launch_batch_cluster_global(b->d_gdesc + n_d, n_e, b->d_next + 3, kKE, kThreadsE, units_e, b->se);
+        // once its own films are done, it takes the resident cluster films not yet started
+        const StealQueue steal{b->d_desc + n_a, n_b, b->d_next + 1};
+        int e = launch_batch_cluster_global(b->d_gdesc + n_d, n_e, b->d_next + 3, kKE, kThreadsE, units_e, b->se, steal);
         if (e) return cuda_fail((cudaError_t)e, "batch launch (one cluster per film, global memory)");
         CUDA_TRY(cudaEventRecord(b->ev_e, b->se), "join");
         CUDA_TRY(cudaStreamWaitEvent(s, b->ev_e, 0), "join");

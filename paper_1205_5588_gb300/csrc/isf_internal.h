@@ -258,10 +258,18 @@ int sweep_items_per_pass(const DevFilm& f);                            // work i
 // Batched films one CTA each in global memory (kernels_sweep.cu): `units` persistent CTAs take
 // films from the device queue films[0..n) via the counter *next; any layout and boundary.
 int batch_global_units(int threads, int* units);
-int launch_batch_global(const SweepArgs* films, int n, unsigned* next, int threads, int units, void* stream);
+// A resident queue whose films a global-memory queue kernel takes once its own queue is empty
+// (films[0..n) claimed through the same counter *next as the resident kernel; n = 0: none).
+struct StealQueue {
+    const ResArgs* films;
+    int32_t n;
+    unsigned* next;
+};
+int launch_batch_global(const SweepArgs* films, int n, unsigned* next, int threads, int units, void* stream,
+                        StealQueue steal);
 // The same with one thread-block cluster of K (2, 4 or 8) CTAs per film.
 int batch_cluster_global_units(int K, int threads, int* units);
 int launch_batch_cluster_global(const SweepArgs* films, int n, unsigned* next, int K, int threads, int units,
-                                void* stream);
+                                void* stream, StealQueue steal);
 
 }  // namespace isf

@@ -299,17 +299,35 @@ __global__ void __launch_bounds__(kBlock) k_sweep(const __grid_constant__ SweepA
 
 __device__ __forceinline__ int mode_of_film(const DevFilm& f);
 
+// The next film of a global-memory queue kernel: its own queue first; once that is empty, the
+// not yet started films of a resident queue (`steal`, the films of the resident kernel of the
+// same size class), which it runs in global memory with the same trajectory.  Returns the film's
+// index in its queue, own (>= 0) or stolen (-2 - index), or -1 when both are empty.
+__device__ __forceinline__ int take_film(unsigned* next, int nfilms, const StealQueue& steal, bool& own_done) {
+    if (!own_done) {
+        const int idx = (int)atomicAdd(next, 1u);
+        if (idx < nfilms) return idx;
+        own_done = true;
+    }
+    if (steal.n > 0) {
+        const int idx = (int)atomicAdd(steal.next, 1u);
+        if (idx < steal.n) return -2 - idx;
+    }
+    return -1;
+}
+
 // Batched films one thread-block cluster of K CTAs each, with their state in global memory:
 // every cluster takes the next film of the queue and runs its sweeps, colour passes separated
-// by the cluster barrier.
+// by the cluster barrier; then films of the resident cluster queue that have not started yet.
 template <int K>
 __global__ void __launch_bounds__(kBlock) k_batch_cluster_global(const SweepArgs* films, int nfilms,
-                                                                 unsigned* next) {
+                                                                 unsigned* next, StealQueue steal) {
     __shared__ int film_s;
     const unsigned rank = cluster_ctarank();
+    bool own_done = false;
     for (;;) {
         if (rank == 0 && threadIdx.x == 0) {
-            const int idx = (int)atomicAdd(next, 1u);
+            const int idx = take_film(next, nfilms, steal, own_done);
             for (unsigned r = 0; r < (unsigned)K; ++r) {
                 uint64_t p;
                 asm volatile("mapa.u64 %0, %1, %2;" : "=l"(p) : "l"(reinterpret_cast<uint64_t>(&film_s)), "r"(r));
@@ -319,8 +337,8 @@ __global__ void __launch_bounds__(kBlock) k_batch_cluster_global(const SweepArgs
         cluster_barrier();
         const int idx = film_s;
         cluster_barrier();      // every CTA has the index before CTA 0 writes the next one
-        if (idx < 0 || idx >= nfilms) break;
-        const SweepArgs& a = films[idx];
+        if (idx == -1 || idx >= nfilms || (idx < -1 && -2 - idx >= steal.n)) break;
+        const SweepArgs& a = idx >= 0 ? films[idx] : steal.films[-2 - idx].s;
         switch (mode_of_film(a.f)) {
             case MODE_INT8: sweep_body<MODE_INT8, BAR_CLUSTER>(a, (unsigned)K, rank); break;
             case MODE_GENERIC: sweep_body<MODE_GENERIC, BAR_CLUSTER>(a, (unsigned)K, rank); break;
@@ -335,16 +353,19 @@ __device__ __forceinline__ int mode_of_film(const DevFilm& f) {
 
 // Batched films one CTA each, with their state in global memory: every CTA takes the next film
 // of the queue (a device counter), runs its sweeps (colour passes separated by __syncthreads
-// only) and takes another until the queue is empty.  Films are independent chains.
-__global__ void __launch_bounds__(kBlock) k_batch_global(const SweepArgs* films, int nfilms, unsigned* next) {
+// only) and takes another until the queue is empty; then films of the resident single-CTA
+// queue that have not started yet.  Films are independent chains.
+__global__ void __launch_bounds__(kBlock) k_batch_global(const SweepArgs* films, int nfilms, unsigned* next,
+                                                         StealQueue steal) {
     __shared__ int film_s;
+    bool own_done = false;
     for (;;) {
-        if (threadIdx.x == 0) film_s = (int)atomicAdd(next, 1u);
+        if (threadIdx.x == 0) film_s = take_film(next, nfilms, steal, own_done);
         __syncthreads();
         const int idx = film_s;
         __syncthreads();        // every thread has the index before thread 0 takes the next one
-        if (idx < 0 || idx >= nfilms) break;
-        const SweepArgs& a = films[idx];
+        if (idx == -1 || idx >= nfilms || (idx < -1 && -2 - idx >= steal.n)) break;
+        const SweepArgs& a = idx >= 0 ? films[idx] : steal.films[-2 - idx].s;
         switch (mode_of_film(a.f)) {
             case MODE_INT8: sweep_body<MODE_INT8>(a, 1u, 0u); break;
             case MODE_GENERIC: sweep_body<MODE_GENERIC>(a, 1u, 0u); break;
@@ -417,9 +438,10 @@ int batch_global_units(int threads, int* units) {
     return (int)e;
 }
 
-int launch_batch_global(const SweepArgs* films, int n, unsigned* next, int threads, int units, void* stream) {
+int launch_batch_global(const SweepArgs* films, int n, unsigned* next, int threads, int units, void* stream,
+                        StealQueue steal) {
     if (threads % 32 || threads < 32 || threads > kBlock || units < 1) return (int)cudaErrorInvalidValue;
-    k_batch_global<<<units, threads, 0, static_cast<cudaStream_t>(stream)>>>(films, n, next);
+    k_batch_global<<<units, threads, 0, static_cast<cudaStream_t>(stream)>>>(films, n, next, steal);
     return (int)cudaGetLastError();
 }
 
@@ -446,10 +468,11 @@ int cluster_global_units_k(int threads, int* units) {
     return (int)cudaOccupancyMaxActiveClusters(units, k_batch_cluster_global<K>, &cfg);
 }
 template <int K>
-int launch_cluster_global_k(const SweepArgs* films, int n, unsigned* next, int threads, int units, cudaStream_t s) {
+int launch_cluster_global_k(const SweepArgs* films, int n, unsigned* next, int threads, int units, cudaStream_t s,
+                            StealQueue steal) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cluster_global_config<K>(threads, units, s, attr);
-    return (int)cudaLaunchKernelEx(&cfg, k_batch_cluster_global<K>, films, n, next);
+    return (int)cudaLaunchKernelEx(&cfg, k_batch_cluster_global<K>, films, n, next, steal);
 }
 }  // namespace
 
@@ -463,13 +486,13 @@ int batch_cluster_global_units(int K, int threads, int* units) {
 }
 
 int launch_batch_cluster_global(const SweepArgs* films, int n, unsigned* next, int K, int threads, int units,
-                                void* stream) {
+                                void* stream, StealQueue steal) {
     if (threads % 32 || threads < 32 || threads > kBlock || units < 1) return (int)cudaErrorInvalidValue;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     switch (K) {
-        case 2: return launch_cluster_global_k<2>(films, n, next, threads, units, s);
-        case 4: return launch_cluster_global_k<4>(films, n, next, threads, units, s);
-        case 8: return launch_cluster_global_k<8>(films, n, next, threads, units, s);
+        case 2: return launch_cluster_global_k<2>(films, n, next, threads, units, s, steal);
+        case 4: return launch_cluster_global_k<4>(films, n, next, threads, units, s, steal);
+        case 8: return launch_cluster_global_k<8>(films, n, next, threads, units, s, steal);
         default: return (int)cudaErrorInvalidValue;
     }
 }
