@@ -61,9 +61,15 @@ def workload(name: str, schedule_steps: int = 0):
     return spec
 
 
-KERNEL_OF_PATH = {"global": "k_sweep (global-memory persistent kernel, all SMs)",
-                  "resident": "k_resident (film in one cluster's shared memory)",
-                  "slabs": "k_slabs (row bands in shared memory)"}
+KERNEL_OF_PATH = {("global", True): "k_words (bit-packed word lists, persistent kernel on all SMs)",
+                  ("global", False): "k_sweep<int8> (global-memory persistent kernel)",
+                  ("resident", False): "k_resident (film in one cluster's shared memory)",
+                  ("resident", True): "k_resident (film in one cluster's shared memory)",
+                  ("slabs", True): "k_slabs (row bands in shared memory)"}
+
+
+def kernel_of(shape, packed):
+    return KERNEL_OF_PATH.get((shape["path"], bool(packed)), shape["path"])
 
 
 class Clocks:
@@ -187,7 +193,7 @@ def roofline(attempts_per_launch, t_launch, peaks, sms, sm_max_mhz, kernel, shap
 
 
 # ---------------------------------------------------------------- one film, timed ----
-def time_film(I, spec, seed, steps, warmup, stream, l2buf, path="auto"):
+def time_film(I, spec, seed, steps, warmup, stream, l2buf, path="auto", launch=(0, 0)):
     """W warm-up and K timed passes of the whole schedule of one film; returns per-step seconds
     (CUDA events on `stream`), attempts per step, launch shape, records and a sweep-kernel launch
     count of the timed region."""
@@ -197,6 +203,8 @@ def time_film(I, spec, seed, steps, warmup, stream, l2buf, path="auto"):
                     packed=spec["packed"], seed=seed, init=spec["init"], stream=stream)
     if path != "auto":
         lat.set_path(path)
+    if launch[0] or launch[1]:
+        lat.set_launch(*launch)
     n_occ = lat.info()["n_occ"]
     per_step = attempts_of(spec, n_occ)
     times = []
@@ -300,7 +308,8 @@ def run_impl(args):
 
     D.barrier(ranks)
     clocks = Clocks(dev) if rank == 0 else None
-    leg = time_film(I, spec, seed, args.steps, args.warmup, stream, l2buf, path=args.path)
+    leg = time_film(I, spec, seed, args.steps, args.warmup, stream, l2buf, path=args.path,
+                    launch=(args.ctas, args.threads))
     clk = clocks.stop() if clocks else None
     total = D.max_over_ranks(sum(leg["times"]), ranks, device="cuda")
     D.barrier(ranks)
@@ -331,7 +340,7 @@ def run_impl(args):
                 "what": "isf_lattice_create from pinned host heights + isf_set_schedule + isf_run_sweeps + "
                         "isf_read_observables, every step"},
         "gpu_launches": args.steps,
-        "roofline": roofline(per_step, t_launch, peaks, sms, sm_max, KERNEL_OF_PATH.get(shape["path"], shape["path"]),
+        "roofline": roofline(per_step, t_launch, peaks, sms, sm_max, kernel_of(shape, spec["packed"]),
                              shape, load_traffic(args.workload), ncu_record(args.workload, "inst_per_attempt")),
         "clocks": clk,
     }
@@ -345,7 +354,7 @@ def run_impl(args):
                 "unit": UNIT, "dtype": "int8", "occupied_sites": t["n_occ"], "attempts_per_step": t["per_step"],
                 "seconds_per_step": tl, "steps": len(t["times"]), "warmup": 3,
                 "roofline": roofline(t["per_step"], tl, peaks, sms, sm_max,
-                                     KERNEL_OF_PATH.get(t["shape"]["path"], t["shape"]["path"]), t["shape"],
+                                     kernel_of(t["shape"], False), t["shape"],
                                      load_traffic("fractal256"), ncu_record("fractal256", "inst_per_attempt"))}
     del l2buf
     if not args.no_batched:

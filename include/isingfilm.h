@@ -251,8 +251,10 @@ int isf_batch_clear(isf_batch* batch);
  * cluster kernel (multiples of 32 in 64..512, one warp folding); 0 = tuned or default (256; 16
  * and 512). */
 int isf_batch_set_launch(isf_batch* batch, int32_t threads_single, int32_t cluster_K, int32_t threads_cluster);
-/* on != 0: capture the queue upload and the two persistent launches in a CUDA graph once and
- * replay it on later runs with the same shape (the per-film arguments are refreshed each run). */
+/* on != 0: capture each persistent queue launch in its own single-kernel CUDA graph once and
+ * replay them on later runs with the same shapes (the per-film arguments are uploaded each run).
+ * With or without graphs the queue kernels are launched in one fixed order, so the way they
+ * share the SMs does not change from run to run. */
 int isf_batch_set_graph(isf_batch* batch, int32_t on);
 /* Autotuner: times short probe runs (copies, not the members) over threads {128, 256, 384, 512}:
  * of the largest single-CTA film, keeping the fastest threads; and, for cluster sizes {8, 16},

@@ -39,11 +39,11 @@ struct isf_batch {
     SweepArgs* d_gdesc = nullptr;   // class D entries, then class E entries
     SweepArgs* h_gdesc = nullptr;
     size_t gcap = 0;
-    cudaStream_t sa = nullptr, sb = nullptr, sc = nullptr, sd = nullptr, se = nullptr;
+    cudaStream_t sa = nullptr, sb = nullptr, sd = nullptr, se = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_a = nullptr, ev_b = nullptr, ev_d = nullptr, ev_e = nullptr, ev_done = nullptr;
     bool pending = false;
-    // graph
-    cudaGraphExec_t gexec = nullptr;
+    // one single-kernel graph per queue kernel (A, B, D, E), for the launch shape in gsig
+    cudaGraphExec_t gx[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t gsig[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     // last run
     int32_t n_a = 0, n_b = 0, n_c = 0, units_a = 0, units_b = 0, used_K = 0, used_ta = 0, used_tb = 0;
@@ -78,7 +78,6 @@ int ensure_streams(isf_batch* b) {
     CUDA_TRY(cudaGetDevice(&b->device), "cudaGetDevice");
     CUDA_TRY(cudaStreamCreateWithFlags(&b->sa, cudaStreamNonBlocking), "stream");
     CUDA_TRY(cudaStreamCreateWithFlags(&b->sb, cudaStreamNonBlocking), "stream");
-    CUDA_TRY(cudaStreamCreateWithFlags(&b->sc, cudaStreamNonBlocking), "stream");
     CUDA_TRY(cudaStreamCreateWithFlags(&b->sd, cudaStreamNonBlocking), "stream");
     CUDA_TRY(cudaStreamCreateWithFlags(&b->se, cudaStreamNonBlocking), "stream");
     CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "event");
@@ -91,6 +90,11 @@ int ensure_streams(isf_batch* b) {
     return ISF_OK;
 }
 
+void drop_graphs(isf_batch* b) {
+    for (cudaGraphExec_t& g : b->gx)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
 int ensure_gcapacity(isf_batch* b, size_t n) {
     if (n <= b->gcap) return ISF_OK;
     if (b->d_gdesc) cudaFree(b->d_gdesc);
@@ -98,7 +102,7 @@ int ensure_gcapacity(isf_batch* b, size_t n) {
     b->d_gdesc = nullptr;
     b->h_gdesc = nullptr;
     b->gcap = 0;
-    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    drop_graphs(b);
     CUDA_TRY(cudaMalloc(&b->d_gdesc, n * sizeof(SweepArgs)), "cudaMalloc batch queue");
     CUDA_TRY(cudaMallocHost(&b->h_gdesc, n * sizeof(SweepArgs)), "cudaMallocHost batch queue");
     b->gcap = n;
@@ -112,11 +116,36 @@ int ensure_capacity(isf_batch* b, size_t n) {
     b->d_desc = nullptr;
     b->h_desc = nullptr;
     b->cap = 0;
-    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    drop_graphs(b);
     CUDA_TRY(cudaMalloc(&b->d_desc, n * sizeof(ResArgs)), "cudaMalloc batch queue");
     CUDA_TRY(cudaMallocHost(&b->h_desc, n * sizeof(ResArgs)), "cudaMallocHost batch queue");
     b->cap = n;
     return ISF_OK;
+}
+
+// One queue kernel launched on its stream, or (graph mode) its single-kernel graph, captured from
+// that launch the first time and replayed after.  The kernels are launched, graph or not, in the
+// same host order, so they reach the GPU in a fixed order: the sibling kernel nodes of one graph
+// do not, and which persistent kernel the hardware places first decides how the SMs are shared.
+// Returns a cudaError_t value.
+template <class F>
+int launch_on(isf_batch* b, int cls, cudaStream_t st, F&& launch) {
+    if (!b->use_graph) return launch(st);
+    if (!b->gx[cls]) {
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+        if (ce != cudaSuccess) return (int)ce;
+        const int e = launch(st);
+        ce = cudaStreamEndCapture(st, &g);
+        if (e || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return e ? e : (int)ce;
+        }
+        ce = cudaGraphInstantiate(&b->gx[cls], g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) { b->gx[cls] = nullptr; return (int)ce; }
+    }
+    return (int)cudaGraphLaunch(b->gx[cls], st);
 }
 
 // The launch sequence: queue uploads, counters, fork, the persistent launches, join.
@@ -134,7 +163,9 @@ int enqueue(isf_batch* b, cudaStream_t s, int n_a, int n_b, int K, int ta, int t
         CUDA_TRY(cudaStreamWaitEvent(b->sd, b->ev_fork, 0), "fork");
         // once its own films are done, it takes the single-CTA resident films not yet started
         const StealQueue steal{b->d_desc, n_a, b->d_next + 0};
-        int e = launch_batch_global(b->d_gdesc, n_d, b->d_next + 2, kThreadsD, units_d, b->sd, steal);
+        int e = launch_on(b, 2, b->sd, [&](cudaStream_t st) {
+            return launch_batch_global(b->d_gdesc, n_d, b->d_next + 2, kThreadsD, units_d, st, steal);
+        });
         if (e) return cuda_fail((cudaError_t)e, "batch launch (one CTA per film, global memory)");
         CUDA_TRY(cudaEventRecord(b->ev_d, b->sd), "join");
         CUDA_TRY(cudaStreamWaitEvent(s, b->ev_d, 0), "join");
@@ -143,21 +174,27 @@ int enqueue(isf_batch* b, cudaStream_t s, int n_a, int n_b, int K, int ta, int t
         CUDA_TRY(cudaStreamWaitEvent(b->se, b->ev_fork, 0), "fork");
         // once its own films are done, it takes the resident cluster films not yet started
         const StealQueue steal{b->d_desc + n_a, n_b, b->d_next + 1};
-        int e = launch_batch_cluster_global(b->d_gdesc + n_d, n_e, b->d_next + 3, kKE, kThreadsE, units_e, b->se, steal);
+        int e = launch_on(b, 3, b->se, [&](cudaStream_t st) {
+            return launch_batch_cluster_global(b->d_gdesc + n_d, n_e, b->d_next + 3, kKE, kThreadsE, units_e, st, steal);
+        });
         if (e) return cuda_fail((cudaError_t)e, "batch launch (one cluster per film, global memory)");
         CUDA_TRY(cudaEventRecord(b->ev_e, b->se), "join");
         CUDA_TRY(cudaStreamWaitEvent(s, b->ev_e, 0), "join");
     }
     if (n_a) {
         CUDA_TRY(cudaStreamWaitEvent(b->sa, b->ev_fork, 0), "fork");
-        int e = launch_batch(b->d_desc, n_a, b->d_next, 1, ta, smem_a, units_a, b->sa);
+        int e = launch_on(b, 0, b->sa, [&](cudaStream_t st) {
+            return launch_batch(b->d_desc, n_a, b->d_next, 1, ta, smem_a, units_a, st);
+        });
         if (e) return cuda_fail((cudaError_t)e, "batch launch (single-CTA films)");
         CUDA_TRY(cudaEventRecord(b->ev_a, b->sa), "join");
         CUDA_TRY(cudaStreamWaitEvent(s, b->ev_a, 0), "join");
     }
     if (n_b) {
         CUDA_TRY(cudaStreamWaitEvent(b->sb, b->ev_fork, 0), "fork");
-        int e = launch_batch(b->d_desc + n_a, n_b, b->d_next + 1, K, tb, smem_b, units_b, b->sb);
+        int e = launch_on(b, 1, b->sb, [&](cudaStream_t st) {
+            return launch_batch(b->d_desc + n_a, n_b, b->d_next + 1, K, tb, smem_b, units_b, st);
+        });
         if (e) return cuda_fail((cudaError_t)e, "batch launch (cluster films)");
         CUDA_TRY(cudaEventRecord(b->ev_b, b->sb), "join");
         CUDA_TRY(cudaStreamWaitEvent(s, b->ev_b, 0), "join");
@@ -478,7 +515,8 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
     // per site, so work is a fair measure of time), the GPU is shared in proportion to their work
     // and both kernels are resident from the start.  The resident int8 classes run several times
     // faster per site than the global-memory ones, so there work is no measure of time; they keep
-    // whole-GPU grids.
+    // whole-GPU grids, and the order of the launches (global-memory kernels, then the single-CTA
+    // and the cluster kernel: the fastest order measured) is fixed, with or without graphs.
     if (A.empty() && B.empty()) share_units(A, B, D, E, &units_a, &units_b, &units_d, &units_e);
     units_a = std::min(units_a, n_a);
     units_b = std::min(units_b, n_b);
@@ -487,25 +525,12 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
     if (n_a || n_b || n_d || n_e) {
         const int64_t sig[12] = {n_a, n_b, K, ta, tb, (int64_t)smem_a << 32 | smem_b, units_a, units_b, n_d, units_d,
                                  n_e, units_e};
-        if (b->use_graph) {
-            if (!b->gexec || std::memcmp(sig, b->gsig, sizeof sig)) {
-                if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
-                cudaGraph_t g = nullptr;
-                CUDA_TRY(cudaStreamBeginCapture(b->sc, cudaStreamCaptureModeRelaxed), "begin capture");
-                rc = enqueue(b, b->sc, n_a, n_b, K, ta, tb, smem_a, smem_b, units_a, units_b, n_d, units_d, n_e, units_e);
-                cudaError_t ce = cudaStreamEndCapture(b->sc, &g);
-                if (rc) { if (g) cudaGraphDestroy(g); return rc; }
-                if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
-                ce = cudaGraphInstantiate(&b->gexec, g, 0);
-                cudaGraphDestroy(g);
-                if (ce != cudaSuccess) { b->gexec = nullptr; return cuda_fail(ce, "graph instantiate"); }
-                std::memcpy(b->gsig, sig, sizeof sig);
-            }
-            CUDA_TRY(cudaGraphLaunch(b->gexec, s), "graph launch");
-        } else {
-            rc = enqueue(b, s, n_a, n_b, K, ta, tb, smem_a, smem_b, units_a, units_b, n_d, units_d, n_e, units_e);
-            if (rc) return rc;
+        if (b->use_graph && std::memcmp(sig, b->gsig, sizeof sig)) {
+            drop_graphs(b);
+            std::memcpy(b->gsig, sig, sizeof sig);
         }
+        rc = enqueue(b, s, n_a, n_b, K, ta, tb, smem_a, smem_b, units_a, units_b, n_d, units_d, n_e, units_e);
+        if (rc) return rc;
         CUDA_TRY(cudaEventRecord(b->ev_done, s), "batch done");
         b->pending = true;
     }
@@ -559,10 +584,9 @@ void isf_batch_destroy(isf_batch* b) {
     if (b->sa) {
         cudaSetDevice(b->device);
         if (b->pending) cudaEventSynchronize(b->ev_done);
-        if (b->gexec) cudaGraphExecDestroy(b->gexec);
+        drop_graphs(b);
         cudaStreamDestroy(b->sa);
         cudaStreamDestroy(b->sb);
-        cudaStreamDestroy(b->sc);
         cudaStreamDestroy(b->sd);
         cudaStreamDestroy(b->se);
         cudaEventDestroy(b->ev_fork);

@@ -313,7 +313,7 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
         }
         fold_t = -1;
     };
-    stage_table<false>(s.tables, k, tab, gate);
+    stage_table<false, !PX>(s.tables, k, tab, gate);
     for (long long t = 0; t < s.nsweeps; ++t) {
         if (pos == s.step_total[k]) {
             ++k;
@@ -321,11 +321,12 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
             // with the split barrier a thread gets here while others may still read the old
             // table in the last pass: everyone first
             if (SPLIT) __syncthreads();
-            stage_table<false>(s.tables, k, tab, gate);
+            stage_table<false, !PX>(s.tables, k, tab, gate);
             if (folder) { k_eq = s.step_eq[k]; k_tot = s.step_total[k]; }
         }
         const unsigned long long sweep = (unsigned long long)(s.sweep0 + t + 1);
         const uint32_t gthr = gate[0];
+        const bool neg = !PX && (gate[1] & kFlagNoNever);    // table staged negated (carry form)
         int dM = 0, dB = 0;
         for (int c = 0; c < 4; ++c) {
             if (SPLIT && pending) {
@@ -378,14 +379,14 @@ __device__ __forceinline__ void run_film(const ResArgs& a, uint8_t* sm) {
                     const uint4 a4 = neighbour_sum16_from(nv, ne, sgn);
                     Aw[0] = a4.x; Aw[1] = a4.y; Aw[2] = a4.z; Aw[3] = a4.w;
                     any = s.use_gate
-                        ? decide16<true, PX, 4, true>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB, u)
-                        : decide16<false, PX, 4, true>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB, u);
+                        ? decide16<true, PX, 4, true>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB, u, neg)
+                        : decide16<false, PX, 4, true>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB, u, neg);
                 } else {
                     const uint2 a2 = neighbour_sum8_sc<CLUSTER>(nbp, sgn);
                     Aw[0] = a2.x; Aw[1] = a2.y;
                     any = s.use_gate
-                        ? decide16<true, PX, NW>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB)
-                        : decide16<false, PX, NW>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB);
+                        ? decide16<true, PX, NW>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB, nullptr, neg)
+                        : decide16<false, PX, NW>(Sw, Aw, q0, sweep, tab, gthr, f.key0, f.key1, W * ck, Ch, fm, dM, dB, nullptr, neg);
                 }
                 if (any) {
                     if (!PX) {

@@ -28,20 +28,20 @@ constexpr int kBlock = 512;      // largest CTA of the global kernel (<= 128 reg
 template <bool GATE>
 __device__ __forceinline__ void chunk_int8_at(const DevFilm& f, int c, int zp, int64_t base, uint32_t q0,
                                               unsigned long long sweep, const uint32_t* tab, uint32_t gthr, int& dM,
-                                              int& dB) {
+                                              int& dB, bool neg) {
     const NbrClass& nc = f.nb[c][zp];
     uint8_t* own = f.s8 + base;
     const uint8_t* nbp[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) nbp[k] = own + nc.off[k];
-    update_chunk16<GATE>(own, nbp, nc.sgn, q0, sweep, tab, gthr, f.key0, f.key1, 0, f.Ch, dM, dB);
+    update_chunk16<GATE>(own, nbp, nc.sgn, q0, sweep, tab, gthr, f.key0, f.key1, 0, f.Ch, dM, dB, neg);
 }
 template <bool GATE>
 __device__ __forceinline__ void chunk_int8(const DevFilm& f, int c, int z, int j, int ck,
                                            unsigned long long sweep, const uint32_t* tab,
-                                           uint32_t gthr, int& dM, int& dB) {
+                                           uint32_t gthr, int& dM, int& dB, bool neg) {
     chunk_int8_at<GATE>(f, c, z & 1, addr8(f, c, z, j, 16 * ck), block_counter(f, c, z, j, 16 * ck), sweep, tab, gthr,
-                        dM, dB);
+                        dM, dB, neg);
 }
 
 // ---- int8 layout, any boundary (periodic wraps): one thread per 4-site Philox block --------
@@ -188,13 +188,15 @@ __device__ __forceinline__ void colour_pass(const DevFilm& f, int c, unsigned lo
         const int n = f.nitems[c];
         for (int it = first_item(G, cta); it < n; it += stride) {
             const uint2 pq = ent[it];
-            chunk_int8_at<GATE>(f, c, (int)(pq.x >> 31), (int64_t)(pq.x & 0x7FFFFFFFu), pq.y, sweep, tab, gthr, dM, dB);
+            chunk_int8_at<GATE>(f, c, (int)(pq.x >> 31), (int64_t)(pq.x & 0x7FFFFFFFu), pq.y, sweep, tab, gthr, dM, dB,
+                                (sflags & kFlagNoNever) != 0u);
         }
         return;
     }
     const int j0 = f.slab ? f.jlo : 0;
     for (int it = first_item(G, cta); it < items; it += stride, w.next()) {
-        if (MODE == MODE_INT8) chunk_int8<GATE>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB);
+        if (MODE == MODE_INT8) chunk_int8<GATE>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB,
+                                                (sflags & kFlagNoNever) != 0u);
         else if (MODE == MODE_GENERIC) block_generic<GATE>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, dM, dB);
         else word_packed<GATE, false>(f, c, w.z, j0 + w.jr, w.ck, sweep, tab, gthr, sflags, dM, dB, pre, false);
     }
@@ -235,12 +237,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, unsigned G, unsig
         k_eq = a.step_eq[k];
         k_tot = a.step_total[k];
     }
-    stage_table<MODE == MODE_PACKED>(a.tables, k, tab, gate_s);
+    stage_table<MODE == MODE_PACKED, MODE == MODE_INT8>(a.tables, k, tab, gate_s);
     for (long long t = 0; t < a.nsweeps; ++t) {
         if (pos == a.step_total[k]) {
             ++k;
             pos = 0;
-            stage_table<MODE == MODE_PACKED>(a.tables, k, tab, gate_s);
+            stage_table<MODE == MODE_PACKED, MODE == MODE_INT8>(a.tables, k, tab, gate_s);
             if (folder) { k_eq = a.step_eq[k]; k_tot = a.step_total[k]; }
         }
         const unsigned long long sweep = (unsigned long long)(a.sweep0 + t + 1);

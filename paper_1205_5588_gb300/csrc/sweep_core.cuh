@@ -15,20 +15,25 @@ namespace isf {
 //   packed : (up << 5) | (n + 12); the packed kernel masks vacant sites out of the flips itself.
 //            Entries 64..127 hold the same thresholds negated, 2^32 - thr ("always": 0), for
 //            the carry form of the comparison (kFlagNoNever).
-template <bool PACKED>
+// INT8_NEG (int8 kernels that take the carry form): on steps with kFlagNoNever the int8 entries
+// are negated the same way (vacancies stay 0; the kernel masks them out of the flips).
+__device__ __forceinline__ uint32_t neg_threshold(uint32_t thr) { return thr == kAlways ? 0u : 0u - thr; }
+template <bool PACKED, bool INT8_NEG = false>
 __device__ __forceinline__ void stage_table(const uint32_t* tables, int k, uint32_t* tab, uint32_t* gate) {
     const uint32_t* src = tables + (size_t)k * kTableStride;
+    const bool neg8 = INT8_NEG && (src[kFlagSlot] & kFlagNoNever);
     for (int t = threadIdx.x; t < 128; t += blockDim.x) {
         uint32_t v = 0;
         const int X = t & 31;
         if (X <= 24) {
             if (PACKED) {
                 const uint32_t thr = src[X * 2 + ((t >> 5) & 1)];
-                v = t < 64 ? thr : (thr == kAlways ? 0u : 0u - thr);
+                v = t < 64 ? thr : neg_threshold(thr);
             } else {
                 const int sb = t >> 5;
                 if (sb == 0) v = src[X * 2 + 0];
                 else if (sb == 2) v = src[X * 2 + 1];
+                if (neg8 && (sb == 0 || sb == 2)) v = neg_threshold(v);
             }
         }
         tab[t] = v;
@@ -161,16 +166,21 @@ __device__ __forceinline__ void philox10_sc(uint32_t q0, uint32_t stream, const 
 // sum of the 12 neighbour bytes, n + 12.  All 16 table lookups first; then, if any lane's
 // threshold is neither 0 nor "always", the chunk's NW Philox blocks at once (a real word
 // decides a 0 / "always" lane exactly as no word does, so computing it never changes a
-// result).  The flips come back as a byte mask per word (0 <-> 2 is XOR 2); dM and dB from
-// popcounts of that mask and a multiply-add of the masked neighbour sums.  PX: lanes past the
+// result).  The flips come back as a byte mask per word (0 <-> 2 is XOR 2).  PX: lanes past the
 // row end (column Ch on) are masked.  Returns the OR of the four masks.
 // U_IN: the chunk's NW Philox blocks are already in u_in (drawn before the neighbour sum was
 // available, to fill the wait for its loads); else they are drawn here only if a lane needs one.
+// neg (steps with kFlagNoNever, tables staged with INT8_NEG; not with PX): the table holds
+// 2^32 - thr and each lane's rejection is the carry of u + that (shift_in_reject), vacant lanes
+// masked out afterwards.
+// dM, dB: a signed byte per lane (+1 for a flip from down, -1 from up) dotted with all-ones and
+// with Aw gives #down - #up flips and the same sum of n + 12; dM = 2 (#down - #up),
+// dB = 2 [sum over down-flips of n - sum over up-flips of n].
 template <bool GATE, bool PX, int NW = 4, bool U_IN = false>
 __device__ __forceinline__ uint32_t decide16(const uint32_t Sw[NW], const uint32_t Aw[NW], uint32_t q0,
                                              unsigned long long sweep, const uint32_t* tab, uint32_t gthr,
                                              uint32_t key0, uint32_t key1, int i0, int Ch, uint32_t fm[NW],
-                                             int& dM, int& dB, const uint4* u_in = nullptr) {
+                                             int& dM, int& dB, const uint4* u_in = nullptr, bool neg = false) {
     uint32_t thr[4 * NW];
     bool need = false;
 #pragma unroll
@@ -178,10 +188,11 @@ __device__ __forceinline__ uint32_t decide16(const uint32_t Sw[NW], const uint32
         const uint32_t iw = (Sw[v] << 5) + Aw[v];
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            uint32_t t = tab[(iw >> (8 * b)) & 0xFFu];
+            uint32_t t = tab[__byte_perm(iw, 0u, 0x4440u + b)];
             if (PX && i0 + 4 * v + b >= Ch) t = 0u;
             thr[4 * v + b] = t;
-            if (!U_IN) need |= needs_word(t);
+            // negated entries: 0 is "always" (or a vacancy), and no lane is "never"
+            if (!U_IN) need |= neg ? t != 0u : needs_word(t);
         }
     }
     uint4 u[NW];
@@ -194,28 +205,41 @@ __device__ __forceinline__ uint32_t decide16(const uint32_t Sw[NW], const uint32
         if (need) philox10_xn<NW>(q0, (uint32_t)sweep, (uint32_t)(sweep >> 32), 0u, key0, key1, u);
     }
     uint32_t any = 0;
+    int dn = 0, dx = 0;     // #down - #up flips; sum of n + 12 over down-flips minus over up-flips
 #pragma unroll
     for (int v = 0; v < NW; ++v) {
-        uint32_t m = (metropolis_accept(u[v].x, thr[4 * v + 0]) ? 0x00000002u : 0u) |
-                     (metropolis_accept(u[v].y, thr[4 * v + 1]) ? 0x00000200u : 0u) |
-                     (metropolis_accept(u[v].z, thr[4 * v + 2]) ? 0x00020000u : 0u) |
-                     (metropolis_accept(u[v].w, thr[4 * v + 3]) ? 0x02000000u : 0u);
+        uint32_t m;
+        if (!PX && neg) {
+            // rejection bits, lane 3 shifted in first (bit b = lane b); bit b -> bit 8b + 1 by one
+            // multiply (the partial products do not overlap); accepted lanes of occupied sites
+            // (stored byte 1 has bit 1 set once shifted) become bytes 2
+            uint32_t R = shift_in_reject(0u, u[v].w, thr[4 * v + 3]);
+            R = shift_in_reject(R, u[v].z, thr[4 * v + 2]);
+            R = shift_in_reject(R, u[v].y, thr[4 * v + 1]);
+            R = shift_in_reject(R, u[v].x, thr[4 * v + 0]);
+            m = ~(R * 0x00408102u) & ~(Sw[v] << 1) & 0x02020202u;
+        } else {
+            m = (metropolis_accept(u[v].x, thr[4 * v + 0]) ? 0x00000002u : 0u) |
+                (metropolis_accept(u[v].y, thr[4 * v + 1]) ? 0x00000200u : 0u) |
+                (metropolis_accept(u[v].z, thr[4 * v + 2]) ? 0x00020000u : 0u) |
+                (metropolis_accept(u[v].w, thr[4 * v + 3]) ? 0x02000000u : 0u);
+        }
         if (GATE && m) {
             uint32_t lanes = ((m >> 1) & 1u) | ((m >> 8) & 2u) | ((m >> 15) & 4u) | ((m >> 22) & 8u);
             lanes = gate_block(lanes, gthr, q0 + v, sweep, key0, key1);
             m = ((lanes & 1u) << 1) | ((lanes & 2u) << 8) | ((lanes & 4u) << 15) | ((lanes & 8u) << 22);
         }
-        // flipped from up (byte 2) and from down (byte 0); dM = -2 (n_up - n_down),
-        // dB = -2 [sum over up-flips of n - sum over down-flips of n], n = byte of Aw - 12
-        const uint32_t up = m & Sw[v], dn = m ^ up;
-        const int nu = __popc(up), nd = __popc(dn);
-        const uint32_t xu = ((Aw[v] & ((up >> 1) * 0xFFu)) * 0x01010101u) >> 24;
-        const uint32_t xd = ((Aw[v] & ((dn >> 1) * 0xFFu)) * 0x01010101u) >> 24;
-        dM += 2 * (nd - nu);
-        dB += 2 * (((int)xd - 12 * nd) - ((int)xu - 12 * nu));
+        // byte of sg: 1 where a down spin flips, 0xFF (-1) where an up spin flips (bytes of up are
+        // 0 or 2, so up * 0x7F stays within each byte)
+        const uint32_t up = m & Sw[v];
+        const uint32_t sg = (m >> 1) ^ (up * 0x7Fu);
+        dn = __dp4a((int)sg, 0x01010101, dn);
+        dx = __dp4a((int)sg, (int)Aw[v], dx);
         fm[v] = m;
         any |= m;
     }
+    dM += 2 * dn;
+    dB += 2 * dx - 24 * dn;
     return any;
 }
 
@@ -224,7 +248,7 @@ template <bool GATE>
 __device__ __forceinline__ void update_chunk16(uint8_t* own, const uint8_t* const* nb, int sgn, uint32_t q0,
                                                unsigned long long sweep, const uint32_t* tab, uint32_t gthr,
                                                uint32_t key0, uint32_t key1, int i0, int Ch,
-                                               int& dM, int& dB) {
+                                               int& dM, int& dB, bool neg) {
     const uint4 S = ld16(own);
     // the 15 neighbour loads first, then the chunk's four Philox blocks while they are in flight
     uint4 v[12];
@@ -252,7 +276,7 @@ __device__ __forceinline__ void update_chunk16(uint8_t* own, const uint8_t* cons
     const uint32_t Sw[4] = {S.x, S.y, S.z, S.w};
     const uint32_t Aw[4] = {acc.x, acc.y, acc.z, acc.w};
     uint32_t fm[4];
-    if (decide16<GATE, false, 4, true>(Sw, Aw, q0, sweep, tab, gthr, key0, key1, i0, Ch, fm, dM, dB, u))
+    if (decide16<GATE, false, 4, true>(Sw, Aw, q0, sweep, tab, gthr, key0, key1, i0, Ch, fm, dM, dB, u, neg))
         *reinterpret_cast<uint4*>(own) = make_uint4(Sw[0] ^ fm[0], Sw[1] ^ fm[1], Sw[2] ^ fm[2], Sw[3] ^ fm[3]);
 }
 
