@@ -183,6 +183,11 @@ def roofline(attempts_per_launch, t_launch, peaks, sms, sm_max_mhz, kernel, shap
         "frac_of_dispatch_by_instructions": (inst_per_attempt * rate / derived if inst_per_attempt and derived
                                              else None),
     }
+    # a film held by one cluster runs on that cluster's SMs only: its share of their ceiling
+    used = shape.get("ctas") if shape.get("path") == "resident" else sms
+    if used and used < sms:
+        ceil["sms_in_use"] = used
+        ceil["frac_of_arithmetic_ceiling_of_sms_in_use"] = rate / (peaks["attempts_per_s_arithmetic"] * used / sms)
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": kernel, "launch": shape, "ops_per_attempt": OPS_PER_ATTEMPT,
             "peak_from": "measured in this run on this GPU: 40 x the attempts/s of the per-attempt integer "
@@ -259,11 +264,11 @@ def e2e_film(I, spec, seed, steps, stream):
 # hash to the recorded value (None: not captured for the current sources).
 NCU_RECORDS = {
     "fractal256": {"sources": ["kernels_resident.cu", "sweep_core.cuh", "device_common.cuh"],
-                   "sources_sha256": "d574bb97950cbc05a389bc6df92c2722c877c9c503b0b4e9abaad1b845f40836",
-                   "bytes_per_launch": 1080064.0, "inst_per_attempt": None},
+                   "sources_sha256": "7eb0ceb4c157983f4913e350a6e95a2ee2a8151005e81e97642390bfe346bf67",
+                   "bytes_per_launch": 1785344.0 + 0.0, "inst_per_attempt": None},
     "fractal2048": {"sources": ["kernels_words.cu", "sweep_core.cuh", "device_common.cuh", "grid_sync.cuh"],
-                    "sources_sha256": "398dba028473de84ae47f72fcc5ebddbd022b1aef160b04808563df77a274f1a",
-                    "bytes_per_launch": 20967936.0 + 623104.0, "inst_per_attempt": 25.85},
+                    "sources_sha256": "03fa43aa3b5ac631b510b1dab797589a2e3e49d1af96b5f1c0b3c544ee1b47ef",
+                    "bytes_per_launch": 21731584.0 + 781824.0, "inst_per_attempt": 25.86},
 }
 
 
@@ -364,6 +369,10 @@ def run_impl(args):
         bp = measure_batched(I, n_films=args.batch_films, sweeps_per_step=args.batch_sweeps, ranks=ranks,
                              plain=ranks.world == 1, packed=True)
         if rank == 0:
+            # the whole GPU's share of the per-attempt arithmetic ceiling measured above (the packed
+            # word's form; an int8 attempt costs more instructions)
+            for leg in (b, bp):
+                leg["frac_of_arithmetic_ceiling"] = leg["value"] / (ws * peaks["attempts_per_s_arithmetic"])
             line["batched"] = b
             line["batched_packed"] = bp
     if rank == 0 and not args.no_served:
@@ -562,7 +571,7 @@ def run_reference(args):
 
 def profile_case(args):
     """Small case for ncu captures of the sweep kernel: the workload's film, one launch of
-    --profile-sweeps sweeps at the first schedule step."""
+    --profile-sweeps sweeps at schedule step --profile-step (default the first)."""
     import torch
     torch.cuda.set_device(0)
     from paper_1205_5588_gb300 import build as B
@@ -576,7 +585,8 @@ def profile_case(args):
         lat.set_path(args.path)
     if args.ctas or args.threads:
         lat.set_launch(args.ctas, args.threads)
-    lat.set_schedule(s["T"][:1], s["h"][:1], [0], [args.profile_sweeps], J=spec["J"])
+    k = args.profile_step
+    lat.set_schedule(s["T"][k:k + 1], s["h"][k:k + 1], [0], [args.profile_sweeps], J=spec["J"])
     lat.run(-1)
     print("profile case done, M_last =", lat.observables()[0]["M_last"], "launch", lat.launch_info())
     lat.close()
@@ -632,6 +642,7 @@ def main():
     ap.add_argument("--ref-sweeps", type=int, default=0)
     ap.add_argument("--schedule-steps", type=int, default=0,
                     help="time only the first N steps of the workload's schedule (quick kernel timings)")
+    ap.add_argument("--profile-step", type=int, default=0, help="schedule step of the --profile-sweeps case")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling case: one launch of this many sweeps at the first schedule step, no JSON")
     ap.add_argument("--probe", action="store_true", help="print the integer-issue ceilings only")

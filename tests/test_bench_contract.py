@@ -50,3 +50,10 @@ def test_roofline_bookkeeping():
     assert abs(c["frac_of_philox_ceiling"] - 0.5e12 / 4e12) < 1e-12
     assert abs(c["frac_of_arithmetic_ceiling"] - 0.25) < 1e-12
     assert abs(c["frac_of_lop3_issue_by_instructions"] - 27.0 * 0.5e12 / 40e12) < 1e-12
+    # a film on one 16-CTA cluster is also set against the ceiling of the 16 SMs it can use
+    r = bench.roofline(1e12, 2.0, peaks, 152, 2070.0, "k", {"path": "resident", "ctas": 16}, None, None)
+    c = r["ceilings"]
+    assert c["sms_in_use"] == 16
+    assert abs(c["frac_of_arithmetic_ceiling_of_sms_in_use"] - 0.25 * 152 / 16) < 1e-12
+    assert "sms_in_use" not in bench.roofline(1e12, 2.0, peaks, 152, 2070.0, "k", {"path": "global", "ctas": 152},
+                                              None, None)["ceilings"]
