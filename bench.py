@@ -379,6 +379,11 @@ def run_impl(args):
         line["served"] = measure_served(I, rate=args.serve_rate, duration=args.serve_seconds)
         line["served_sustainable"] = measure_served(I, rate=args.serve_rate_sustainable,
                                                     duration=args.serve_seconds_sustainable)
+        if args.serve_rate_over > 0:
+            # twice the stated stream: offered load above what the GPU serves, so the achieved
+            # rate is the server's capacity and the latencies include the backlog
+            line["served_over_capacity"] = measure_served(I, rate=args.serve_rate_over,
+                                                          duration=args.serve_seconds_over)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, budget_s=args.cpu_seconds)
     if rank == 0:
@@ -639,6 +644,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate-sustainable", type=float, default=100.0)
     ap.add_argument("--serve-seconds-sustainable", type=float, default=20.0)
+    ap.add_argument("--serve-rate-over", type=float, default=400.0, help="0 = no over-capacity serving leg")
+    ap.add_argument("--serve-seconds-over", type=float, default=20.0)
     ap.add_argument("--ref-sweeps", type=int, default=0)
     ap.add_argument("--schedule-steps", type=int, default=0,
                     help="time only the first N steps of the workload's schedule (quick kernel timings)")
