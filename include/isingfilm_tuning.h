@@ -89,6 +89,11 @@ int isf_launch_info(isf_lattice* lat, int32_t* path, int32_t* ctas, int32_t* thr
  * packed global; 0 before any launch).  No device work. */
 int isf_launch_item_sites(isf_lattice* lat, int32_t* sites);
 
+/* Films of the last isf_batch_run_sweeps that a global-memory queue kernel took from a resident
+ * queue of its size class once its own queue was empty: out2[0] from the single-CTA resident
+ * queue, out2[1] from the cluster resident queue.  Waits for the run. */
+int isf_batch_taken(isf_batch* batch, int32_t* out2);
+
 /* Device Philox4x32-10 blocks for checking the generator: for b in [0, nblocks), the block
  * with key (seed_lo, seed_hi) and counter (q0 + b, sweep_lo, sweep_hi, stream) goes to
  * host_out[4b .. 4b+3].  Synchronous. */

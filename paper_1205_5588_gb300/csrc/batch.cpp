@@ -34,7 +34,7 @@ struct isf_batch {
     // device-side queues: class A entries, then class B entries; class D entries
     ResArgs* d_desc = nullptr;
     size_t cap = 0;
-    unsigned* d_next = nullptr;  // queue counters of A, B, D, E
+    unsigned* d_next = nullptr;  // queue counters of A, B, D, E; films D and E took from A and B
     ResArgs* h_desc = nullptr;   // pinned staging
     SweepArgs* d_gdesc = nullptr;   // class D entries, then class E entries
     SweepArgs* h_gdesc = nullptr;
@@ -86,7 +86,8 @@ int ensure_streams(isf_batch* b) {
     CUDA_TRY(cudaEventCreateWithFlags(&b->ev_d, cudaEventDisableTiming), "event");
     CUDA_TRY(cudaEventCreateWithFlags(&b->ev_e, cudaEventDisableTiming), "event");
     CUDA_TRY(cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming), "event");
-    CUDA_TRY(cudaMalloc(&b->d_next, 4 * sizeof(unsigned)), "cudaMalloc");
+    CUDA_TRY(cudaMalloc(&b->d_next, 6 * sizeof(unsigned)), "cudaMalloc");
+    CUDA_TRY(cudaMemset(b->d_next, 0, 6 * sizeof(unsigned)), "cudaMemset");
     return ISF_OK;
 }
 
@@ -157,12 +158,12 @@ int enqueue(isf_batch* b, cudaStream_t s, int n_a, int n_b, int K, int ta, int t
     if (n_d + n_e)
         CUDA_TRY(cudaMemcpyAsync(b->d_gdesc, b->h_gdesc, (size_t)(n_d + n_e) * sizeof(SweepArgs),
                                  cudaMemcpyHostToDevice, s), "upload queue");
-    CUDA_TRY(cudaMemsetAsync(b->d_next, 0, 4 * sizeof(unsigned), s), "reset queue");
+    CUDA_TRY(cudaMemsetAsync(b->d_next, 0, 6 * sizeof(unsigned), s), "reset queue");
     CUDA_TRY(cudaEventRecord(b->ev_fork, s), "fork");
     if (n_d) {
         CUDA_TRY(cudaStreamWaitEvent(b->sd, b->ev_fork, 0), "fork");
         // once its own films are done, it takes the single-CTA resident films not yet started
-        const StealQueue steal{b->d_desc, n_a, b->d_next + 0};
+        const StealQueue steal{b->d_desc, n_a, b->d_next + 0, b->d_next + 4};
         int e = launch_on(b, 2, b->sd, [&](cudaStream_t st) {
             return launch_batch_global(b->d_gdesc, n_d, b->d_next + 2, kThreadsD, units_d, st, steal);
         });
@@ -173,7 +174,7 @@ int enqueue(isf_batch* b, cudaStream_t s, int n_a, int n_b, int K, int ta, int t
     if (n_e) {
         CUDA_TRY(cudaStreamWaitEvent(b->se, b->ev_fork, 0), "fork");
         // once its own films are done, it takes the resident cluster films not yet started
-        const StealQueue steal{b->d_desc + n_a, n_b, b->d_next + 1};
+        const StealQueue steal{b->d_desc + n_a, n_b, b->d_next + 1, b->d_next + 5};
         int e = launch_on(b, 3, b->se, [&](cudaStream_t st) {
             return launch_batch_cluster_global(b->d_gdesc + n_d, n_e, b->d_next + 3, kKE, kThreadsE, units_e, st, steal);
         });
@@ -576,6 +577,19 @@ int isf_batch_info(isf_batch* b, int32_t* out12) {
     const int32_t v[12] = {b->n_a, b->n_b, b->n_c, b->units_a, b->units_b, b->used_K, b->used_ta, b->used_tb,
                            b->n_d, b->units_d, b->n_e, b->units_e};
     std::memcpy(out12, v, sizeof v);
+    return ISF_OK;
+}
+
+int isf_batch_taken(isf_batch* b, int32_t* out2) {
+    if (!b || !out2) return fail(ISF_ERR_ARG, "bad arguments");
+    unsigned v[2] = {0u, 0u};
+    if (b->d_next) {
+        CUDA_TRY(cudaSetDevice(b->device), "cudaSetDevice");
+        if (b->pending) CUDA_TRY(cudaEventSynchronize(b->ev_done), "batch sync");
+        CUDA_TRY(cudaMemcpy(v, b->d_next + 4, sizeof v, cudaMemcpyDeviceToHost), "read counters");
+    }
+    out2[0] = (int32_t)v[0];
+    out2[1] = (int32_t)v[1];
     return ISF_OK;
 }
 

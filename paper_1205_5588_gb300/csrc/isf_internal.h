@@ -264,6 +264,7 @@ struct StealQueue {
     const ResArgs* films;
     int32_t n;
     unsigned* next;
+    unsigned* taken;    // films the global-memory kernel took from this queue
 };
 int launch_batch_global(const SweepArgs* films, int n, unsigned* next, int threads, int units, void* stream,
                         StealQueue steal);

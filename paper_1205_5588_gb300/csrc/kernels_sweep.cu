@@ -313,7 +313,10 @@ __device__ __forceinline__ int take_film(unsigned* next, int nfilms, const Steal
     }
     if (steal.n > 0) {
         const int idx = (int)atomicAdd(steal.next, 1u);
-        if (idx < steal.n) return -2 - idx;
+        if (idx < steal.n) {
+            atomicAdd(steal.taken, 1u);
+            return -2 - idx;
+        }
     }
     return -1;
 }

@@ -101,6 +101,7 @@ def _declare(lib):
         "isf_batch_tune": (C.c_int, [vp, vp]),
         "isf_batch_run": (C.c_int, [vp, vp]),
         "isf_batch_info": (C.c_int, [vp, i32p]),
+        "isf_batch_taken": (C.c_int, [vp, i32p]),
         "isf_batch_destroy": (None, [vp]),
         "isf_batch_run_sweeps": (C.c_int, [vp, C.c_int64, vp]),
         "isf_server_create": (C.c_int, [C.c_size_t, C.c_int64, C.POINTER(vp)]),
@@ -460,6 +461,13 @@ class Batch:
                 "threads_single", "threads_cluster", "global_cta_films", "global_ctas",
                 "global_cluster_films", "global_clusters")
         return dict(zip(keys, list(v)))
+
+    def taken(self) -> dict:
+        """Films of the last run that a global-memory queue kernel took from the single-CTA and
+        from the cluster resident queue (waits for the run)."""
+        v = (C.c_int32 * 2)()
+        _check(lib.isf_batch_taken(self._h, v), "batch_taken")
+        return {"single_cta": int(v[0]), "cluster": int(v[1])}
 
     def close(self):
         if getattr(self, "_h", None):

@@ -92,6 +92,37 @@ def test_batch_matches_oracle_and_solo(I, graph, tune):
         lat.close()
 
 
+def test_global_kernel_takes_waiting_resident_films(I):
+    """More single-CTA resident films than the resident kernel holds at once, beside one tiny
+    global-memory film: the one-CTA global-memory kernel, done with its own film, takes resident
+    films that have not started and runs them in global memory; every film ends exactly where it
+    ends alone."""
+    rng = np.random.Generator(np.random.PCG64(78))
+    films = []
+    for i in range(800):
+        H = W.fractal_heights(16, 16, 0.7, 1, 2, seed=3000 + i)
+        sc = W.schedule(rng.uniform(1.0, 8.0, size=2), rng.uniform(-2.0, 2.0, size=2), [0, 0], [20, 20])
+        films.append({"heights": H, "layers": 2, "seed": 5000 + i, "init": "random", "schedule": sc})
+    films.append({"heights": np.full((16, 16), 2, dtype=np.uint8), "layers": 2, "seed": 77, "init": "random",
+                  "packed": True, "schedule": W.schedule([3.0], [0.0], [0], [1])})
+    lats = [make(I, f) for f in films]
+    b = I.Batch(lats)
+    b.run()
+    info, taken = b.info(), b.taken()
+    assert info["single_cta_films"] == 800 and info["global_cta_films"] == 1, info
+    assert info["ctas"] < 800, info          # films wait for a resident CTA
+    assert taken["single_cta"] > 0 and taken["cluster"] == 0, taken
+    for f, lat in zip(films, lats):
+        solo = make(I, f)
+        solo.run(-1)
+        assert_records_equal(lat.observables(), solo.observables())
+        assert np.array_equal(lat.spins(), solo.spins())
+        solo.close()
+    b.close()
+    for lat in lats:
+        lat.close()
+
+
 def test_batch_of_one_and_empty(I):
     f = mixed_films()[0]
     lat = make(I, f)
