@@ -597,6 +597,41 @@ def profile_case(args):
     lat.close()
 
 
+def sizes_case(args):
+    """The bit-packed film of the headline's kind (fractal map, Hurst 0.8, layers 2..6, all up) at
+    several sizes, on the global-memory word kernel and on the row-slab kernel: microseconds per
+    sweep over the loop's first 3 field steps (200 sweeps each), best of 3 after a warm-up, CUDA
+    events; one JSON line per film and path."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1205_5588_gb300 import build as B
+    B.build()
+    from paper_1205_5588_gb300 import isingfilm as I
+    from paper_1205_5588_gb300 import workloads as W
+    spec = W.fractal2048_hysteresis()
+    s = spec["schedule"]
+    T, h, eq, me = (s[k][:3] for k in ("T", "h", "eq", "meas"))
+    sweeps = int(eq.sum() + me.sum())
+    stream = torch.cuda.current_stream()
+    for n in [int(x) for x in args.sizes.split(",")]:
+        H = W.fractal_heights(n, n, 0.8, 2, 6, seed=3)
+        for path in ("global", "slabs"):
+            lat = I.Lattice(H, 6, packed=True, seed=1, init="up", stream=stream)
+            lat.set_path(path)
+            ts = []
+            for rep in range(4):
+                lat.set_schedule(T, h, eq, me, J=spec["J"])
+                a, b = events()
+                a.record(stream)
+                lat.run(-1, stream=stream)
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b) / 1e3)
+            print(json.dumps({"size": n, "path": path, "us_per_sweep": min(ts[1:]) / sweeps * 1e6,
+                              "occupied_sites": lat.info()["n_occ"], "launch": lat.launch_info()}), flush=True)
+            lat.close()
+
+
 def probe_case(args):
     """The integer-issue probes alone: the ceilings as the bench measures them, or (with
     --probe-iters) one launch of each probe of that many iterations, for ncu captures."""
@@ -652,6 +687,7 @@ def main():
     ap.add_argument("--profile-step", type=int, default=0, help="schedule step of the --profile-sweeps case")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling case: one launch of this many sweeps at the first schedule step, no JSON")
+    ap.add_argument("--sizes", default="", help="comma-separated film sides: time the packed film on both paths")
     ap.add_argument("--probe", action="store_true", help="print the integer-issue ceilings only")
     ap.add_argument("--probe-iters", type=int, default=0,
                     help="with --probe: one launch of each probe of this many iterations per thread")
@@ -659,6 +695,9 @@ def main():
     args.e2e_steps = max(1, args.e2e_steps)
     if args.profile_sweeps:
         profile_case(args)
+        return
+    if args.sizes:
+        sizes_case(args)
         return
     if args.probe or args.probe_iters:
         probe_case(args)

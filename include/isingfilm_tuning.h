@@ -29,8 +29,8 @@ extern "C" {
  *     its two neighbours only (the same row decomposition, over the whole GPU); launches of at
  *     most 2048 sweeps, each followed by a one-thread fold of the per-sweep M, B series;
  *   ISF_PATH_AUTO (default): int8 films resident when the film fits, else global; packed films
- *     slabs when a colour pass has more than 512 and at most (SMs x 512) / 5 occupied words
- *     (films of roughly 100^2 to 650^2 sites per layer), else global.
+ *     slabs when a colour pass has more than 512 and at most 4096 occupied words (films of
+ *     roughly 150^2 to 350^2 sites per layer), else global.
  * Errors: ISF_ERR_ARG (unknown path; resident for a packed film; slabs for an int8 film, a slab
  * film or a packed film whose word lists could not be built). */
 enum { ISF_PATH_AUTO = 0, ISF_PATH_GLOBAL = 1, ISF_PATH_RESIDENT = 2, ISF_PATH_SLABS = 3 };

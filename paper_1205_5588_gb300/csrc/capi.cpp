@@ -583,20 +583,15 @@ static int run_slabs(isf_lattice* L, int64_t nsweeps, cudaStream_t s, bool* fits
 }
 
 // Automatic choice for packed whole films: the row-slab kernel when a colour pass has more words
-// than one CTA of the global kernel takes (512) but at most a fifth of a word per thread of a
-// full-GPU launch of it; else the global kernel.  Measured on 64^2 to 4096^2 fractal films of
-// 6 layers: in that range the global kernel's sweep is its four grid barriers plus one round of
-// words (about 17 us) and the slab kernel's 13 to 16 us; from about a quarter of a word per
-// thread on the global kernel is the faster one.
+// than one CTA of the word kernel takes (512) and at most eight CTAs' worth; else the word kernel
+// on global memory.  Measured on fractal films of 6 layers (bench.py --sizes): with one word per
+// thread the word kernel's sweep is its four grid barriers and one round of words, 13.5 to
+// 13.7 us from 256^2 to 1536^2; the slab kernel's is 13.1 us at 256^2, equal at 384^2 and
+// 15 to 27 us from 512^2 up, so it is kept only where the word kernel runs on a handful of CTAs.
 static bool slabs_preferred(const isf_lattice* L) {
     if (!L->lay.packed || L->f.slab || !L->f.items || L->roff_h.empty() || L->lay.L > kSlabMaxLayers) return false;
-    int dev = 0, sms = 1;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
     const int64_t words = sweep_items_per_pass(L->f);
-    return words > 512 && words * 5 <= (int64_t)sms * 512;
+    return words > 512 && words <= 8 * 512;
 }
 
 int isf_run_sweeps(isf_lattice* L, int64_t nsweeps, void* cuda_stream) {

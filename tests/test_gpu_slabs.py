@@ -111,12 +111,12 @@ def test_fractal2048_slabs_equal_global(I):
     assert_records_equal(a["recs"], b["recs"])
 
 
-@pytest.mark.parametrize("R,L,want", [(16, 3, "global"), (256, 6, "slabs"), (512, 6, "slabs"), (768, 6, "global"),
+@pytest.mark.parametrize("R,L,want", [(16, 3, "global"), (256, 6, "slabs"), (512, 6, "global"), (768, 6, "global"),
                                       (2048, 6, "global")])
 def test_automatic_path_choice(I, R, L, want):
-    """Packed films: the row-slab kernel between about 100^2 and 650^2 sites per layer, where it
-    is the faster one; the global kernel for smaller films (one CTA, no grid barrier) and larger
-    ones (more than a fifth of a word per thread of a full-GPU launch)."""
+    """Packed films: the row-slab kernel while a colour pass has 513 to 4096 words (about 150^2 to
+    350^2 sites per layer), where it is the faster one; the word kernel on global memory for
+    smaller films (one CTA) and larger ones."""
     H = W.fractal_heights(R, R, 0.8, 2, L, seed=3)
     lat = I.Lattice(H, L, seed=1, init="up", packed=True)
     lat.set_schedule([2.0], [0.0], [0], [1])
