@@ -254,7 +254,8 @@ int isf_batch_set_launch(isf_batch* batch, int32_t threads_single, int32_t clust
 /* on != 0: capture each persistent queue launch in its own single-kernel CUDA graph once and
  * replay them on later runs with the same shapes (the per-film arguments are uploaded each run).
  * With or without graphs the queue kernels are launched in one fixed order, so the way they
- * share the SMs does not change from run to run. */
+ * share the SMs does not change from run to run.  With graphs on, a run must not itself be
+ * captured into a caller's graph (its capture would nest). */
 int isf_batch_set_graph(isf_batch* batch, int32_t on);
 /* Autotuner: times short probe runs (copies, not the members) over threads {128, 256, 384, 512}:
  * of the largest single-CTA film, keeping the fastest threads; and, for cluster sizes {8, 16},
