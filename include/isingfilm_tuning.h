@@ -94,6 +94,15 @@ int isf_launch_item_sites(isf_lattice* lat, int32_t* sites);
  * queue, out2[1] from the cluster resident queue.  Waits for the run. */
 int isf_batch_taken(isf_batch* batch, int32_t* out2);
 
+/* Test of the bounded device waits: `ctas` (>= 2, all co-resident) CTAs of one cooperative launch
+ * arrive at the grid barrier of the sweep kernels and then wait, with the kernels' own bounded
+ * wait, for one arrival more than there are CTAs, which nothing makes.  The wait gives up after
+ * 2^22 polls (a few seconds), records ISF_ERR_TIMEOUT and its site in a status word, and the
+ * kernel returns: *status_out = that status (ISF_ERR_TIMEOUT), *where_out = the site (1: grid
+ * barrier).  No fault, no trap; the context stays usable.  Synchronous.
+ * Errors: ISF_ERR_ARG (ctas < 2 or more than can be co-resident), ISF_ERR_CUDA. */
+int isf_debug_wait_timeout(int32_t ctas, int32_t* status_out, int32_t* where_out);
+
 /* Device Philox4x32-10 blocks for checking the generator: for b in [0, nblocks), the block
  * with key (seed_lo, seed_hi) and counter (q0 + b, sweep_lo, sweep_hi, stream) goes to
  * host_out[4b .. 4b+3].  Synchronous. */

@@ -1020,6 +1020,17 @@ int isf_load(const char* path, void* cuda_stream, isf_lattice** out) {
     return ISF_OK;
 }
 
+int isf_debug_wait_timeout(int32_t ctas, int32_t* status_out, int32_t* where_out) {
+    if (ctas < 2 || !status_out || !where_out) return fail(ISF_ERR_ARG, "bad arguments");
+    int status = 0, where = 0;
+    const cudaError_t e = (cudaError_t)wait_probe(ctas, &status, &where);
+    if (e == cudaErrorInvalidValue) return fail(ISF_ERR_ARG, "more CTAs than can be co-resident");
+    if (e != cudaSuccess) return cuda_fail(e, "wait probe");
+    *status_out = status;
+    *where_out = where;
+    return ISF_OK;
+}
+
 int isf_philox_blocks(uint64_t seed, uint32_t stream, uint64_t sweep, uint32_t q0, int64_t nblocks,
                       uint32_t* host_out) {
     if (nblocks < 0 || (nblocks > 0 && !host_out)) return fail(ISF_ERR_ARG, "bad arguments");

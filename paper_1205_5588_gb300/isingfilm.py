@@ -102,6 +102,7 @@ def _declare(lib):
         "isf_batch_run": (C.c_int, [vp, vp]),
         "isf_batch_info": (C.c_int, [vp, i32p]),
         "isf_batch_taken": (C.c_int, [vp, i32p]),
+        "isf_debug_wait_timeout": (C.c_int, [C.c_int32, i32p, i32p]),
         "isf_batch_destroy": (None, [vp]),
         "isf_batch_run_sweeps": (C.c_int, [vp, C.c_int64, vp]),
         "isf_server_create": (C.c_int, [C.c_size_t, C.c_int64, C.POINTER(vp)]),
@@ -515,6 +516,14 @@ def peak_probe(mode, ctas=0, threads=0, iters=1024, stream=None) -> float:
     _check(lib.isf_peak_probe(int(mode), int(ctas), int(threads), int(iters), _stream_handle(stream),
                               C.byref(units)), "peak_probe")
     return units.value
+
+
+def debug_wait_timeout(ctas=2) -> tuple:
+    """Run the grid barrier's bounded wait against an arrival nothing makes
+    (isf_debug_wait_timeout); returns (status the kernel recorded, wait site)."""
+    st, wh = C.c_int32(), C.c_int32()
+    _check(lib.isf_debug_wait_timeout(int(ctas), C.byref(st), C.byref(wh)), "debug_wait_timeout")
+    return st.value, wh.value
 
 
 JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}

@@ -39,7 +39,8 @@ def test_header_declares_the_boundary():
     # tuning and test hooks live in their own header, not in the method's boundary
     hooks = declared_functions(os.path.join(INCLUDE, "isingfilm_tuning.h"))
     for hook in ("isf_set_launch", "isf_set_path", "isf_set_item_sites", "isf_debug_checks", "isf_debug_item_lists",
-                 "isf_debug_slab_partition", "isf_philox_blocks", "isf_peak_probe"):
+                 "isf_debug_slab_partition", "isf_philox_blocks", "isf_peak_probe", "isf_batch_taken",
+                 "isf_debug_wait_timeout"):
         assert hook in hooks and hook not in names
 
 
@@ -96,3 +97,10 @@ def test_peak_probe_rejects_bad_arguments_without_a_gpu(lib):
         with pytest.raises(I.IsfError) as e:
             I.peak_probe(mode, 0, threads, iters, stream=0)
         assert e.value.code == -1
+
+
+def test_wait_probe_argument_errors(lib):
+    from paper_1205_5588_gb300 import isingfilm as I
+    for ctas in (-1, 0, 1):
+        with pytest.raises(I.IsfError):
+            I.debug_wait_timeout(ctas)
