@@ -24,7 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["kernels_sweep.cu", "kernels_words.cu", "kernels_slabs.cu", "kernels_resident.cu", "kernels_aux.cu",
               "noalloc.cu", "kernels_peak.cu"]
 CPP_SOURCES = ["capi.cpp", "batch.cpp", "serve.cpp", "lattice.cpp", "schedule.cpp"]
-HEADERS = ["isf_internal.h", "device_common.cuh", "sweep_core.cuh", "grid_sync.cuh", "capi_internal.h"]
+HEADERS = ["isf_internal.h", "device_common.cuh", "sweep_core.cuh", "grid_sync.cuh", "capi_internal.h", "trace.h"]
 
 
 def cuda_home() -> str:
@@ -81,7 +81,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
         for l in logs:
             sys.stderr.write(l)
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    _run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *[o for _, o in jobs], "-lpthread"])
+    _run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *[o for _, o in jobs], "-lpthread", "-ldl"])
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
 

@@ -423,6 +423,7 @@ void share_units(const std::vector<Item>& A, const std::vector<Item>& B, const s
 int isf_batch_run(isf_batch* b, void* cuda_stream) { return isf_batch_run_sweeps(b, -1, cuda_stream); }
 
 int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
+    const isf::TraceRange trace("isf_batch_run_sweeps");
     if (!b) return fail(ISF_ERR_ARG, "batch is NULL");
     if (max_sweeps < -1 || max_sweeps == 0) return fail(ISF_ERR_ARG, "max_sweeps must be >= 1 or -1");
     int rc = ensure_streams(b);

@@ -595,6 +595,7 @@ static bool slabs_preferred(const isf_lattice* L) {
 }
 
 int isf_run_sweeps(isf_lattice* L, int64_t nsweeps, void* cuda_stream) {
+    const isf::TraceRange trace("isf_run_sweeps");
     if (!L) return fail(ISF_ERR_ARG, "lattice is NULL");
     if (!L->nsteps) return fail(ISF_ERR_STATE, "no schedule set");
     if (L->f.slab) return fail(ISF_ERR_STATE, "a slab film advances by isf_run_pass, with halo exchanges between passes");

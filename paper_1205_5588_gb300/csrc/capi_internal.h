@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "isf_internal.h"
+#include "trace.h"
 #include "../../include/isingfilm_tuning.h"
 
 using isf::Layout;

@@ -160,6 +160,7 @@ void worker_main(isf_server* S) {
             act = S->active;
         }
         if (act.empty()) continue;
+        const isf::TraceRange trace("isf_server_tick");
         isf_batch_clear(batch);
         for (Job* j : act) isf_batch_add(batch, j->lat);
         const auto t_start = Clock::now();
