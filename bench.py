@@ -159,7 +159,8 @@ def probe_peaks(I, stream, target_s=0.05, reps=3) -> dict:
     return out
 
 
-def roofline(attempts_per_launch, t_launch, peaks, sms, sm_max_mhz, kernel, shape, traffic, inst_per_attempt):
+def roofline(attempts_per_launch, t_launch, peaks, sms, sm_max_mhz, kernel, shape, traffic, inst_per_attempt,
+             pipes=None):
     """ALU roofline of one sweep launch, both sides in the algorithmic unit (40 int-ops per
     attempt): achieved = 40 x attempts / launch time; peak = 40 x the attempts/s this GPU reaches
     on the per-attempt arithmetic alone (isf_peak_probe ISF_PEAK_ATTEMPT, measured in this run)."""
@@ -183,6 +184,13 @@ def roofline(attempts_per_launch, t_launch, peaks, sms, sm_max_mhz, kernel, shap
         "frac_of_dispatch_by_instructions": (inst_per_attempt * rate / derived if inst_per_attempt and derived
                                              else None),
     }
+    if pipes:
+        # from the committed ncu capture of the kernel's small case: how busy its issue slots and its
+        # integer ALU pipe were, and the attempts/s its own ALU work would allow at a full ALU pipe
+        ceil["ncu_issue_active"] = pipes["issue_active"]
+        ceil["ncu_alu_pipe_busy"] = pipes["alu_pipe"]
+        ceil["attempts_per_s_at_full_alu_pipe"] = rate / pipes["alu_pipe"]
+        ceil["frac_of_own_alu_pipe_ceiling"] = pipes["alu_pipe"]
     # a film held by one cluster runs on that cluster's SMs only: its share of their ceiling
     used = shape.get("ctas") if shape.get("path") == "resident" else sms
     if used and used < sms:
@@ -265,10 +273,12 @@ def e2e_film(I, spec, seed, steps, stream):
 NCU_RECORDS = {
     "fractal256": {"sources": ["kernels_resident.cu", "sweep_core.cuh", "device_common.cuh"],
                    "sources_sha256": "7eb0ceb4c157983f4913e350a6e95a2ee2a8151005e81e97642390bfe346bf67",
-                   "bytes_per_launch": 1785344.0 + 0.0, "inst_per_attempt": None},
+                   "bytes_per_launch": 1785344.0 + 0.0, "inst_per_attempt": None,
+                   "pipes": {"issue_active": 0.491, "alu_pipe": 0.381}},
     "fractal2048": {"sources": ["kernels_words.cu", "sweep_core.cuh", "device_common.cuh", "grid_sync.cuh"],
                     "sources_sha256": "03fa43aa3b5ac631b510b1dab797589a2e3e49d1af96b5f1c0b3c544ee1b47ef",
-                    "bytes_per_launch": 21731584.0 + 781824.0, "inst_per_attempt": 25.86},
+                    "bytes_per_launch": 21731584.0 + 781824.0, "inst_per_attempt": 25.86,
+                    "pipes": {"issue_active": 0.513, "alu_pipe": 0.477}},
 }
 
 
@@ -346,7 +356,8 @@ def run_impl(args):
                         "isf_read_observables, every step"},
         "gpu_launches": args.steps,
         "roofline": roofline(per_step, t_launch, peaks, sms, sm_max, kernel_of(shape, spec["packed"]),
-                             shape, load_traffic(args.workload), ncu_record(args.workload, "inst_per_attempt")),
+                             shape, load_traffic(args.workload), ncu_record(args.workload, "inst_per_attempt"),
+                             ncu_record(args.workload, "pipes")),
         "clocks": clk,
     }
     if not args.no_tscan and args.workload != "fractal256":
@@ -360,7 +371,8 @@ def run_impl(args):
                 "seconds_per_step": tl, "steps": len(t["times"]), "warmup": 3,
                 "roofline": roofline(t["per_step"], tl, peaks, sms, sm_max,
                                      kernel_of(t["shape"], False), t["shape"],
-                                     load_traffic("fractal256"), ncu_record("fractal256", "inst_per_attempt"))}
+                                     load_traffic("fractal256"), ncu_record("fractal256", "inst_per_attempt"),
+                                     ncu_record("fractal256", "pipes"))}
     del l2buf
     if not args.no_batched:
         # independent films: each rank runs its own share of the list (weak scaling)

@@ -32,7 +32,8 @@ def test_roofline_bookkeeping():
     import bench
     assert bench.OPS_PER_ATTEMPT == 40 and bench.LANES_PER_SM == 128
     for name, rec in bench.NCU_RECORDS.items():
-        assert set(rec) == {"sources", "sources_sha256", "bytes_per_launch", "inst_per_attempt"}
+        assert set(rec) == {"sources", "sources_sha256", "bytes_per_launch", "inst_per_attempt", "pipes"}
+        assert 0 < rec["pipes"]["issue_active"] <= 1 and 0 < rec["pipes"]["alu_pipe"] <= 1
         if rec["sources_sha256"] is not None:
             assert len(rec["sources_sha256"]) == 64
         valid = rec["sources_sha256"] == bench.kernel_sources_sha256(rec["sources"])
@@ -57,3 +58,7 @@ def test_roofline_bookkeeping():
     assert abs(c["frac_of_arithmetic_ceiling_of_sms_in_use"] - 0.25 * 152 / 16) < 1e-12
     assert "sms_in_use" not in bench.roofline(1e12, 2.0, peaks, 152, 2070.0, "k", {"path": "global", "ctas": 152},
                                               None, None)["ceilings"]
+    # with the ncu pipe record: the attempts/s the kernel's own ALU work allows at a full ALU pipe
+    r = bench.roofline(1e12, 2.0, peaks, 152, 2070.0, "k", {}, None, None, {"issue_active": 0.5, "alu_pipe": 0.4})
+    c = r["ceilings"]
+    assert c["ncu_alu_pipe_busy"] == 0.4 and abs(c["attempts_per_s_at_full_alu_pipe"] - 0.5e12 / 0.4) < 1e-3
