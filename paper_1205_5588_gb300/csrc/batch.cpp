@@ -470,6 +470,14 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
         else C.push_back(L);
         cudaGetLastError();
     }
+    // With films on the cluster global-memory kernel, the cluster-resident films join its queue:
+    // launched first, that kernel holds the SMs a resident cluster would need, and it runs these
+    // films about as fast per SM; a resident cluster kernel placed beside it only leaves some of
+    // them on fewer SMs, from run to run (the bench's int8 batch: 10.7 s, or 13 s).
+    if (!E.empty() && !B.empty()) {
+        E.insert(E.end(), B.begin(), B.end());
+        B.clear();
+    }
     auto longest_first = [](const Item& x, const Item& y) { return x.work > y.work; };
     std::sort(A.begin(), A.end(), longest_first);
     std::sort(B.begin(), B.end(), longest_first);

@@ -199,7 +199,7 @@ int sweep_max_ctas_for(const DevFilm& f, int threads, int* max_ctas);  // co-res
 // bit-packed whole film with occupied-word lists; co-resident CTAs with this block size.
 int launch_words(const SweepArgs& a, int ctas, int threads, void* stream);
 int words_max_ctas(int threads, int* out);
-// `ctas` co-resident CTAs wait at the grid barrier for an arrival nothing makes (kernels_words.cu);
+// `ctas` co-resident CTAs wait at the grid barrier for an arrival nothing makes (kernels_sweep.cu);
 // *status, *where: the status word and wait site the kernel recorded.
 int wait_probe(int ctas, int* status, int* where);
 

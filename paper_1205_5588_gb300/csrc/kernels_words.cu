@@ -229,41 +229,7 @@ cudaError_t words_smem_attr(int threads) {
     return cudaFuncSetAttribute(k_words<GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ahead_bytes(threads));
 }
 
-// Test of the grid barrier's bounded wait: every CTA arrives once, then waits, with the kernels'
-// own wait, for one arrival more than there are CTAs, which nothing makes; the wait gives up,
-// records ISF_ERR_TIMEOUT in the status word and the kernel returns.
-__global__ void k_wait_probe(FilmState* st) {
-    __shared__ int ok_s;
-    unsigned target = 0;
-    grid_arrive(st, gridDim.x, target);
-    grid_wait(st, gridDim.x, target + 1u, &ok_s);
-}
-
 }  // namespace
-
-int wait_probe(int ctas, int* status, int* where) {
-    if (ctas < 2) return (int)cudaErrorInvalidValue;
-    int dev = 0, sms = 0, per = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wait_probe, 32, 0);
-    if (e != cudaSuccess) return (int)e;
-    if (ctas > sms * per) return (int)cudaErrorInvalidValue;       // all CTAs must be co-resident
-    FilmState* st = nullptr;
-    e = cudaMalloc(&st, sizeof(FilmState));
-    if (e != cudaSuccess) return (int)e;
-    e = cudaMemset(st, 0, sizeof(FilmState));
-    void* args[] = {&st};
-    if (e == cudaSuccess) e = cudaLaunchCooperativeKernel((const void*)k_wait_probe, dim3(ctas), dim3(32), args, 0, nullptr);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    FilmState h{};
-    if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof h, cudaMemcpyDeviceToHost);
-    cudaFree(st);
-    if (e != cudaSuccess) return (int)e;
-    *status = h.error;
-    *where = h.error_where;
-    return 0;
-}
 
 int words_smem_bytes(int threads) { return (int)ahead_bytes(threads); }
 

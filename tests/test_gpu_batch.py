@@ -63,10 +63,13 @@ def test_batch_matches_oracle_and_solo(I, graph, tune):
         b.tune()
     b.run()
     info = b.info()
-    assert info["single_cta_films"] >= 5 and info["cluster_films"] >= 2, info
+    # the batch has films for the cluster global-memory kernel, so the two films that fit a
+    # cluster's shared memory join its queue (the resident cluster kernel is covered by
+    # test_batch_launch_shapes, whose films fit)
+    assert info["single_cta_films"] >= 5 and info["cluster_films"] == 0, info
     # a global-memory film takes one CTA only if its work is at most an even share of the batch's
     # per CTA (here the two largest films hold most of the work): one CTA or a cluster each
-    assert info["global_cta_films"] >= 1 and info["global_cta_films"] + info["global_cluster_films"] == 5, info
+    assert info["global_cta_films"] >= 1 and info["global_cta_films"] + info["global_cluster_films"] == 7, info
     for f, lat in zip(films, lats):
         o = run_oracle(f, f["schedule"])
         assert_records_equal(lat.observables(), o["recs"])
@@ -138,12 +141,14 @@ def test_batch_of_one_and_empty(I):
 
 @pytest.mark.parametrize("shape", [(64, 8, 64), (512, 16, 96), (160, 2, 512)])
 def test_batch_launch_shapes(I, shape):
-    """Explicit launch shapes, down to one site-taking warp next to the folding warp."""
+    """Explicit launch shapes, down to one site-taking warp next to the folding warp; no film
+    needs the cluster global-memory kernel, so the two large films run cluster-resident."""
     films = mixed_films()[:6]
     lats = [make(I, f) for f in films]
     b = I.Batch(lats)
     b.set_launch(*shape)
     b.run()
+    assert b.info()["cluster_films"] == 2 and b.info()["global_cluster_films"] == 0, b.info()
     for f, lat in zip(films, lats):
         o = run_oracle(f, f["schedule"])
         assert_records_equal(lat.observables(), o["recs"])
