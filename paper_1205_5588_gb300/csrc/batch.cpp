@@ -523,8 +523,8 @@ int isf_batch_run_sweeps(isf_batch* b, int64_t max_sweeps, void* cuda_stream) {
     // others wait, so the batch's time would depend on the placement.  When all the work is on the
     // two global-memory classes (bit-packed, periodic-column or over-sized films: the same code
     // per site, so work is a fair measure of time), the GPU is shared in proportion to their work
-    // and both kernels are resident from the start.  The resident int8 classes run several times
-    // faster per site than the global-memory ones, so there work is no measure of time; they keep
+    // and both kernels are resident from the start.  With resident int8 classes the same sharing
+    // measured slower (27 s for the bench's int8 batch against 10.7), so those batches keep
     // whole-GPU grids, and the order of the launches (global-memory kernels, then the single-CTA
     // and the cluster kernel: the fastest order measured) is fixed, with or without graphs.
     if (A.empty() && B.empty()) share_units(A, B, D, E, &units_a, &units_b, &units_d, &units_e);
